@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the short-range P3M path on GB300: SR pair interactions/s and
+particle-steps/s.
+
+Workload (default): one periodic box of 256^3 particles, side 256 grid units,
+positions from Zel'dovich displacements of a Gaussian field with P(k) ~ k^-2
+(sigma_delta = 1 on the grid), velocities N(0, 0.1^2), unit masses, seed 2.
+One step = one full step of Eq. (tstep): long-range PM half kick, 5 short-range
+SKS sub-cycles (each: stream, rebin, pair force + kick, stream), PM half kick.
+Inputs stay resident in HBM; the working set (~1.5 GB) is far larger than L2,
+so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  value = SR pair interactions (ordered pairs i != j
+inside r_cut, summed over all sub-cycles and ranks) per second of device time.
+The inside-cutoff counts come from a deterministic replay of the timed steps
+with the counting kernel variant (the replay reproduces the timed trajectory
+bit for bit, which is asserted).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SR pair interactions/s and particle-steps/s on 1 GB300 (served vs plain); p99 latency"
+FLOPS_PER_PAIR = 29  # counted FP32 flops per candidate pair (plus one rsqrt)
+
+CONFIGS = {
+    # name: (grid side, box L, seed, sub-cycles per step, dt per step)
+    "zeldovich256": dict(side=256, L=256.0, seed=2, n_c=5, dt=0.5,
+                         desc="256^3 Zel'dovich (P(k)~k^-2, sigma_delta=1), box 256, "
+                              "PM half kicks + 5 SR sub-cycles per step"),
+    "zeldovich128": dict(side=128, L=128.0, seed=2, n_c=5, dt=0.5,
+                         desc="128^3 Zel'dovich (P(k)~k^-2, sigma_delta=1), box 128, "
+                              "PM half kicks + 5 SR sub-cycles per step"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="zeldovich256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU oracle sample time")
+    ap.add_argument("--no-pm", action="store_true", help="short-range sub-cycles only (no PM half kicks)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def make_inputs(cfg):
+    import synth
+    pos = synth.zeldovich(cfg["side"], seed=cfg["seed"], L=cfg["L"])
+    vel = synth.gaussian_velocities(len(pos), seed=cfg["seed"], sigma=0.1)
+    return pos, vel
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(pos, L, split_params, target_s: float, seed: int = 99):
+    """Oracle (FP64, all host cores) on a bounded random sample of particles of
+    the same box: inside-cutoff pair interactions per second."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    n = len(pos)
+    sel = rng.choice(n, size=min(n, 4096), replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    _, w = oracle.force_mesh(pos, L, split_params, sel=sel)
+    t_probe = time.perf_counter() - t0
+    # the probe includes the oracle's cell-list build over all n particles; size
+    # the sample so that the measured call lasts about target_s
+    m = int(min(n, max(4096, 4096 * target_s / max(t_probe, 1e-3))))
+    sel = rng.choice(n, size=m, replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    _, w = oracle.force_mesh(pos, L, split_params, sel=sel)
+    dt = time.perf_counter() - t0
+    return dict(value=w / dt, pairs=w, seconds=dt, sample_particles=m, threads=oracle.threads())
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    import numpy as np
+
+    import oracle
+    from oracle import split
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    cfg = CONFIGS[args.config]
+    pos, _ = make_inputs(cfg)
+    sp = split.default_split()
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup) / 2)
+    probe = cpu_oracle_rate(pos, cfg["L"], sp, target_s=per_step)
+    m = probe["sample_particles"]
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        oracle.force_mesh(pos, cfg["L"], sp, sel=rng.choice(len(pos), size=m, replace=False).astype(np.int64))
+    tot_pairs, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        sel = rng.choice(len(pos), size=m, replace=False).astype(np.int64)
+        t0 = time.perf_counter()
+        _, w = oracle.force_mesh(pos, cfg["L"], sp, sel=sel)
+        tot_t += time.perf_counter() - t0
+        tot_pairs += w
+    value = tot_pairs / tot_t
+    sample = ("short-range force of %d random particles of the %s box per step (all %d particles as sources, "
+              "cell list rebuilt per call), FP64" % (m, cfg["desc"].split(",")[0], len(pos)))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pair interactions/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.config, "desc": cfg["desc"]},
+            "cpu_baseline": {"value": value, "unit": "pair interactions/s", "cores": oracle.threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pair interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1410_2805_gb300 as hacc
+    from paper_1410_2805_gb300 import build as hbuild
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hbuild.build()
+    cfg = CONFIGS[args.config]
+    L = cfg["L"]
+    pos_np, vel_np = make_inputs(cfg)
+    n = len(pos_np)
+    split = hacc.default_split()
+    pm = hacc.PM()
+    box = hacc.Box(L=L)
+    ctx = hacc.Context(local)
+    stream = torch.cuda.current_stream()
+    pos = torch.from_numpy(pos_np).cuda()
+    vel = torch.from_numpy(vel_np).cuda()
+    use_pm = not args.no_pm
+    dt, n_c = cfg["dt"], cfg["n_c"]
+
+    def step(p, v):
+        if use_pm:
+            ctx.step(box, split, pm, p, v, dt, n_c)
+        else:
+            ctx.subcycle(box, split, p, v, dt, n_c)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(pos, vel)
+    ctx.sync()
+    snap_p, snap_v = pos.clone(), vel.clone()
+
+    # ---- timed region: device-resident inputs ----
+    ctx.stats_read(reset=True)
+    ctx.stats_enable(timing=True, counting=False)
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(pos, vel)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ctx.sync()
+    st = ctx.stats_read(reset=True)
+    ctx.stats_enable(timing=False, counting=False)
+    final_p, final_v = pos.clone(), vel.clone()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+
+    # ---- deterministic replay with pair counting (untimed) ----
+    pos.copy_(snap_p)
+    vel.copy_(snap_v)
+    ctx.stats_enable(timing=False, counting=True)
+    for _ in range(args.steps):
+        step(pos, vel)
+    ctx.sync()
+    cnt = ctx.stats_read(reset=True)
+    ctx.stats_enable(timing=False, counting=False)
+    replay_ok = bool(torch.equal(pos, final_p) and torch.equal(vel, final_v))
+    within = cnt["within_pairs"]
+    cand = cnt["candidate_pairs"]
+
+    # ---- end to end through the host-buffer C ABI (pinned memory) ----
+    e2e = None
+    if not args.no_e2e:
+        hp = snap_p.cpu().pin_memory()
+        hv = snap_v.cpu().pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            if use_pm:
+                ctx.step_host(box, split, pm, hp, hv, dt, n_c)
+            else:
+                ctx.subcycle_host(box, split, hp, hv, dt, n_c)
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e_same = bool(torch.equal(hp.cuda(), final_p) and torch.equal(hv.cuda(), final_v))
+        e2e = {"value": world * within / t_e2e, "unit": "pair interactions/s",
+               "h2d_bytes_per_step": 2 * n * 16, "d2h_bytes_per_step": 2 * n * 16,
+               "ms_per_step": 1e3 * t_e2e / args.steps, "same_result_as_device_run": e2e_same}
+
+    # ---- numbers ----
+    secs = ms_max / 1e3
+    value = world * within / secs
+    psteps = world * n * n_c * args.steps / secs
+    peaks = measured_peaks()
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    smax = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    peak = fp32_peak_tflops(num_sms, smax)
+    force_s = st["force_ms"] / 1e3
+    achieved = cand * FLOPS_PER_PAIR / force_s / 1e12 if force_s > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "k_sr_force (pair force + kick + stream)",
+                "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (sm_max_mhz of measured peaks)"
+                              % (num_sms, smax),
+                "flops_per_pair": FLOPS_PER_PAIR, "force_ms_per_launch": st["force_ms"] / max(1, st["force_launches"]),
+                "force_launches": st["force_launches"], "force_share_of_step": st["force_ms"] / ms if ms else None}
+    line = {"metric": METRIC, "value": value, "unit": "pair interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.config, "desc": cfg["desc"], "particles": n, "box": L,
+                       "sub_cycles_per_step": n_c, "pm": use_pm, "dt": dt,
+                       "l2": "inputs larger than L2 (working set ~%.1f GB)" % (n * 100 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "particle_steps_per_s": psteps,
+            "candidate_pairs_per_s": world * cand / secs,
+            "within_cutoff_pairs_per_step": within / args.steps,
+            "candidate_pairs_per_step": cand / args.steps,
+            "replay_bitwise_equal": replay_ok,
+            "gpu_launches": st["kernel_launches"],
+            "roofline": roofline, "e2e": e2e, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import split as osplit
+        sp = osplit.default_split()
+        sp["r_cut"] = float(np.float32(sp["r_cut"]))
+        sp["eps"] = float(np.float32(sp["eps"]))
+        cb = cpu_oracle_rate(snap_p.cpu().numpy(), L, sp, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "pair interactions/s", "cores": cb["threads"],
+                                "kind": "oracle",
+                                "sample": "FP64 short-range force of %d random particles of the warmed-up box "
+                                          "(all %d particles as sources, %.1f s)" % (cb["sample_particles"], n,
+                                                                                      cb["seconds"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * hacc.h - C ABI of a GB300 (sm_103a) library for the short-range
+ * particle-particle force of HACC's force-split N-body method
+ * (Habib et al., arXiv 1410.2805).
+ *
+ * The method (Sec. 2.3-2.5, Sec. 3.1, Sec. 3.3 of the paper): particles in a
+ * periodic cube of side L are binned into a chaining mesh of nc^3 cells of
+ * width L/nc >= r_cut; each particle i then sums, over the particles j of the
+ * 27 cells around its own (periodic minimum image),
+ *
+ *     a_i = G * sum_{j != i, s < r_cut^2} m_j r_ij f_SR(s),
+ *     f_SR(s) = (s + eps)^(-3/2) - P5(s),   s = r_ij . r_ij,  r_ij = x_j - x_i
+ *
+ * (Eq. (force)), and the short-range map is sub-cycled with symmetric
+ * stream-kick-stream steps (Sec. 2.5) inside a kick-sub-cycle-kick full step
+ * around the long-range particle-mesh force (Eq. (tstep)).
+ *
+ * Units: grid units (the PM grid spacing is 1 when ng = L).  Positions and
+ * velocities are FP32; arithmetic of the pair force is FP32 with FP32
+ * accumulation; FP64 only in the diagnostics.
+ *
+ * Memory: every particle array is a DEVICE pointer owned by the caller
+ * (unless an entry point's name ends in _host), 16-byte aligned, with one
+ * 4-float row per particle:
+ *     pos_m : (x, y, z, m)      positions in [-L, 2L) and masses
+ *     vel   : (vx, vy, vz, w)   w is ignored and preserved as 0 on output
+ *     acc   : (ax, ay, az, 0)
+ * Row i of every output belongs to row i of the inputs (the library sorts
+ * internally and un-permutes).  The library never frees caller memory.  The
+ * context owns its scratch (a pool grown on demand and bounded by the HBM
+ * budget given at creation) and reuses it across calls.
+ *
+ * Streams: each call enqueues its work on `stream` (NULL = legacy default
+ * stream) and returns without synchronising, except the _host variants and
+ * hacc_ctx_sync, which wait for their stream.  Calls on one context must not
+ * run concurrently from several host threads.
+ *
+ * Errors: argument and domain errors are returned before anything is
+ * enqueued.  Errors found on the device (a coordinate outside [-L, 2L) or
+ * not finite, a device-side wait that gave up) raise a flag that the next
+ * hacc_ctx_sync returns (and clears); affected outputs are then undefined
+ * but every memory access stays in bounds.  hacc_last_error gives a message.
+ */
+#ifndef HACC_H
+#define HACC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *hacc_stream_t;
+
+typedef enum {
+    HACC_OK = 0,
+    HACC_EINVAL = 1,   /* null pointer, negative size, box side not an FP32 value, ... */
+    HACC_EDOMAIN = 2,  /* nc < 3, cell width below r_cut, r_cut >= L/2, or a position
+                          outside [-L, 2L) / not finite (reported by hacc_ctx_sync) */
+    HACC_ENOMEM = 3,   /* scratch would exceed the context's HBM budget, or cudaMalloc failed */
+    HACC_ECUDA = 4,    /* a CUDA runtime / cuFFT call failed */
+    HACC_ETIMEOUT = 5  /* a bounded device-side wait gave up (reported by hacc_ctx_sync) */
+} hacc_status;
+
+/* Periodic box.  L: side in grid units; must be exactly representable in FP32
+ * (the wrap and the minimum image are done in FP32).  nc: chaining-mesh cells
+ * per side, 0 = floor(L / r_cut) (one fewer if the cell width would come
+ * within a relative 1e-6 of r_cut); 3 <= nc <= 1024 and L/nc >= r_cut
+ * (Sec. 2.4 "chaining mesh", Sec. 3.1 "26 neighbouring" cells).  ng: PM grid
+ * points per side, used by hacc_step only (0 = round(L)). */
+typedef struct {
+    double L;
+    int32_t nc;
+    int32_t ng;
+} hacc_box;
+
+/* Force split of Sec. 2.3/3.1.  r_cut: matching scale (pairs with s >= r_cut^2
+ * do not interact); eps: Plummer softening in units of length^2 (it is added
+ * to s); poly: P5(s) = sum_k poly[k] s^k, ascending powers; G: prefactor.
+ * Requires 0 < r_cut, eps >= 0. */
+typedef struct {
+    float r_cut;
+    float eps;
+    double poly[6];
+    float G;
+} hacc_split;
+
+/* Long-range spectral PM parameters (Sec. 2.3): Gauss-sinc filter width sigma
+ * and sinc power ns of Eq. (filter) (nominal 0.8 and 3). */
+typedef struct {
+    float sigma;
+    int32_t ns;
+} hacc_pm;
+
+typedef struct hacc_ctx hacc_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * scratch the context may hold (0 = no bound beyond the device's memory).
+ * *out receives the context or NULL on failure. */
+hacc_status hacc_ctx_create(hacc_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Free the context and its scratch (synchronises the device first).  NULL is a no-op. */
+void hacc_ctx_destroy(hacc_ctx *ctx);
+
+/* Message for the last error seen on this context ("" if none).  Owned by the context. */
+const char *hacc_last_error(const hacc_ctx *ctx);
+
+/* Wait for `stream`, then return and clear any flag raised on the device
+ * (HACC_EDOMAIN, HACC_ETIMEOUT) or a pending CUDA error. */
+hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream);
+
+/* Bytes of scratch the context currently holds. */
+size_t hacc_ctx_scratch_bytes(const hacc_ctx *ctx);
+
+/* Default split parameters, computed on the host in FP64 from Eq. (fitform):
+ * r_cut = root of r^2 F_grid(r) = 1 near three grid cells; P5 = least-squares
+ * fit of F_grid(r)/r on (0, r_cut], residuals weighted by r^3, constrained to
+ * P5(r_cut^2) = F_grid(r_cut)/r_cut; eps = 2.5e-4; G = 1. */
+hacc_status hacc_split_default(hacc_split *out);
+
+/* The chaining-mesh size hacc_box.nc = 0 resolves to, or -1 if the box is too
+ * small (fewer than 3 cells of width >= r_cut). */
+int32_t hacc_mesh_cells(double L, float r_cut);
+
+/* Chaining-mesh build (Sec. 2.4 / Sec. 3.3; Hockney's chaining mesh):
+ * wraps pos_m into [0, L) IN PLACE (x < 0 -> x + L, x >= L -> x - L, in FP32;
+ * a result that rounds to L becomes 0), assigns each particle the cell
+ * (ix, iy, iz) with ix the largest integer such that ix * L <= x * nc (exact),
+ * linear id (iz*nc + iy)*nc + ix, and sorts stably by cell:
+ *   cell_id    [n]       cell of each particle (input order)
+ *   cell_start [nc^3+1]  first sorted slot of each cell; cell_start[nc^3] = n
+ *   perm       [n]       perm[k] = input row of sorted slot k; within a cell,
+ *                        ascending input row
+ * All three are caller-owned device arrays. */
+hacc_status hacc_bin(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, float *pos_m,
+                     int32_t *cell_id, int32_t *cell_start, int32_t *perm, hacc_stream_t stream);
+
+/* Short-range force (Eq. (force)) on every particle from the particles of its
+ * 27 neighbouring chaining-mesh cells, cut at r_cut, periodic minimum image.
+ * pos_m is not modified.  acc[n] receives (ax, ay, az, 0).
+ * pair_counts: NULL, or a device array of 2 uint64 that receives
+ *   [0] candidate pairs of the 27-cell chaining mesh, sum_c n_c * sum_nbr n_j
+ *       (self pairs included), exact;
+ *   [1] ordered pairs (i, j), j != i, evaluated inside the cutoff.
+ * Counting runs a slower kernel variant; forces are bitwise the same. */
+hacc_status hacc_sr_force(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                          const float *pos_m, float *acc, uint64_t *pair_counts, hacc_stream_t stream);
+
+/* n_sub short-range sub-cycles of step h = dt / n_sub (Sec. 2.5, SKS form):
+ *   x += (h/2) v;  rebin;  v += h a_SR(x);  x += (h/2) v
+ * Adjacent half streams are fused.  pos_m and vel are updated in place;
+ * positions come back wrapped into [0, L).  n_sub >= 1. */
+hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                          float *pos_m, float *vel, double dt, int32_t n_sub, hacc_stream_t stream);
+
+/* One full step of Eq. (tstep): M_lr(dt/2) (M_sr(dt/n_c))^n_c M_lr(dt/2), where
+ * M_lr is a kick by the long-range spectral PM force (CIC deposit, Eq. (filter)
+ * Gauss-sinc filter, Eq. (greenf) influence function, Eq. (sldiff) Super-Lanczos
+ * gradient, CIC interpolation; Sec. 2.3) on an ng^3 grid, and M_sr the
+ * sub-cycle above. */
+hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
+                      int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
+
+/* Long-range PM acceleration alone: acc[n] receives (ax, ay, az, 0). */
+hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, int64_t n,
+                          const float *pos_m, float *acc, hacc_stream_t stream);
+
+/* FP64 diagnostics of one box: out (device, 5 doubles) receives
+ * [0..2] sum m v, [3] kinetic energy sum m v^2/2, [4] short-range pair
+ * potential energy sum_{i<j, s<r_cut^2} G m_i m_j phi(s), where
+ * phi(s) = -(s+eps)^(-1/2) - sum_k poly[k] s^(k+1)/(2(k+1)) shifted so that
+ * phi(r_cut^2) = 0 (so that -grad phi gives Eq. (force)). Per-pair terms are
+ * FP32, per-particle sums FP32, the box sums FP64. */
+hacc_status hacc_diagnostics(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                             const float *pos_m, const float *vel, double *out, hacc_stream_t stream);
+
+/* Host-buffer variants: pos_m, vel (and acc) are HOST pointers (page-locked
+ * memory gives the fastest copies).  Each call copies the inputs to scratch
+ * on the device, runs the device entry point of the same name, copies the
+ * results back and waits for the stream. */
+hacc_status hacc_sr_force_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                               const float *pos_m, float *acc, hacc_stream_t stream);
+hacc_status hacc_subcycle_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                               float *pos_m, float *vel, double dt, int32_t n_sub, hacc_stream_t stream);
+hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
+                           int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
+
+/* Run statistics kept by a context (instrumentation, not part of the method). */
+typedef struct {
+    int64_t kernel_launches;  /* kernels this context launched */
+    int64_t force_launches;   /* pair-force kernel launches */
+    double force_ms;          /* summed CUDA-event durations of those launches (timing on) */
+    uint64_t candidate_pairs; /* 27-cell candidate pairs of those launches (counting on) */
+    uint64_t within_pairs;    /* ordered pairs (i, j != i) inside the cutoff (counting on) */
+} hacc_stats;
+
+/* timing != 0: record a CUDA event pair on the call's stream around every
+ * pair-force launch.  counting != 0: run the counting variant of the pair
+ * kernel (bitwise the same forces) and accumulate pair counts.  Both off by
+ * default. */
+hacc_status hacc_stats_enable(hacc_ctx *ctx, int timing, int counting);
+
+/* Wait for the device, fill *out, and zero the statistics if reset != 0. */
+hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HACC_H */

@@ -1,0 +1,312 @@
+"""Python binding of the hacc GB300 library (short-range P3M force of HACC,
+arXiv 1410.2805).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+libhacc.so (csrc/), reached through the C ABI declared in include/hacc.h.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if
+the library has not been built, importing the binding's entry points raises.
+
+    import torch, paper_1410_2805_gb300 as hacc
+    ctx = hacc.Context()
+    split = hacc.default_split()
+    box = hacc.Box(L=32.0)
+    acc = ctx.sr_force(box, split, pos)            # pos: (n, 4) float32 CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhacc.so")
+
+HACC_OK, HACC_EINVAL, HACC_EDOMAIN, HACC_ENOMEM, HACC_ECUDA, HACC_ETIMEOUT = range(6)
+_STATUS_NAMES = {0: "HACC_OK", 1: "HACC_EINVAL", 2: "HACC_EDOMAIN", 3: "HACC_ENOMEM", 4: "HACC_ECUDA",
+                 5: "HACC_ETIMEOUT"}
+
+
+class HaccError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("nc", ctypes.c_int32), ("ng", ctypes.c_int32)]
+
+
+class _Split(ctypes.Structure):
+    _fields_ = [("r_cut", ctypes.c_float), ("eps", ctypes.c_float), ("poly", ctypes.c_double * 6),
+                ("G", ctypes.c_float)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("force_launches", ctypes.c_int64),
+                ("force_ms", ctypes.c_double), ("candidate_pairs", ctypes.c_uint64),
+                ("within_pairs", ctypes.c_uint64)]
+
+
+class _Pm(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_float), ("ns", ctypes.c_int32)]
+
+
+@dataclass
+class Box:
+    """Periodic cube: side L (an FP32 value, grid units), nc chaining-mesh
+    cells per side (0 = default), ng PM grid points per side (0 = round(L))."""
+    L: float
+    nc: int = 0
+    ng: int = 0
+
+    def _c(self):
+        return _Box(float(self.L), int(self.nc), int(self.ng))
+
+
+@dataclass
+class Split:
+    """Force split: cutoff r_cut, softening eps (length^2), P5 coefficients in
+    ascending powers of s, prefactor G."""
+    r_cut: float
+    eps: float
+    poly: tuple = field(default_factory=lambda: (0.0,) * 6)
+    G: float = 1.0
+
+    def _c(self):
+        return _Split(float(self.r_cut), float(self.eps), (ctypes.c_double * 6)(*[float(x) for x in self.poly]),
+                      float(self.G))
+
+    def as_dict(self):
+        return dict(r_cut=float(self.r_cut), eps=float(self.eps), poly=list(self.poly), G=float(self.G))
+
+
+@dataclass
+class PM:
+    """Gauss-sinc filter width sigma and sinc power ns (Eq. (filter))."""
+    sigma: float = 0.8
+    ns: int = 3
+
+    def _c(self):
+        return _Pm(float(self.sigma), int(self.ns))
+
+
+_lib = None
+
+
+def lib():
+    """Load libhacc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhacc.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                               "or `python -m paper_1410_2805_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i32, i64, d, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        sig = {
+            "hacc_ctx_create": (st, [ctypes.POINTER(p), ctypes.c_int, ctypes.c_size_t]),
+            "hacc_ctx_destroy": (None, [p]),
+            "hacc_last_error": (ctypes.c_char_p, [p]),
+            "hacc_ctx_sync": (st, [p, p]),
+            "hacc_ctx_scratch_bytes": (ctypes.c_size_t, [p]),
+            "hacc_split_default": (st, [ctypes.POINTER(_Split)]),
+            "hacc_mesh_cells": (i32, [d, ctypes.c_float]),
+            "hacc_bin": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p, p]),
+            "hacc_sr_force": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, p]),
+            "hacc_subcycle": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, d, i32, p]),
+            "hacc_step": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), ctypes.POINTER(_Pm), i64, p, p, d,
+                               i32, p]),
+            "hacc_pm_force": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Pm), i64, p, p, p]),
+            "hacc_diagnostics": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, p]),
+            "hacc_sr_force_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p]),
+            "hacc_subcycle_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, d, i32, p]),
+            "hacc_step_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), ctypes.POINTER(_Pm), i64, p,
+                                    p, d, i32, p]),
+            "hacc_stats_enable": (st, [p, ctypes.c_int, ctypes.c_int]),
+            "hacc_stats_read": (st, [p, ctypes.POINTER(_Stats), ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_split() -> Split:
+    """The library's default split (host FP64 fit of Eq. (fitform))."""
+    s = _Split()
+    st = lib().hacc_split_default(ctypes.byref(s))
+    if st != HACC_OK:
+        raise HaccError(st, "hacc_split_default")
+    return Split(r_cut=s.r_cut, eps=s.eps, poly=tuple(s.poly), G=s.G)
+
+
+def mesh_cells(L: float, r_cut: float) -> int:
+    return int(lib().hacc_mesh_cells(float(L), float(r_cut)))
+
+
+def _split_of(split) -> Split:
+    if isinstance(split, Split):
+        return split
+    return Split(r_cut=split["r_cut"], eps=split["eps"], poly=tuple(split["poly"]), G=split.get("G", 1.0))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _dev_rows(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2
+            and t.shape[1] == 4 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous (n, 4) float32 CUDA tensor" % name)
+    return t
+
+
+class Context:
+    """One hacc_ctx on a CUDA device; owns the scratch pool of the calls."""
+
+    def __init__(self, device: int | None = None, hbm_budget_bytes: int = 0):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self._h = ctypes.c_void_p()
+        st = lib().hacc_ctx_create(ctypes.byref(self._h), self.device, int(hbm_budget_bytes))
+        if st != HACC_OK:
+            raise HaccError(st, "hacc_ctx_create(device=%d)" % self.device)
+
+    def close(self):
+        if self._h:
+            lib().hacc_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _check(self, st, what):
+        if st != HACC_OK:
+            msg = lib().hacc_last_error(self._h)
+            raise HaccError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def sync(self, stream=None):
+        self._check(lib().hacc_ctx_sync(self._h, self._stream(stream)), "hacc_ctx_sync")
+
+    def stats_enable(self, timing: bool = False, counting: bool = False):
+        self._check(lib().hacc_stats_enable(self._h, int(timing), int(counting)), "hacc_stats_enable")
+
+    def stats_read(self, reset: bool = True) -> dict:
+        st = _Stats()
+        self._check(lib().hacc_stats_read(self._h, ctypes.byref(st), int(reset)), "hacc_stats_read")
+        return dict(kernel_launches=st.kernel_launches, force_launches=st.force_launches, force_ms=st.force_ms,
+                    candidate_pairs=st.candidate_pairs, within_pairs=st.within_pairs)
+
+    def scratch_bytes(self) -> int:
+        return int(lib().hacc_ctx_scratch_bytes(self._h))
+
+    def bin(self, box: Box, r_cut: float, pos, stream=None):
+        """Wrap pos in place and bin it; returns (cell_id, cell_start, perm) int32 tensors."""
+        import torch
+        _dev_rows(pos, "pos")
+        n = pos.shape[0]
+        nc = box.nc or mesh_cells(box.L, r_cut)
+        cell = torch.empty(n, dtype=torch.int32, device=pos.device)
+        start = torch.empty(nc ** 3 + 1, dtype=torch.int32, device=pos.device)
+        perm = torch.empty(n, dtype=torch.int32, device=pos.device)
+        self._check(lib().hacc_bin(self._h, ctypes.byref(box._c()), float(r_cut), n, _ptr(pos), _ptr(cell),
+                                   _ptr(start), _ptr(perm), self._stream(stream)), "hacc_bin")
+        return cell, start, perm
+
+    def sr_force(self, box: Box, split, pos, acc=None, pair_counts=None, stream=None):
+        import torch
+        _dev_rows(pos, "pos")
+        sp = _split_of(split)
+        if acc is None:
+            acc = torch.empty_like(pos)
+        _dev_rows(acc, "acc")
+        self._check(lib().hacc_sr_force(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
+                                        _ptr(pos), _ptr(acc), _ptr(pair_counts), self._stream(stream)),
+                    "hacc_sr_force")
+        return acc
+
+    def pair_counts(self, box: Box, split, pos, stream=None):
+        """(candidate pairs, pairs inside the cutoff) of one force evaluation."""
+        import torch
+        pc = torch.zeros(2, dtype=torch.int64, device=pos.device)
+        self.sr_force(box, split, pos, pair_counts=pc, stream=stream)
+        self.sync(stream)
+        c, w = pc.tolist()
+        return int(c), int(w)
+
+    def subcycle(self, box: Box, split, pos, vel, dt: float, n_sub: int, stream=None):
+        _dev_rows(pos, "pos")
+        _dev_rows(vel, "vel")
+        sp = _split_of(split)
+        self._check(lib().hacc_subcycle(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
+                                        _ptr(pos), _ptr(vel), float(dt), int(n_sub), self._stream(stream)),
+                    "hacc_subcycle")
+
+    def step(self, box: Box, split, pm: PM, pos, vel, dt: float, n_c: int, stream=None):
+        _dev_rows(pos, "pos")
+        _dev_rows(vel, "vel")
+        sp = _split_of(split)
+        self._check(lib().hacc_step(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), ctypes.byref(pm._c()),
+                                    pos.shape[0], _ptr(pos), _ptr(vel), float(dt), int(n_c), self._stream(stream)),
+                    "hacc_step")
+
+    def pm_force(self, box: Box, pm: PM, pos, acc=None, stream=None):
+        import torch
+        _dev_rows(pos, "pos")
+        if acc is None:
+            acc = torch.empty_like(pos)
+        self._check(lib().hacc_pm_force(self._h, ctypes.byref(box._c()), ctypes.byref(pm._c()), pos.shape[0],
+                                        _ptr(pos), _ptr(acc), self._stream(stream)), "hacc_pm_force")
+        return acc
+
+    def diagnostics(self, box: Box, split, pos, vel, stream=None):
+        """FP64 (momentum[3], kinetic, potential) as a 5-element float64 CUDA tensor."""
+        import torch
+        _dev_rows(pos, "pos")
+        _dev_rows(vel, "vel")
+        sp = _split_of(split)
+        out = torch.empty(5, dtype=torch.float64, device=pos.device)
+        self._check(lib().hacc_diagnostics(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
+                                           _ptr(pos), _ptr(vel), _ptr(out), self._stream(stream)),
+                    "hacc_diagnostics")
+        return out
+
+    # ---- host-buffer entry points (numpy or pinned CPU tensors) -------------
+    @staticmethod
+    def _host_ptr(a):
+        import numpy as np
+        if isinstance(a, np.ndarray):
+            assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] and a.ndim == 2 and a.shape[1] == 4
+            return ctypes.c_void_p(a.ctypes.data)
+        assert (not a.is_cuda) and a.is_contiguous() and a.dtype.is_floating_point
+        return ctypes.c_void_p(a.data_ptr())
+
+    def sr_force_host(self, box: Box, split, pos, acc, stream=None):
+        sp = _split_of(split)
+        self._check(lib().hacc_sr_force_host(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), len(pos),
+                                             self._host_ptr(pos), self._host_ptr(acc), self._stream(stream)),
+                    "hacc_sr_force_host")
+
+    def subcycle_host(self, box: Box, split, pos, vel, dt: float, n_sub: int, stream=None):
+        sp = _split_of(split)
+        self._check(lib().hacc_subcycle_host(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), len(pos),
+                                             self._host_ptr(pos), self._host_ptr(vel), float(dt), int(n_sub),
+                                             self._stream(stream)), "hacc_subcycle_host")
+
+    def step_host(self, box: Box, split, pm: PM, pos, vel, dt: float, n_c: int, stream=None):
+        sp = _split_of(split)
+        self._check(lib().hacc_step_host(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()),
+                                         ctypes.byref(pm._c()), len(pos), self._host_ptr(pos), self._host_ptr(vel),
+                                         float(dt), int(n_c), self._stream(stream)), "hacc_step_host")

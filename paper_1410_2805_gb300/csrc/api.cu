@@ -1,0 +1,555 @@
+// C-ABI entry points of the hacc library: context, validation, scratch pool
+// and the composition of the binning, pair-force and PM kernels into the
+// calls declared in include/hacc.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "hacc_internal.cuh"
+
+namespace hacc {
+
+thread_local int64_t *tl_launches = nullptr;
+
+hacc_status set_error(hacc_ctx *ctx, hacc_status st, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+hacc_status check_cuda(hacc_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return HACC_OK;
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_error(ctx, e == cudaErrorMemoryAllocation ? HACC_ENOMEM : HACC_ECUDA, msg);
+}
+
+// Grow-only scratch arena (allocated once per size class, reused across calls:
+// the phase-scoped pool of Sec. 2.7 reduced to one region per context).
+hacc_status ensure_scratch(hacc_ctx *ctx, size_t bytes, cudaStream_t stream) {
+    if (bytes <= ctx->scratch.cap) return HACC_OK;
+    size_t want = bytes + bytes / 8;
+    if (ctx->budget && want > ctx->budget) want = bytes;
+    if (ctx->budget && want > ctx->budget) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "scratch of %zu bytes exceeds the context budget of %zu bytes", bytes, ctx->budget);
+        return set_error(ctx, HACC_ENOMEM, msg);
+    }
+    if (ctx->scratch.base) {
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return check_cuda(ctx, e, "cudaStreamSynchronize");
+        cudaFree(ctx->scratch.base);
+        ctx->scratch.base = nullptr;
+        ctx->scratch.cap = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, HACC_ENOMEM, std::string("cudaMalloc of scratch failed: ") + cudaGetErrorString(e));
+    }
+    ctx->scratch.base = static_cast<char *>(p);
+    ctx->scratch.cap = want;
+    return HACC_OK;
+}
+
+int32_t default_nc(double L, double r_cut) {
+    if (!(L > 0) || !(r_cut > 0)) return -1;
+    int64_t nc = (int64_t)std::floor(L / r_cut);
+    if (nc >= 1 && L / (double)nc < r_cut * (1.0 + 1e-6)) --nc;
+    if (nc < 3) return -1;
+    if (nc > 1024) nc = 1024;
+    return (int32_t)nc;
+}
+
+hacc_status make_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geometry *g) {
+    if (!box) return set_error(ctx, HACC_EINVAL, "box is NULL");
+    const double L = box->L;
+    if (!(L > 0) || !std::isfinite(L)) return set_error(ctx, HACC_EINVAL, "box side L must be finite and > 0");
+    if ((double)(float)L != L) return set_error(ctx, HACC_EINVAL, "box side L must be exactly representable in FP32");
+    if (!(r_cut > 0) || !std::isfinite(r_cut)) return set_error(ctx, HACC_EINVAL, "r_cut must be finite and > 0");
+    int nc = box->nc;
+    if (nc == 0) {
+        nc = default_nc(L, r_cut);
+        if (nc < 0) return set_error(ctx, HACC_EDOMAIN, "box holds fewer than 3 chaining-mesh cells of width >= r_cut");
+    }
+    if (nc < 3 || nc > 1024) return set_error(ctx, HACC_EDOMAIN, "nc must be in [3, 1024]");
+    if (L / (double)nc < (double)r_cut)
+        return set_error(ctx, HACC_EDOMAIN, "chaining-mesh cell width L/nc is below r_cut");
+    g->Lf = (float)L;
+    g->Ld = L;
+    g->nc = nc;
+    g->ncell = (int64_t)nc * nc * nc;
+    g->inv_w = (float)((double)nc / L);
+    return HACC_OK;
+}
+
+static double binom(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+hacc_status make_force_consts(hacc_ctx *ctx, const hacc_split *split, const Geometry &g, ForceConsts *fc) {
+    (void)g;
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (!(split->r_cut > 0) || !(split->eps >= 0) || !std::isfinite(split->eps) || !std::isfinite(split->G))
+        return set_error(ctx, HACC_EINVAL, "split needs r_cut > 0, eps >= 0 and a finite G");
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(split->poly[k])) return set_error(ctx, HACC_EINVAL, "split poly must be finite");
+    const double eps = split->eps, rc = split->r_cut;
+    fc->eps = split->eps;
+    fc->T = (float)(rc * rc + eps);
+    fc->G = split->G;
+    // P5(s) with s = t - eps, expanded in powers of t
+    for (int m = 0; m < 6; ++m) {
+        double q = 0.0;
+        for (int k = m; k < 6; ++k) q += split->poly[k] * binom(k, m) * std::pow(-eps, k - m);
+        fc->q[m] = (float)q;
+    }
+    // U(s) = sum_k c_k s^(k+1) / (2(k+1)) = sum_j a_j s^j, j = 1..6; in powers of t
+    double a[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; ++k) a[k + 1] = split->poly[k] / (2.0 * (k + 1));
+    for (int m = 0; m < 7; ++m) {
+        double u = 0.0;
+        for (int j = m; j < 7; ++j) u += a[j] * binom(j, m) * std::pow(-eps, j - m);
+        fc->u[m] = (float)u;
+    }
+    double s = rc * rc, Us = 0.0, sj = s;
+    for (int j = 1; j < 7; ++j) { Us += a[j] * sj; sj *= s; }
+    fc->phi0 = (float)(-1.0 / std::sqrt(s + eps) - Us);
+    return HACC_OK;
+}
+
+}  // namespace hacc
+
+using namespace hacc;
+
+namespace {
+
+// Device staging for the *_host entry points.
+hacc_status ensure_io(hacc_ctx *ctx, size_t bytes, cudaStream_t s) {
+    if (bytes <= ctx->io_cap) return HACC_OK;
+    if (ctx->io_base) {
+        cudaStreamSynchronize(s);
+        cudaFree(ctx->io_base);
+        ctx->io_base = nullptr;
+        ctx->io_cap = 0;
+    }
+    if (cudaMalloc(&ctx->io_base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, HACC_ENOMEM, "cudaMalloc of host-copy staging failed");
+    }
+    ctx->io_cap = bytes;
+    return HACC_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+hacc_status enter(hacc_ctx *ctx) {
+    if (!ctx) return HACC_EINVAL;
+    ctx->last_error.clear();
+    tl_launches = &ctx->launches;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return check_cuda(ctx, e, "cudaSetDevice");
+    return HACC_OK;
+}
+
+#define HACC_TRY(x)                      \
+    do {                                 \
+        hacc_status st__ = (x);          \
+        if (st__ != HACC_OK) return st__; \
+    } while (0)
+#define HACC_CUDA(x, what) HACC_TRY(check_cuda(ctx, (x), what))
+
+// Sorted working set of one box for the force and sub-cycle paths.
+struct Work {
+    float4 *P, *V, *Ps, *Vs;
+    int32_t *ID, *IDs;
+    int *counter;
+    unsigned long long *within;
+    float *phi;
+    double *diag;
+    BinBuffers b;
+};
+
+size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w) {
+    Carver c(base);
+    w->P = c.take<float4>(n);
+    w->Ps = c.take<float4>(n);
+    w->V = dyn ? c.take<float4>(n) : nullptr;
+    w->Vs = dyn ? c.take<float4>(n) : nullptr;
+    w->ID = dyn ? c.take<int32_t>(n) : nullptr;
+    w->IDs = dyn ? c.take<int32_t>(n) : nullptr;
+    w->counter = c.take<int>(1);
+    w->within = c.take<unsigned long long>(1);
+    w->phi = c.take<float>(n);
+    w->diag = c.take<double>(5);
+    carve_bin(c, n, ncell, &w->b);
+    return c.off + 256;
+}
+
+hacc_status prepare_work(hacc_ctx *ctx, int64_t n, const Geometry &g, bool dyn, cudaStream_t s, Work *w) {
+    size_t need = carve_work(nullptr, n, g.ncell, dyn, w);
+    HACC_TRY(ensure_scratch(ctx, need, s));
+    carve_work(ctx->scratch.base, n, g.ncell, dyn, w);
+    return HACC_OK;
+}
+
+hacc_status check_particles(hacc_ctx *ctx, int64_t n, const void *a, const void *b) {
+    if (n < 0) return set_error(ctx, HACC_EINVAL, "n must be >= 0");
+    if (n >= (int64_t)1 << 31) return set_error(ctx, HACC_EINVAL, "n must be below 2^31");
+    if (n > 0 && (!a || !aligned16(a))) return set_error(ctx, HACC_EINVAL, "particle array NULL or not 16-byte aligned");
+    if (n > 0 && b && !aligned16(b)) return set_error(ctx, HACC_EINVAL, "particle array not 16-byte aligned");
+    return HACC_OK;
+}
+
+// The short-range force on sorted positions (w->Ps, cell starts and items in w->b).
+hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, Work *w, int mode,
+                             float4 *out, const int32_t *perm, float4 *vel, float4 *pos_next, float hk, float hd,
+                             unsigned long long *within, cudaStream_t s) {
+    ForceLaunch fl;
+    fl.pos = w->Ps;
+    fl.items = w->b.items;
+    fl.n_items = w->b.n_items;
+    fl.cell_start = w->b.cell_start;
+    fl.work_counter = w->counter;
+    fl.mode = mode;
+    fl.out = out;
+    fl.perm = perm;
+    fl.vel = vel;
+    fl.pos_next = pos_next;
+    fl.h_kick = hk;
+    fl.h_drift = hd;
+    fl.phi_out = w->phi;
+    fl.within = within;
+    if (ctx->counting && mode != kModePotential && !within) {
+        HACC_CUDA(candidate_count(g, w->b.cell_start, ctx->d_pairs, s), "candidate count");
+        fl.within = ctx->d_pairs + 1;
+    }
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->timing && mode != kModePotential) {
+        if (ctx->ev_free.empty()) {
+            cudaEvent_t a, b;
+            HACC_CUDA(cudaEventCreate(&a), "cudaEventCreate");
+            HACC_CUDA(cudaEventCreate(&b), "cudaEventCreate");
+            ctx->ev_free.emplace_back(a, b);
+        }
+        ev = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        HACC_CUDA(cudaEventRecord(ev.first, s), "cudaEventRecord");
+    }
+    HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch");
+    if (mode != kModePotential) ctx->force_launches++;
+    if (ev.first) {
+        HACC_CUDA(cudaEventRecord(ev.second, s), "cudaEventRecord");
+        ctx->ev_used.push_back(ev);
+    }
+    return HACC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hacc_status hacc_ctx_create(hacc_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) return HACC_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HACC_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return HACC_ECUDA;
+    hacc_ctx *ctx = new hacc_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_flags, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_flags, 0, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_pairs, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return HACC_ENOMEM;
+    }
+    *out = ctx;
+    return HACC_OK;
+}
+
+void hacc_ctx_destroy(hacc_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    pm_destroy(ctx);
+    if (ctx->scratch.base) cudaFree(ctx->scratch.base);
+    if (ctx->io_base) cudaFree(ctx->io_base);
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+    for (auto &e : ctx->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    for (auto &e : ctx->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    if (tl_launches == &ctx->launches) tl_launches = nullptr;
+    delete ctx;
+}
+
+const char *hacc_last_error(const hacc_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+size_t hacc_ctx_scratch_bytes(const hacc_ctx *ctx) {
+    if (!ctx) return 0;
+    return ctx->scratch.cap + ctx->io_cap;
+}
+
+hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    HACC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    HACC_CUDA(cudaGetLastError(), "pending CUDA error");
+    int flags[4] = {0, 0, 0, 0};
+    HACC_CUDA(cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost), "reading device flags");
+    HACC_CUDA(cudaMemset(ctx->d_flags, 0, sizeof flags), "clearing device flags");
+    if (flags[0] & kFlagTimeout) return set_error(ctx, HACC_ETIMEOUT, "a device-side wait gave up");
+    if (flags[0] & kFlagDomain)
+        return set_error(ctx, HACC_EDOMAIN, "a coordinate was outside [-L, 2L) or not finite");
+    return HACC_OK;
+}
+
+int32_t hacc_mesh_cells(double L, float r_cut) { return default_nc(L, r_cut); }
+
+hacc_status hacc_stats_enable(hacc_ctx *ctx, int timing, int counting) {
+    HACC_TRY(enter(ctx));
+    ctx->timing = timing != 0;
+    ctx->counting = counting != 0;
+    return HACC_OK;
+}
+
+hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset) {
+    HACC_TRY(enter(ctx));
+    if (!out) return set_error(ctx, HACC_EINVAL, "out is NULL");
+    HACC_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    for (auto &e : ctx->ev_used) {
+        float ms = 0.f;
+        HACC_CUDA(cudaEventElapsedTime(&ms, e.first, e.second), "cudaEventElapsedTime");
+        ctx->force_ms += ms;
+        ctx->ev_free.push_back(e);
+    }
+    ctx->ev_used.clear();
+    unsigned long long pairs[2] = {0, 0};
+    HACC_CUDA(cudaMemcpy(pairs, ctx->d_pairs, sizeof pairs, cudaMemcpyDeviceToHost), "reading pair counts");
+    out->kernel_launches = ctx->launches;
+    out->force_launches = ctx->force_launches;
+    out->force_ms = ctx->force_ms;
+    out->candidate_pairs = pairs[0];
+    out->within_pairs = pairs[1];
+    if (reset) {
+        ctx->launches = 0;
+        ctx->force_launches = 0;
+        ctx->force_ms = 0.0;
+        HACC_CUDA(cudaMemset(ctx->d_pairs, 0, sizeof pairs), "clearing pair counts");
+    }
+    return HACC_OK;
+}
+
+hacc_status hacc_bin(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, float *pos_m, int32_t *cell_id,
+                     int32_t *cell_start, int32_t *perm, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, r_cut, &g));
+    HACC_TRY(check_particles(ctx, n, pos_m, nullptr));
+    if (!cell_start || (n > 0 && (!cell_id || !perm))) return set_error(ctx, HACC_EINVAL, "output array is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // scratch: everything of BinBuffers except the caller-owned outputs
+    auto carve = [&](char *base, BinBuffers *b) {
+        Carver c(base);
+        carve_bin(c, n, g.ncell, b);
+        return c.off + 256;
+    };
+    BinBuffers b;
+    HACC_TRY(ensure_scratch(ctx, carve(nullptr, &b), s));
+    carve(ctx->scratch.base, &b);
+    b.key = cell_id;
+    b.cell_start = cell_start;
+    b.perm = perm;
+    float4 *p = reinterpret_cast<float4 *>(pos_m);
+    HACC_CUDA(bin_build(g, n, p, nullptr, 0.0f, p, b, ctx->d_flags, false, s), "binning");
+    return HACC_OK;
+}
+
+hacc_status hacc_sr_force(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                          const float *pos_m, float *acc, uint64_t *pair_counts, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, pos_m, acc));
+    if (n > 0 && !acc) return set_error(ctx, HACC_EINVAL, "acc is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
+    const float4 *src = reinterpret_cast<const float4 *>(pos_m);
+    HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s), "binning");
+    HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
+    unsigned long long *within = nullptr;
+    if (pair_counts) {
+        unsigned long long *pc = reinterpret_cast<unsigned long long *>(pair_counts);
+        HACC_CUDA(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), s), "clearing pair counts");
+        HACC_CUDA(candidate_count(g, w.b.cell_start, pc, s), "candidate count");
+        within = pc + 1;
+    }
+    if (n > 0)
+        HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModeForce, reinterpret_cast<float4 *>(acc), w.b.perm, nullptr,
+                                  nullptr, 0.f, 0.f, within, s));
+    return HACC_OK;
+}
+
+hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
+                          float *vel, double dt, int32_t n_sub, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (n_sub < 1) return set_error(ctx, HACC_EINVAL, "n_sub must be >= 1");
+    if (!std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, pos_m, vel));
+    if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
+    if (n == 0) return HACC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
+    const float h = (float)(dt / n_sub);
+    const float h2 = (float)(0.5 * dt / n_sub);
+    float4 *pos_in = reinterpret_cast<float4 *>(pos_m);
+    float4 *vel_in = reinterpret_cast<float4 *>(vel);
+    for (int k = 0; k < n_sub; ++k) {
+        const bool first = k == 0, last = k == n_sub - 1;
+        // stream h/2 (first sub-cycle only; later ones were fused into the
+        // previous kick) + wrap + rebin
+        HACC_CUDA(bin_build(g, n, first ? pos_in : w.P, first ? vel_in : nullptr, h2, w.P, w.b, ctx->d_flags, true,
+                            s),
+                  "binning");
+        HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, first ? vel_in : w.V, w.Vs, first ? nullptr : w.ID, w.IDs,
+                                s),
+                  "gather");
+        // kick h, then stream h (fused halves) or h/2 (closing the last sub-cycle);
+        // positions of this sub-cycle's sorted order go to w.P
+        HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModeKickDrift, nullptr, nullptr, w.Vs, w.P, h, last ? h2 : h,
+                                  nullptr, s));
+        std::swap(w.V, w.Vs);
+        std::swap(w.ID, w.IDs);
+    }
+    // wrap the final positions and return rows to input order
+    HACC_CUDA(scatter_rows(n, w.ID, w.P, pos_in, w.V, vel_in, g.Lf, ctx->d_flags, s), "scatter");
+    return HACC_OK;
+}
+
+hacc_status hacc_diagnostics(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                             const float *pos_m, const float *vel, double *out, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split || !out) return set_error(ctx, HACC_EINVAL, "split or out is NULL");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, pos_m, vel));
+    if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
+    if (n == 0) {
+        HACC_CUDA(cudaMemsetAsync(out, 0, 5 * sizeof(double), s), "clearing diagnostics");
+        return HACC_OK;
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(pos_m);
+    HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s), "binning");
+    HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, reinterpret_cast<const float4 *>(vel), w.Vs, nullptr, nullptr, s),
+              "gather");
+    HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModePotential, nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr,
+                              s));
+    HACC_CUDA(diag_reduce(n, w.Ps, w.Vs, w.phi, out, s), "diagnostics");
+    return HACC_OK;
+}
+
+hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, int64_t n, const float *pos_m,
+                          float *acc, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    HACC_TRY(check_particles(ctx, n, pos_m, acc));
+    if (n > 0 && !acc) return set_error(ctx, HACC_EINVAL, "acc is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return pm_accel(ctx, box, pm, n, reinterpret_cast<const float4 *>(pos_m), reinterpret_cast<float4 *>(acc),
+                    nullptr, 0.0f, s);
+}
+
+hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm, int64_t n,
+                      float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (n_c < 1) return set_error(ctx, HACC_EINVAL, "n_c must be >= 1");
+    HACC_TRY(check_particles(ctx, n, pos_m, vel));
+    if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float4 *p = reinterpret_cast<float4 *>(pos_m);
+    float4 *v = reinterpret_cast<float4 *>(vel);
+    // M_lr(dt/2): kick by the long-range force
+    HACC_TRY(pm_accel(ctx, box, pm, n, p, nullptr, v, (float)(0.5 * dt), s));
+    HACC_TRY(hacc_subcycle(ctx, box, split, n, pos_m, vel, dt, n_c, stream));
+    HACC_TRY(pm_accel(ctx, box, pm, n, p, nullptr, v, (float)(0.5 * dt), s));
+    return HACC_OK;
+}
+
+hacc_status hacc_sr_force_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                               const float *pos_m, float *acc, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (n < 0 || (n > 0 && (!pos_m || !acc))) return set_error(ctx, HACC_EINVAL, "bad host arrays");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t bytes = (size_t)n * 16;
+    HACC_TRY(ensure_io(ctx, 2 * bytes + 512, s));
+    char *base = static_cast<char *>(ctx->io_base);
+    float *dp = reinterpret_cast<float *>(base);
+    float *da = reinterpret_cast<float *>(base + ((bytes + 255) & ~size_t(255)));
+    HACC_CUDA(cudaMemcpyAsync(dp, pos_m, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
+    HACC_TRY(hacc_sr_force(ctx, box, split, n, dp, da, nullptr, stream));
+    HACC_CUDA(cudaMemcpyAsync(acc, da, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    return hacc_ctx_sync(ctx, stream);
+}
+
+hacc_status hacc_subcycle_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
+                               float *vel, double dt, int32_t n_sub, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (n < 0 || (n > 0 && (!pos_m || !vel))) return set_error(ctx, HACC_EINVAL, "bad host arrays");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t bytes = (size_t)n * 16;
+    HACC_TRY(ensure_io(ctx, 2 * bytes + 512, s));
+    char *base = static_cast<char *>(ctx->io_base);
+    float *dp = reinterpret_cast<float *>(base);
+    float *dv = reinterpret_cast<float *>(base + ((bytes + 255) & ~size_t(255)));
+    HACC_CUDA(cudaMemcpyAsync(dp, pos_m, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
+    HACC_CUDA(cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
+    HACC_TRY(hacc_subcycle(ctx, box, split, n, dp, dv, dt, n_sub, stream));
+    HACC_CUDA(cudaMemcpyAsync(pos_m, dp, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    HACC_CUDA(cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    return hacc_ctx_sync(ctx, stream);
+}
+
+hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
+                           int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (n < 0 || (n > 0 && (!pos_m || !vel))) return set_error(ctx, HACC_EINVAL, "bad host arrays");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t bytes = (size_t)n * 16;
+    HACC_TRY(ensure_io(ctx, 2 * bytes + 512, s));
+    char *base = static_cast<char *>(ctx->io_base);
+    float *dp = reinterpret_cast<float *>(base);
+    float *dv = reinterpret_cast<float *>(base + ((bytes + 255) & ~size_t(255)));
+    HACC_CUDA(cudaMemcpyAsync(dp, pos_m, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
+    HACC_CUDA(cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
+    HACC_TRY(hacc_step(ctx, box, split, pm, n, dp, dv, dt, n_c, stream));
+    HACC_CUDA(cudaMemcpyAsync(pos_m, dp, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    HACC_CUDA(cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    return hacc_ctx_sync(ctx, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,388 @@
+// Chaining-mesh build on the GPU (Sec. 2.4 / Sec. 3.3: Hockney's chaining
+// mesh controls the number of particle-particle interactions; Sec. 2.7: the
+// particle arrays are reordered out of place through a permutation).
+//
+// Pipeline (all HBM-bound, one pass each):
+//   k_key     wrap (after an optional drift), exact cell id, per-cell count
+//             and arrival slot (atomic)                    read 16-32 B, write 24 B
+//   scan      exclusive scan of (count, work-item count) packed in 64 bits
+//   k_place   perm_tmp[start[c] + slot] = i                 read 12 B, write 4 B
+//   k_order   within each cell, sort perm by input row (stable order)
+//   k_items   cell starts and force work items
+//   gather    sorted copies of positions / velocities / ids
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hacc_internal.cuh"
+
+namespace hacc {
+namespace {
+
+constexpr int kBlock = 256;
+
+// Wrap one FP32 coordinate into [0, L): x<0 -> x+L, x>=L -> x-L, a sum that
+// rounds to L becomes 0.  Returns false (and leaves 0) outside [-L, 2L).
+__device__ __forceinline__ bool wrap1(float &x, float Lf) {
+    float v = x;
+    if (!(v >= -Lf && v < 2.0f * Lf)) {
+        x = 0.0f;
+        return false;
+    }
+    if (v < 0.0f) v = __fadd_rn(v, Lf);
+    else if (v >= Lf) v = __fsub_rn(v, Lf);
+    if (v >= Lf) v = 0.0f;
+    x = v;
+    return true;
+}
+
+// Largest k with k*L <= x*nc, for x in [0, L).  The FP32 product is within
+// 2e-4 of the exact quotient for nc <= 1024, so away from a cell face its
+// floor is exact; near a face the decision is made with exact FP64 products
+// (x has 24 significant bits, nc < 2^11, L is an FP32 value).
+__device__ __forceinline__ int cell1(float x, float inv_w, double Ld, int nc) {
+    float f = x * inv_w;
+    int k = (int)f;
+    k = k < 0 ? 0 : (k > nc - 1 ? nc - 1 : k);
+    float fr = f - (float)k;
+    if (fr < 1e-3f || fr > 0.999f) {
+        double xn = (double)x * (double)nc;
+        if (k > 0 && (double)k * Ld > xn) --k;
+        else if (k < nc - 1 && (double)(k + 1) * Ld <= xn) ++k;
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restrict__ src,
+                                                 const float4 *__restrict__ vel, float drift,
+                                                 float4 *dst, float Lf, float inv_w, double Ld, int nc,
+                                                 int32_t *__restrict__ key, int32_t *__restrict__ rank,
+                                                 uint32_t *__restrict__ count, int *flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = src[i];
+    if (vel) {
+        float4 v = vel[i];
+        p.x = __fmaf_rn(drift, v.x, p.x);
+        p.y = __fmaf_rn(drift, v.y, p.y);
+        p.z = __fmaf_rn(drift, v.z, p.z);
+    }
+    bool ok = wrap1(p.x, Lf);
+    ok &= wrap1(p.y, Lf);
+    ok &= wrap1(p.z, Lf);
+    if (!ok) atomicOr(flags, kFlagDomain);
+    int cx = cell1(p.x, inv_w, Ld, nc), cy = cell1(p.y, inv_w, Ld, nc), cz = cell1(p.z, inv_w, Ld, nc);
+    int32_t c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
+    dst[i] = p;
+    key[i] = c;
+    rank[i] = (int32_t)atomicAdd(&count[c], 1u);
+}
+
+__device__ __forceinline__ uint32_t items_of(uint32_t cnt) {
+    return cnt == 0 ? 0u : (cnt <= (uint32_t)kItemMax ? 1u : (cnt + kItemMax - 1) / kItemMax);
+}
+
+__global__ void __launch_bounds__(kBlock) k_pack(int64_t ncell, const uint32_t *__restrict__ count,
+                                                  unsigned long long *__restrict__ packed) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    uint32_t k = count[c];
+    packed[c] = (unsigned long long)k | ((unsigned long long)items_of(k) << 32);
+}
+
+// ---- exclusive scan of uint64, reduce-then-scan, 2048 values per block ----
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;
+
+__device__ __forceinline__ unsigned long long block_exclusive(unsigned long long v, unsigned long long *total) {
+    __shared__ unsigned long long warp_sums[kBlock / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = lane < kBlock / 32 ? warp_sums[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kBlock / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    unsigned long long before = w ? warp_sums[w - 1] : 0ull;
+    if (total) *total = warp_sums[kBlock / 32 - 1];
+    unsigned long long r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_reduce(int64_t len, const unsigned long long *__restrict__ in,
+                                                         unsigned long long *__restrict__ sums) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < len) s += in[base + j];
+    unsigned long long total;
+    block_exclusive(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_down(int64_t len, unsigned long long *data,
+                                                       const unsigned long long *__restrict__ offsets) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned long long v[kScanItems];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = base + j < len ? data[base + j] : 0ull;
+        s += v[j];
+    }
+    unsigned long long run = block_exclusive(s, nullptr) + (offsets ? offsets[blockIdx.x] : 0ull);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < len) data[base + j] = run;
+        run += v[j];
+    }
+}
+
+// Exclusive scan of data[0..len) in place; tmp holds the per-level block sums.
+cudaError_t scan_exclusive(unsigned long long *data, int64_t len, unsigned long long *tmp, cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    int64_t nb = (len + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        k_scan_down<<<1, kBlock, 0, s>>>(len, data, nullptr);
+        note_launch();
+        return cudaGetLastError();
+    }
+    unsigned long long *sums = tmp;
+    k_scan_reduce<<<(unsigned)nb, kBlock, 0, s>>>(len, data, sums);
+    note_launch();
+    cudaError_t e = scan_exclusive(sums, nb, tmp + nb, s);
+    if (e != cudaSuccess) return e;
+    k_scan_down<<<(unsigned)nb, kBlock, 0, s>>>(len, data, sums);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock) k_place(int64_t n, const int32_t *__restrict__ key,
+                                                   const int32_t *__restrict__ rank,
+                                                   const unsigned long long *__restrict__ packed,
+                                                   int32_t *__restrict__ perm_tmp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = key[i];
+    uint32_t start = (uint32_t)(packed[c] & 0xffffffffull);
+    perm_tmp[start + (uint32_t)rank[i]] = (int32_t)i;
+}
+
+// One warp per cell: the arrival order from the atomics is arbitrary, so each
+// element's final slot is the number of smaller input rows in its cell (the
+// rows are distinct), which gives ascending input row within the cell.
+__global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t *__restrict__ count,
+                                                   const unsigned long long *__restrict__ packed,
+                                                   const int32_t *__restrict__ perm_tmp,
+                                                   int32_t *__restrict__ perm) {
+    int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (c >= ncell) return;
+    uint32_t cnt = count[c];
+    if (cnt == 0) return;
+    uint32_t s = (uint32_t)(packed[c] & 0xffffffffull);
+    const int32_t *seg = perm_tmp + s;
+    if (cnt <= 32) {
+        int32_t v = lane < (int)cnt ? seg[lane] : 0x7fffffff;
+        int r = 0;
+        for (int q = 0; q < (int)cnt; ++q) {
+            int32_t u = __shfl_sync(0xffffffffu, v, q);
+            r += (u < v);
+        }
+        if (lane < (int)cnt) perm[s + r] = v;
+        return;
+    }
+    for (uint32_t e = lane; e < cnt; e += 32) {
+        int32_t v = seg[e];
+        uint32_t r = 0;
+        for (uint32_t q = 0; q < cnt; ++q) r += (seg[q] < v);
+        perm[s + r] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, const uint32_t *__restrict__ count,
+                                                   const unsigned long long *__restrict__ packed,
+                                                   int32_t *__restrict__ cell_start, int4 *__restrict__ items,
+                                                   int32_t *__restrict__ n_items, int make_items) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) {
+        cell_start[ncell] = (int32_t)n;
+        if (make_items) {
+            unsigned long long last = packed[ncell - 1];
+            *n_items = (int32_t)((last >> 32) + items_of(count[ncell - 1]));
+        }
+    }
+    if (c >= ncell) return;
+    unsigned long long p = packed[c];
+    uint32_t s = (uint32_t)(p & 0xffffffffull);
+    cell_start[c] = (int32_t)s;
+    if (!make_items) return;
+    uint32_t cnt = count[c];
+    uint32_t it = (uint32_t)(p >> 32);
+    if (cnt == 0) return;
+    if (cnt <= (uint32_t)kItemMax) {
+        items[it] = make_int4((int)c, (int)s, (int)cnt, (int)((cnt + 31) / 32));
+        return;
+    }
+    uint32_t m = items_of(cnt);
+    for (uint32_t q = 0; q < m; ++q) {
+        uint32_t ni = cnt - q * kItemMax;
+        ni = ni > (uint32_t)kItemMax ? (uint32_t)kItemMax : ni;
+        items[it + q] = make_int4((int)c, (int)(s + q * kItemMax), (int)ni, 4);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__restrict__ perm,
+                                                    const float4 *__restrict__ p_in, float4 *__restrict__ p_out,
+                                                    const float4 *__restrict__ v_in, float4 *__restrict__ v_out,
+                                                    const int32_t *__restrict__ id_in, int32_t *__restrict__ id_out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int32_t i = perm[k];
+    p_out[k] = p_in[i];
+    if (v_out) v_out[k] = v_in[i];
+    if (id_out) id_out[k] = id_in ? id_in[i] : i;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scatter(int64_t n, const int32_t *__restrict__ id,
+                                                     const float4 *__restrict__ p_in, float4 *__restrict__ p_out,
+                                                     const float4 *__restrict__ v_in, float4 *__restrict__ v_out,
+                                                     float Lf, int *flags) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int32_t i = id[k];
+    if (p_out) {
+        float4 p = p_in[k];
+        bool ok = wrap1(p.x, Lf);
+        ok &= wrap1(p.y, Lf);
+        ok &= wrap1(p.z, Lf);
+        if (!ok) atomicOr(flags, kFlagDomain);
+        p_out[i] = p;
+    }
+    if (v_out) {
+        float4 v = v_in[k];
+        v.w = 0.0f;
+        v_out[i] = v;
+    }
+}
+
+// Candidate pairs of the 27-cell chaining mesh: sum_c n_c * sum_{nbr} n_nbr.
+__global__ void __launch_bounds__(kBlock) k_candidates(int nc, const int32_t *__restrict__ cell_start,
+                                                        unsigned long long *out) {
+    int64_t ncell = (int64_t)nc * nc * nc;
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (c < ncell) {
+        int ni = cell_start[c + 1] - cell_start[c];
+        if (ni) {
+            int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+            unsigned long long nb = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int jx = (cx + dx + nc) % nc, jy = (cy + dy + nc) % nc, jz = (cz + dz + nc) % nc;
+                        int64_t j = ((int64_t)jz * nc + jy) * nc + jx;
+                        nb += (unsigned long long)(cell_start[j + 1] - cell_start[j]);
+                    }
+            v = (unsigned long long)ni * nb;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace
+
+size_t scan_tmp_elems(int64_t len) {
+    size_t total = 0;
+    int64_t nb = (len + kScanTile - 1) / kScanTile;
+    while (nb > 1) {
+        total += (size_t)nb;
+        nb = (nb + kScanTile - 1) / kScanTile;
+    }
+    return total + 1;
+}
+
+int64_t max_items(int64_t n, int64_t ncell) { return ncell + n / kItemMax + 1; }
+
+void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
+    b->key = c.take<int32_t>(n);
+    b->rank = c.take<int32_t>(n);
+    b->count = c.take<uint32_t>(ncell);
+    b->packed = c.take<unsigned long long>(ncell);
+    b->scan_tmp = c.take<unsigned long long>(scan_tmp_elems(ncell));
+    b->cell_start = c.take<int32_t>(ncell + 1);
+    b->item_start = nullptr;
+    b->perm_tmp = c.take<int32_t>(n);
+    b->perm = c.take<int32_t>(n);
+    b->items = c.take<int4>(max_items(n, ncell));
+    b->n_items = c.take<int32_t>(1);
+}
+
+cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
+                      float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_key<<<blocks_for(n), kBlock, 0, s>>>(n, src, vel, drift, dst, g.Lf, g.inv_w, g.Ld, g.nc, b.key,
+                                               b.rank, b.count, d_flags);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_pack<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, b.count, b.packed);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(b.packed, g.ncell, b.scan_tmp, s)) != cudaSuccess) return e;
+    if (n > 0) {
+        k_place<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, b.rank, b.packed, b.perm_tmp);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_order<<<blocks_for(g.ncell * 32), kBlock, 0, s>>>(g.ncell, b.count, b.packed, b.perm_tmp, b.perm);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_items<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, n, b.count, b.packed, b.cell_start, b.items,
+                                                   b.n_items, make_items ? 1 : 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, const float4 *v_in,
+                          float4 *v_out, const int32_t *id_in, int32_t *id_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_gather<<<blocks_for(n), kBlock, 0, s>>>(n, perm, p_in, p_out, v_in, v_out, id_in, id_out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_rows(int64_t n, const int32_t *id, const float4 *p_in, float4 *p_out, const float4 *v_in,
+                         float4 *v_out, float Lf, int *d_flags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_scatter<<<blocks_for(n), kBlock, 0, s>>>(n, id, p_in, p_out, v_in, v_out, Lf, d_flags);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsigned long long *out, cudaStream_t s) {
+    k_candidates<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.nc, cell_start, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hacc

@@ -1,0 +1,177 @@
+// Internal declarations of the hacc library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/hacc.h"
+
+namespace hacc {
+
+// Device-side status flags (one int each, OR-ed by kernels).
+enum DeviceFlag : int {
+    kFlagDomain = 1,   // a coordinate outside [-L, 2L) or not finite
+    kFlagTimeout = 2,  // a bounded device wait gave up
+};
+
+// Chunking of a chaining-mesh cell into force work items: a cell of n
+// particles is one item of K = ceil(n/32) particles per lane when n <= 128,
+// else ceil(n/128) items of up to 128 particles (K = 4).
+constexpr int kItemMax = 128;
+
+struct Scratch {
+    char *base = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace hacc
+
+struct hacc_ctx {
+    int device = 0;
+    size_t budget = 0;         // 0 = unbounded
+    int num_sms = 0;
+    hacc::Scratch scratch;
+    int *d_flags = nullptr;    // device status word
+    std::string last_error;
+    hacc_status pending = HACC_OK;
+    // device staging of the *_host entry points (apart from the scratch arena,
+    // so that the device entry points they call may grow the arena)
+    void *io_base = nullptr;
+    size_t io_cap = 0;
+    // cuFFT state for the PM stage (owned by pm.cu)
+    void *pm_state = nullptr;
+    // statistics (hacc_stats_*)
+    bool timing = false, counting = false;
+    int64_t launches = 0, force_launches = 0;
+    double force_ms = 0.0;
+    unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+};
+
+namespace hacc {
+
+// Bump allocator over a scratch region; with base == nullptr it only sizes.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(char *b) : base(b) {}
+    template <class T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * (count ? count : 1);
+        return p;
+    }
+};
+
+// Kernel launches of the calling API function are counted into the context
+// that entered it (set per call; the library is not re-entrant per context).
+extern thread_local int64_t *tl_launches;
+inline void note_launch(int k = 1) {
+    if (tl_launches) *tl_launches += k;
+}
+
+hacc_status set_error(hacc_ctx *ctx, hacc_status st, const std::string &msg);
+hacc_status check_cuda(hacc_ctx *ctx, cudaError_t e, const char *what);
+hacc_status ensure_scratch(hacc_ctx *ctx, size_t bytes, cudaStream_t stream);
+
+// Validated geometry of one box.
+struct Geometry {
+    float Lf;        // box side (FP32 value)
+    double Ld;       // same value in FP64
+    int nc;          // chaining-mesh cells per side
+    int64_t ncell;   // nc^3
+    float inv_w;     // fl(nc / L), first guess of the cell index
+};
+
+hacc_status make_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geometry *g);
+
+// Force constants in the form the kernel evaluates.
+struct ForceConsts {
+    float T;        // fl(r_cut^2 + eps): cutoff test on t = s + eps
+    float eps;
+    float q[6];     // P5(t - eps) = sum_k q[k] t^k
+    float G;
+    float u[7];     // potential: sum_k c_k (t-eps)^(k+1) / (2(k+1)) = sum_k u[k] t^k
+    float phi0;     // phi(r_cut^2) before the shift
+};
+
+hacc_status make_force_consts(hacc_ctx *ctx, const hacc_split *split, const Geometry &g, ForceConsts *fc);
+
+// ---- binning (bin.cu) ----------------------------------------------------
+struct BinBuffers {
+    int32_t *key;          // [n]
+    int32_t *rank;         // [n]
+    uint32_t *count;       // [ncell]
+    unsigned long long *packed;  // [ncell] scan workspace
+    unsigned long long *scan_tmp;
+    int32_t *cell_start;   // [ncell + 1]
+    int32_t *item_start;   // [ncell + 1]
+    int32_t *perm_tmp;     // [n]
+    int32_t *perm;         // [n]
+    int4 *items;           // [max_items]
+    int32_t *n_items;      // [1] device
+};
+
+size_t scan_tmp_elems(int64_t len);
+int64_t max_items(int64_t n, int64_t ncell);
+void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b);
+
+// Wrap (optionally after a drift x += d v) src into dst and compute keys,
+// counts, stable permutation, cell starts and force work items.
+// vel may be null (no drift).  dst may equal src.
+cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
+                      float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s);
+
+// Gather rows into sorted order: out[k] = in[perm[k]] for float4, int ids.
+cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out,
+                          const float4 *v_in, float4 *v_out, const int32_t *id_in, int32_t *id_out,
+                          cudaStream_t s);
+
+// Scatter rows back to input order: out[id[k]] = in[k]; positions are
+// wrapped into [0, L) on the way (flagging coordinates outside [-L, 2L)).
+cudaError_t scatter_rows(int64_t n, const int32_t *id, const float4 *p_in, float4 *p_out,
+                         const float4 *v_in, float4 *v_out, float Lf, int *d_flags, cudaStream_t s);
+
+cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsigned long long *out,
+                            cudaStream_t s);
+
+// ---- pair force (sr_force.cu) -------------------------------------------
+enum ForceMode : int { kModeForce = 0, kModeKickDrift = 1, kModePotential = 2 };
+
+struct ForceLaunch {
+    const float4 *pos;          // sorted, wrapped
+    const int4 *items;
+    const int32_t *n_items;     // device count
+    const int32_t *cell_start;
+    int *work_counter;          // zeroed before launch
+    int mode;
+    // kModeForce: out[perm[i]] (perm null: out[i])
+    float4 *out;
+    const int32_t *perm;
+    // kModeKickDrift
+    float4 *vel;                // sorted, updated in place
+    float4 *pos_next;           // sorted order of this sub-cycle
+    float h_kick, h_drift;
+    // kModePotential: phi_out[i] = G m_i/2 sum_j m_j phi(s_ij) (sorted order)
+    float *phi_out;
+    unsigned long long *within; // non-null: count pairs inside the cutoff
+};
+
+cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
+                            cudaStream_t s);
+
+// FP64 sums: out[0..2] = sum m v, out[3] = sum m v^2 / 2, out[4] = sum phi.
+cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const float *phi, double *out,
+                        cudaStream_t s);
+
+// ---- PM (pm.cu) ------------------------------------------------------------
+hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, int64_t n, const float4 *pos,
+                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s);
+void pm_destroy(hacc_ctx *ctx);
+
+}  // namespace hacc

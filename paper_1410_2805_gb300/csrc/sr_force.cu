@@ -1,0 +1,353 @@
+// Short-range pair force over the chaining mesh (Sec. 3.1, Eq. (force);
+// Sec. 3.3: P3M with a chaining mesh on accelerators).
+//
+// For every particle i of a cell, the force from the particles of the 27
+// cells around it (periodic):
+//     a_i = G sum_j m_j r_ij f_SR(s),  f_SR(s) = (s+eps)^(-3/2) - P5(s),
+// cut at s < r_cut^2 with a select instead of a branch (the paper folds the
+// cutoff test into the force evaluation the same way, with fsel).
+//
+// GPU mapping.  Work item = up to 128 particles of one cell (one warp; K of
+// them per lane, K = 1..4 by cell occupancy).  Because cells are numbered
+// x-fastest, the three cells (ix-1, ix, ix+1) of each of the 9 (dy, dz) rows
+// are one contiguous run of the cell-sorted particle array, so an item
+// streams 9 runs (a second run when the row wraps in x).  Each run is staged
+// 32 particles at a time into a per-warp shared-memory tile with coalesced
+// 16-byte loads; every lane then reads each j with one broadcast 16-byte
+// shared load and evaluates it against its K particles, accumulating in FP32
+// registers.  Work items are taken from an atomic counter so that clustered
+// cells do not leave SMs idle.
+//
+// Periodic images without rounding error: for a neighbour row that wraps on
+// the low side (cell -1 -> nc-1), the staged j coordinates get -L (they lie in
+// [2L/3, L), so x - L is exact); for a row that wraps on the high side
+// (cell nc -> 0), the i coordinates get -L instead (same argument).  Either
+// way r_ij = x_j' - x_i' carries only the rounding of one subtraction.
+//
+// Per candidate pair (FP32): 3 FADD (r), 3 FFMA (t = s + eps), 1 MUFU rsqrt,
+// 2 FMUL (t^-3/2), 5 FFMA (P5 in t), 1 FADD, 1 FMUL (mass), compare + select
+// (cutoff), 3 FFMA (accumulate); P5 is re-expanded in t = s + eps on the
+// host, and the cutoff test is t < fl(r_cut^2 + eps).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hacc_internal.cuh"
+
+namespace hacc {
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kThreads = kWarps * 32;
+
+struct KParams {
+    const float4 *__restrict__ pos;
+    const int4 *__restrict__ items;
+    const int32_t *__restrict__ n_items;
+    const int32_t *__restrict__ cell_start;
+    int *work_counter;
+    int nc;
+    float L;
+    float T, eps, G;
+    float q0, q1, q2, q3, q4, q5;
+    float u0, u1, u2, u3, u4, u5, u6, phi0;
+    int mode;
+    float4 *out;
+    const int32_t *__restrict__ perm;
+    float4 *vel;
+    float4 *pos_next;
+    float h_kick, h_drift;
+    float *phi_out;
+    unsigned long long *within;
+};
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Accumulate the interaction of one staged j (already image-shifted) with
+// the K i-particles of this lane.
+template <int K, bool COUNT, bool POT, bool EPS0>
+__device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, int iself, const float (&xi)[K],
+                                         const float (&yi)[K], const float (&zi)[K], float (&ax)[K],
+                                         float (&ay)[K], float (&az)[K], unsigned &cnt) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float dx = pj.x - xi[k];
+        float dy = pj.y - yi[k];
+        float dz = pj.z - zi[k];
+        float t = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, P.eps)));
+        float r = rsqrt_approx(t);
+        const bool in = t < P.T;
+        if (POT) {
+            // phi(s) = -(t)^(-1/2) - U(t) - phi0, U in t = s + eps
+            float u = __fmaf_rn(P.u6, t, P.u5);
+            u = __fmaf_rn(u, t, P.u4);
+            u = __fmaf_rn(u, t, P.u3);
+            u = __fmaf_rn(u, t, P.u2);
+            u = __fmaf_rn(u, t, P.u1);
+            u = __fmaf_rn(u, t, P.u0);
+            float ph = -r - u - P.phi0;
+            const bool self = jidx == iself + 32 * k;       // i's own row (sorted index)
+            ax[k] += (in && !self) ? ph * pj.w : 0.0f;
+        } else {
+            float r3 = r * r * r;
+            float q = __fmaf_rn(P.q5, t, P.q4);
+            q = __fmaf_rn(q, t, P.q3);
+            q = __fmaf_rn(q, t, P.q2);
+            q = __fmaf_rn(q, t, P.q1);
+            q = __fmaf_rn(q, t, P.q0);
+            float fm = (r3 - q) * pj.w;
+            // with eps = 0 a pair at zero separation (i itself) would give inf * 0
+            const bool use = EPS0 ? (in && t > 0.0f) : in;
+            float fs = use ? fm : 0.0f;
+            ax[k] = __fmaf_rn(fs, dx, ax[k]);
+            ay[k] = __fmaf_rn(fs, dy, ay[k]);
+            az[k] = __fmaf_rn(fs, dz, az[k]);
+        }
+        if (COUNT) cnt += (in && jidx != iself + 32 * k) ? 1u : 0u;   // j != i
+    }
+}
+
+// Stream one run [ja, jb) of consecutive sorted particles through the warp's
+// shared tile.  (sx, sy, sz): image shift added to the staged j coordinates;
+// (tx, ty, tz): image shift added to this lane's i coordinates.
+template <int K, bool COUNT, bool POT, bool EPS0>
+__device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
+                                            float ty, float tz, int iself, const float (&xi)[K],
+                                            const float (&yi)[K], const float (&zi)[K], float (&ax)[K],
+                                            float (&ay)[K], float (&az)[K], unsigned &cnt, float4 *buf,
+                                            int lane) {
+    const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
+    const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
+    float xs[K], ys[K], zs[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        xs[k] = ishift ? __fadd_rn(xi[k], tx) : xi[k];
+        ys[k] = ishift ? __fadd_rn(yi[k], ty) : yi[k];
+        zs[k] = ishift ? __fadd_rn(zi[k], tz) : zi[k];
+    }
+    for (int j0 = ja; j0 < jb; j0 += 32) {
+        const int nj = min(32, jb - j0);
+        if (lane < nj) {
+            float4 v = P.pos[j0 + lane];
+            if (jshift) {
+                v.x = __fadd_rn(v.x, sx);
+                v.y = __fadd_rn(v.y, sy);
+                v.z = __fadd_rn(v.z, sz);
+            }
+            buf[lane] = v;
+        }
+        __syncwarp();
+        if (nj == 32) {
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j)
+                interact<K, COUNT, POT, EPS0>(P, buf[j], j0 + j, iself, xs, ys, zs, ax, ay, az, cnt);
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < nj; ++j)
+                interact<K, COUNT, POT, EPS0>(P, buf[j], j0 + j, iself, xs, ys, zs, ax, ay, az, cnt);
+        }
+        __syncwarp();
+    }
+}
+
+template <int K, bool COUNT, bool POT, bool EPS0>
+__device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane) {
+    const int nc = P.nc;
+    const int c = item.x, i0 = item.y, ni = item.z;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    const float L = P.L;
+
+    float xi[K], yi[K], zi[K], mi[K];
+    float ax[K], ay[K], az[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int q = lane + 32 * k;
+        float4 p = q < ni ? P.pos[i0 + q] : make_float4(-1e30f, -1e30f, -1e30f, 0.0f);
+        xi[k] = p.x; yi[k] = p.y; zi[k] = p.z; mi[k] = p.w;
+        ax[k] = 0.0f; ay[k] = 0.0f; az[k] = 0.0f;
+    }
+    unsigned cnt = 0;
+    const int iself = i0 + lane;
+
+    for (int dz = -1; dz <= 1; ++dz) {
+        int rz = cz + dz;
+        float sjz = 0.0f, siz = 0.0f;
+        if (rz < 0) { rz += nc; sjz = -L; }
+        else if (rz >= nc) { rz -= nc; siz = -L; }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int ry = cy + dy;
+            float sjy = 0.0f, siy = 0.0f;
+            if (ry < 0) { ry += nc; sjy = -L; }
+            else if (ry >= nc) { ry -= nc; siy = -L; }
+            const int32_t *row = P.cell_start + (rz * nc + ry) * nc;
+            // cells (cx-1, cx, cx+1) of this row: one run, or two when it wraps in x
+            if (cx == 0) {
+                process_run<K, COUNT, POT, EPS0>(P, row[0], row[2], 0.f, sjy, sjz, 0.f, siy, siz, iself, xi, yi, zi,
+                                                 ax, ay, az, cnt, buf, lane);
+                process_run<K, COUNT, POT, EPS0>(P, row[nc - 1], row[nc], -L, sjy, sjz, 0.f, siy, siz, iself, xi, yi,
+                                                 zi, ax, ay, az, cnt, buf, lane);
+            } else if (cx == nc - 1) {
+                process_run<K, COUNT, POT, EPS0>(P, row[nc - 2], row[nc], 0.f, sjy, sjz, 0.f, siy, siz, iself, xi, yi,
+                                                 zi, ax, ay, az, cnt, buf, lane);
+                process_run<K, COUNT, POT, EPS0>(P, row[0], row[1], 0.f, sjy, sjz, -L, siy, siz, iself, xi, yi, zi, ax,
+                                                 ay, az, cnt, buf, lane);
+            } else {
+                process_run<K, COUNT, POT, EPS0>(P, row[cx - 1], row[cx + 2], 0.f, sjy, sjz, 0.f, siy, siz, iself, xi,
+                                                 yi, zi, ax, ay, az, cnt, buf, lane);
+            }
+        }
+    }
+
+    // epilogue
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int q = lane + 32 * k;
+        if (q >= ni) continue;
+        int i = i0 + q;
+        if (POT) {
+            P.phi_out[i] = 0.5f * P.G * mi[k] * ax[k];
+            continue;
+        }
+        float gx = P.G * ax[k], gy = P.G * ay[k], gz = P.G * az[k];
+        if (P.mode == kModeForce) {
+            int o = P.perm ? P.perm[i] : i;
+            P.out[o] = make_float4(gx, gy, gz, 0.0f);
+        } else {
+            float4 v = P.vel[i];
+            v.x = __fmaf_rn(P.h_kick, gx, v.x);
+            v.y = __fmaf_rn(P.h_kick, gy, v.y);
+            v.z = __fmaf_rn(P.h_kick, gz, v.z);
+            P.vel[i] = v;
+            float4 p;
+            p.x = __fmaf_rn(P.h_drift, v.x, xi[k]);
+            p.y = __fmaf_rn(P.h_drift, v.y, yi[k]);
+            p.z = __fmaf_rn(P.h_drift, v.z, zi[k]);
+            p.w = mi[k];
+            P.pos_next[i] = p;
+        }
+    }
+    if (COUNT) {
+        unsigned long long c64 = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c64 += __shfl_down_sync(0xffffffffu, c64, o);
+        if (lane == 0) atomicAdd(P.within, c64);
+    }
+}
+
+template <bool COUNT, bool POT, bool EPS0>
+__global__ void __launch_bounds__(kThreads, 6) k_sr_force(KParams P) {
+    __shared__ float4 tiles[kWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *buf = tiles[w];
+    const int n_items = *P.n_items;
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(P.work_counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        int4 item = P.items[it];
+        switch (item.w) {
+            case 1: process_item<1, COUNT, POT, EPS0>(P, item, buf, lane); break;
+            case 2: process_item<2, COUNT, POT, EPS0>(P, item, buf, lane); break;
+            case 3: process_item<3, COUNT, POT, EPS0>(P, item, buf, lane); break;
+            default: process_item<4, COUNT, POT, EPS0>(P, item, buf, lane); break;
+        }
+    }
+}
+
+template <bool COUNT, bool POT, bool EPS0>
+cudaError_t launch_variant(const KParams &P, int num_sms, cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_force<COUNT, POT, EPS0>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_sr_force<COUNT, POT, EPS0><<<num_sms * per_sm, kThreads, 0, s>>>(P);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(fl.work_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    KParams P;
+    P.pos = fl.pos;
+    P.items = fl.items;
+    P.n_items = fl.n_items;
+    P.cell_start = fl.cell_start;
+    P.work_counter = fl.work_counter;
+    P.nc = g.nc;
+    P.L = g.Lf;
+    P.T = fc.T;
+    P.eps = fc.eps;
+    P.G = fc.G;
+    P.q0 = fc.q[0]; P.q1 = fc.q[1]; P.q2 = fc.q[2]; P.q3 = fc.q[3]; P.q4 = fc.q[4]; P.q5 = fc.q[5];
+    P.u0 = fc.u[0]; P.u1 = fc.u[1]; P.u2 = fc.u[2]; P.u3 = fc.u[3]; P.u4 = fc.u[4]; P.u5 = fc.u[5];
+    P.u6 = fc.u[6];
+    P.phi0 = fc.phi0;
+    P.mode = fl.mode;
+    P.out = fl.out;
+    P.perm = fl.perm;
+    P.vel = fl.vel;
+    P.pos_next = fl.pos_next;
+    P.h_kick = fl.h_kick;
+    P.h_drift = fl.h_drift;
+    P.phi_out = fl.phi_out;
+    P.within = fl.within;
+    const bool eps0 = !(fc.eps > 0.0f);
+    const bool pot = fl.mode == kModePotential;
+    const bool count = fl.within != nullptr;
+    if (pot) return eps0 ? launch_variant<false, true, true>(P, num_sms, s) : launch_variant<false, true, false>(P, num_sms, s);
+    if (count) return eps0 ? launch_variant<true, false, true>(P, num_sms, s) : launch_variant<true, false, false>(P, num_sms, s);
+    return eps0 ? launch_variant<false, false, true>(P, num_sms, s) : launch_variant<false, false, false>(P, num_sms, s);
+}
+
+// ---- FP64 diagnostics ------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(256) k_diag(int64_t n, const float4 *__restrict__ pos,
+                                               const float4 *__restrict__ vel, const float *__restrict__ phi,
+                                               double *out) {
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = vel[i];
+        double m = pos[i].w;
+        s[0] += m * v.x;
+        s[1] += m * v.y;
+        s[2] += m * v.z;
+        s[3] += 0.5 * m * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        s[4] += phi ? (double)phi[i] : 0.0;
+    }
+    __shared__ double red[5][8];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double x = s[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double x = 0;
+        for (int q = 0; q < (int)(blockDim.x / 32); ++q) x += red[threadIdx.x][q];
+        atomicAdd(out + threadIdx.x, x);
+    }
+}
+}  // namespace
+
+cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const float *phi, double *out,
+                        cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 5 * sizeof(double), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    k_diag<<<blocks, 256, 0, s>>>(n, pos, vel, phi, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hacc

@@ -1,0 +1,60 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function include/hacc.h declares, and its host-only entry points behave."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared():
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(hacc_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1410_2805_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("hacc_bin", "hacc_sr_force", "hacc_subcycle", "hacc_step"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_split_matches_oracle_fit():
+    import paper_1410_2805_gb300 as hacc
+    from oracle import split
+    s = hacc.default_split()
+    o = split.default_split()
+    assert s.r_cut == np.float32(o["r_cut"])
+    assert s.eps == np.float32(o["eps"])
+    # two independent FP64 fits (Householder QR here, numpy's SVD there)
+    assert np.allclose(s.poly, o["poly"], rtol=1e-9, atol=0)
+
+
+def test_mesh_cells_rule():
+    import paper_1410_2805_gb300 as hacc
+    rc = hacc.default_split().r_cut
+    assert hacc.mesh_cells(32.0, rc) == 10
+    assert hacc.mesh_cells(256.0, rc) == 82
+    assert hacc.mesh_cells(512.0, rc) == 164
+    assert hacc.mesh_cells(8.0, rc) == -1            # fewer than 3 cells
+    assert hacc.mesh_cells(3.0 * rc, rc) == -1        # width would equal r_cut: one fewer

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Binning (wrap, cell ids, cell starts, stable permutation) must match bit for
+bit.  Forces must satisfy max_i |a_gpu - a_oracle| / rms_i |a_oracle| <= 1e-4
+(FP32 pair arithmetic and accumulation against FP64).  The candidate-pair count
+is exact; the inside-cutoff count may differ only by pairs whose FP32 and FP64
+distances fall on opposite sides of r_cut (a few per million).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def hacc(torch):
+    import paper_1410_2805_gb300 as h
+    from paper_1410_2805_gb300 import build
+    build.build()
+    return h
+
+
+@pytest.fixture(scope="module")
+def ctx(hacc):
+    c = hacc.Context()
+    yield c
+    c.close()
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _force_err(a_gpu, a_ref):
+    rms = np.sqrt((a_ref ** 2).sum(1).mean())
+    return np.abs(a_gpu[:, :3] - a_ref).max() / rms
+
+
+def _check_bin(torch, hacc, ctx, pos, L, r_cut):
+    nc = hacc.mesh_cells(L, r_cut)
+    wrapped_o, cell_o, ok = oracle.wrap_cell(pos, L, nc)
+    assert ok
+    count_o, start_o, perm_o = oracle.bin_cells(cell_o, nc)
+    p = _dev(torch, pos)
+    cell, start, perm = ctx.bin(hacc.Box(L=L), r_cut, p)
+    ctx.sync()
+    assert np.array_equal(p.cpu().numpy(), wrapped_o)
+    assert np.array_equal(cell.cpu().numpy(), cell_o)
+    assert np.array_equal(start.cpu().numpy(), start_o)
+    assert np.array_equal(perm.cpu().numpy(), perm_o)
+
+
+def test_bin_blob_mixture_bit_exact(torch, hacc, ctx, split_params):
+    pos = synth.blob_mixture(32768, 32.0, seed=1)
+    _check_bin(torch, hacc, ctx, pos, 32.0, np.float32(split_params["r_cut"]))
+
+
+def test_bin_faces_and_wrap_bit_exact(torch, hacc, ctx, split_params):
+    rc = np.float32(split_params["r_cut"])
+    for L in (32.0, float(np.float32(45.254834)), 10.0):
+        nc = hacc.mesh_cells(L, rc)
+        rng = np.random.default_rng(5)
+        xs = list(rng.uniform(-L, 2 * L, 2000).astype(np.float32))
+        for k in range(nc + 1):
+            b = np.float32(k * L / nc)
+            xs += [np.nextafter(b, np.float32(-1e9)), b, np.nextafter(b, np.float32(1e9))]
+        xs += [np.float32(-1e-9), np.float32(-L), np.float32(L), np.float32(-1e-30)]
+        x = np.array(xs, np.float32)
+        pos = np.stack([x, np.roll(x, 7), np.roll(x, 13), np.ones_like(x)], 1)
+        _check_bin(torch, hacc, ctx, pos, L, rc)
+
+
+def test_bin_empty_and_tiny(torch, hacc, ctx, split_params):
+    rc = np.float32(split_params["r_cut"])
+    for n in (0, 1, 2, 33):
+        pos = synth.uniform(n, 16.0, seed=n) if n else np.zeros((0, 4), np.float32)
+        if n == 0:
+            p = torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+            cell, start, perm = ctx.bin(hacc.Box(L=16.0), rc, p)
+            ctx.sync()
+            assert start.cpu().numpy().max() == 0
+            continue
+        _check_bin(torch, hacc, ctx, pos, 16.0, rc)
+
+
+@pytest.mark.parametrize("case", ["c1", "ragged", "nc3", "odd_box", "masses_G", "eps0", "dense_cell"])
+def test_sr_force_parity(torch, hacc, ctx, split_params, case):
+    sp = dict(split_params)
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    L = 32.0
+    if case == "c1":
+        pos = synth.blob_mixture(32768, L, seed=1)
+    elif case == "ragged":
+        pos = synth.blob_mixture(4099, 20.0, seed=2, n_blobs=7)
+        L = 20.0
+    elif case == "nc3":
+        L = 9.5
+        pos = synth.blob_mixture(900, L, seed=3, n_blobs=3)
+    elif case == "odd_box":
+        L = float(np.float32(45.254834))
+        pos = synth.blob_mixture(20000, L, seed=4, n_blobs=40)
+    elif case == "masses_G":
+        L = 24.0
+        pos = synth.blob_mixture(12000, L, seed=6, n_blobs=20)
+        pos[:, 3] = np.random.default_rng(0).uniform(0.25, 4.0, len(pos)).astype(np.float32)
+        sp["G"] = 0.75
+    elif case == "eps0":
+        L = 20.0
+        pos = synth.uniform(6000, L, seed=7)
+        sp["eps"] = 0.0
+    else:   # one very crowded cell (several hundred particles) among sparse ones
+        L = 24.0
+        pos = synth.blob_mixture(6000, L, seed=8, n_blobs=2, sigma=0.4)
+    a_ref, within_ref = oracle.force_mesh(pos, L, sp)
+    p = _dev(torch, pos)
+    acc = ctx.sr_force(hacc.Box(L=L), sp, p)
+    cand, within = ctx.pair_counts(hacc.Box(L=L), sp, p)
+    a = acc.cpu().numpy()
+    assert np.all(a[:, 3] == 0)
+    err = _force_err(a, a_ref)
+    assert err <= FORCE_TOL, err
+    # exact 27-cell candidate count from the oracle's own binning
+    nc = hacc.mesh_cells(L, sp["r_cut"])
+    _, cell_o, _ = oracle.wrap_cell(pos, L, nc)
+    count_o, _, _ = oracle.bin_cells(cell_o, nc)
+    assert cand == oracle.candidates(count_o, nc)
+    assert abs(within - within_ref) <= max(2, within_ref // 200000)
+    # counting variant gives bitwise the same forces
+    acc2 = ctx.sr_force(hacc.Box(L=L), sp, p, pair_counts=torch.zeros(2, dtype=torch.int64, device="cuda"))
+    assert torch.equal(acc, acc2)
+
+
+def test_sr_force_deterministic_and_third_law(torch, hacc, ctx, split_params):
+    pos = synth.blob_mixture(32768, 32.0, seed=11)
+    p = _dev(torch, pos)
+    a1 = ctx.sr_force(hacc.Box(L=32.0), split_params, p).clone()
+    a2 = ctx.sr_force(hacc.Box(L=32.0), split_params, p)
+    assert torch.equal(a1, a2)
+    a = a1.double().cpu().numpy()[:, :3]
+    m = pos[:, 3].astype(np.float64)
+    assert np.abs((m[:, None] * a).sum(0)).max() < 1e-5 * (m[:, None] * np.abs(a)).sum()
+
+
+def test_sr_force_lattice_zero(torch, hacc, ctx, split_params):
+    pos = synth.lattice(16)
+    a = ctx.sr_force(hacc.Box(L=16.0), split_params, _dev(torch, pos)).cpu().numpy()
+    assert np.abs(a).max() < 1e-4
+
+
+def test_sr_force_empty(torch, hacc, ctx, split_params):
+    p = torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+    acc = ctx.sr_force(hacc.Box(L=16.0), split_params, p)
+    ctx.sync()
+    assert acc.shape == (0, 4)
+
+
+def test_host_variant_equals_device(torch, hacc, ctx, split_params):
+    pos = synth.blob_mixture(5000, 20.0, seed=12)
+    a_dev = ctx.sr_force(hacc.Box(L=20.0), split_params, _dev(torch, pos)).cpu().numpy()
+    a_host = np.zeros_like(pos)
+    ctx.sr_force_host(hacc.Box(L=20.0), split_params, pos.copy(), a_host)
+    assert np.array_equal(a_dev, a_host)
+
+
+def test_errors(torch, hacc, ctx, split_params):
+    p = _dev(torch, synth.uniform(100, 16.0, seed=1))
+    with pytest.raises(hacc.HaccError) as e:
+        ctx.sr_force(hacc.Box(L=8.0), split_params, p)          # < 3 cells
+    assert e.value.status == hacc.HACC_EDOMAIN
+    with pytest.raises(hacc.HaccError) as e:
+        ctx.sr_force(hacc.Box(L=0.1 + 16.0), split_params, p)   # not an FP32 value
+    assert e.value.status == hacc.HACC_EINVAL
+    bad = synth.uniform(100, 16.0, seed=2)
+    bad[5, 0] = 40.0                                            # outside [-L, 2L)
+    ctx.sr_force(hacc.Box(L=16.0), split_params, _dev(torch, bad))
+    with pytest.raises(hacc.HaccError) as e:
+        ctx.sync()
+    assert e.value.status == hacc.HACC_EDOMAIN
+    ctx.sync()                                                  # flag was cleared
+
+
+def test_subcycle_parity(torch, hacc, ctx, split_params):
+    # FP32 drift/kick against the FP64 SKS oracle.  Positions carry FP32
+    # rounding of ~ulp(L)/2 per stream; over 2*n_sub streams and the force
+    # tolerance of 1e-4 per kick the trajectories stay within the bounds below.
+    L = 16.0
+    pos = synth.blob_mixture(3000, L, seed=21, n_blobs=6, sigma=0.8)
+    vel = synth.gaussian_velocities(3000, seed=21, sigma=0.1)
+    sp = dict(split_params, eps=float(np.float32(0.01)))
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    dt, nsub = 0.05, 4
+    xo, vo = oracle.subcycle(pos, vel, L, sp, dt, nsub)
+    p, v = _dev(torch, pos), _dev(torch, vel)
+    ctx.subcycle(hacc.Box(L=L), sp, p, v, dt, nsub)
+    ctx.sync()
+    x = p.cpu().numpy().astype(np.float64)
+    vv = v.cpu().numpy().astype(np.float64)
+    d = x[:, :3] - xo
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < 2e-5 * L
+    vscale = np.sqrt((vo ** 2).sum(1).mean())
+    assert np.abs(vv[:, :3] - vo).max() < 1e-3 * vscale
+    assert np.all(x[:, 3] == pos[:, 3])
+    assert np.all((x[:, :3] >= 0) & (x[:, :3] < L))
+
+
+def test_diagnostics_parity(torch, hacc, ctx, split_params):
+    L = 16.0
+    pos = synth.blob_mixture(4000, L, seed=31, n_blobs=5)
+    pos[:, 3] = np.random.default_rng(2).uniform(0.5, 2.0, len(pos)).astype(np.float32)
+    vel = synth.gaussian_velocities(4000, seed=31)
+    out = ctx.diagnostics(hacc.Box(L=L), split_params, _dev(torch, pos), _dev(torch, vel)).cpu().numpy()
+    sp = dict(split_params)
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    mom, ke, pe = oracle.diagnostics(pos[:, :3].astype(np.float64), vel[:, :3].astype(np.float64),
+                                     pos[:, 3].astype(np.float64), L, sp)
+    assert np.allclose(out[:3], mom, rtol=1e-12, atol=1e-9)
+    assert out[3] == pytest.approx(ke, rel=1e-12)
+    assert out[4] == pytest.approx(pe, rel=1e-4)
