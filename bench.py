@@ -50,7 +50,7 @@ CONFIGS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="zeldovich256")
@@ -152,13 +152,18 @@ def cpu_oracle_rate(pos, L, split_params, target_s: float, seed: int = 99):
     import oracle
     rng = np.random.default_rng(seed)
     n = len(pos)
-    sel = rng.choice(n, size=min(n, 4096), replace=False).astype(np.int64)
-    t0 = time.perf_counter()
-    _, w = oracle.force_mesh(pos, L, split_params, sel=sel)
-    t_probe = time.perf_counter() - t0
-    # the probe includes the oracle's cell-list build over all n particles; size
-    # the sample so that the measured call lasts about target_s
-    m = int(min(n, max(4096, 4096 * target_s / max(t_probe, 1e-3))))
+    # two probes fit t(m) = a + b m (a: the oracle's cell-list build over all
+    # n particles, b: per sampled particle); then size the measured call
+    times = []
+    for m in (2048, 16384):
+        sel = rng.choice(n, size=min(n, m), replace=False).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.force_mesh(pos, L, split_params, sel=sel)
+        times.append((min(n, m), time.perf_counter() - t0))
+    (m1, t1), (m2, t2) = times
+    b = max((t2 - t1) / max(m2 - m1, 1), 1e-9)
+    a = max(t1 - b * m1, 0.0)
+    m = int(min(n, max(m2, (target_s - a) / b)))
     sel = rng.choice(n, size=m, replace=False).astype(np.int64)
     t0 = time.perf_counter()
     _, w = oracle.force_mesh(pos, L, split_params, sel=sel)

@@ -159,11 +159,13 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
  * M_lr is a kick by the long-range spectral PM force (CIC deposit, Eq. (filter)
  * Gauss-sinc filter, Eq. (greenf) influence function, Eq. (sldiff) Super-Lanczos
  * gradient, CIC interpolation; Sec. 2.3) on an ng^3 grid, and M_sr the
- * sub-cycle above. */
+ * sub-cycle above.  Both forces use split->G. */
 hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                       int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
 
-/* Long-range PM acceleration alone: acc[n] receives (ax, ay, az, 0). */
+/* Long-range PM acceleration alone (with G = 1): acc[n] receives (ax, ay, az, 0).
+ * ng = 0 in the box means ng = round(L); ng must be even, 4 <= ng <= 2048.
+ * The grid, its FFT plans and buffers are kept by the context between calls. */
 hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, int64_t n,
                           const float *pos_m, float *acc, hacc_stream_t stream);
 

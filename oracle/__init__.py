@@ -182,3 +182,19 @@ def diagnostics(x, v, m, L, split_params):
                                   float(split_params["r_cut"]), float(split_params["eps"]), _ptr(c),
                                   float(split_params["G"]), _ptr(out))
     return out[:3].copy(), float(out[3]), float(out[4])
+
+
+def step(pos, vel, L, split_params, dt, n_c, ng=None, sigma=0.8, ns=3):
+    """One full step of Eq. (tstep), FP64: long-range kick dt/2 (spectral PM,
+    oracle/pm.py), n_c short-range SKS sub-cycles of dt/n_c, long-range kick
+    dt/2.  Returns new (x n x 3, v n x 3)."""
+    from . import pm
+    x, m = _xm(pos)
+    v = np.ascontiguousarray(np.asarray(vel)[:, :3], dtype=np.float64).copy()
+    ng = int(round(L)) if ng is None else int(ng)
+    G = float(split_params["G"])
+    v += 0.5 * dt * G * pm.pm_accel(x, m, L, ng, sigma=sigma, ns=ns)
+    p1 = np.concatenate([x, m[:, None]], axis=1)
+    x, v = subcycle(p1, v, L, split_params, dt, n_c)
+    v += 0.5 * dt * G * pm.pm_accel(x, m, L, ng, sigma=sigma, ns=ns)
+    return x, v

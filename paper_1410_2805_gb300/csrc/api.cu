@@ -480,7 +480,7 @@ hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm,
     HACC_TRY(check_particles(ctx, n, pos_m, acc));
     if (n > 0 && !acc) return set_error(ctx, HACC_EINVAL, "acc is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return pm_accel(ctx, box, pm, n, reinterpret_cast<const float4 *>(pos_m), reinterpret_cast<float4 *>(acc),
+    return pm_accel(ctx, box, pm, 1.0, n, reinterpret_cast<const float4 *>(pos_m), reinterpret_cast<float4 *>(acc),
                     nullptr, 0.0f, s);
 }
 
@@ -493,10 +493,11 @@ hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     float4 *p = reinterpret_cast<float4 *>(pos_m);
     float4 *v = reinterpret_cast<float4 *>(vel);
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     // M_lr(dt/2): kick by the long-range force
-    HACC_TRY(pm_accel(ctx, box, pm, n, p, nullptr, v, (float)(0.5 * dt), s));
+    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s));
     HACC_TRY(hacc_subcycle(ctx, box, split, n, pos_m, vel, dt, n_c, stream));
-    HACC_TRY(pm_accel(ctx, box, pm, n, p, nullptr, v, (float)(0.5 * dt), s));
+    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s));
     return HACC_OK;
 }
 

@@ -77,6 +77,22 @@ __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restr
     rank[i] = (int32_t)atomicAdd(&count[c], 1u);
 }
 
+// Lane layout of a work item of n <= 128 particles: 2^lg groups of 32 >> lg
+// lanes, K particles per lane; the smallest slot count (32 >> lg) * K >= n,
+// preferring larger K.  Encoded as (lg << 4) | K.
+__device__ __forceinline__ int item_shape(uint32_t n) {
+    if (n <= 4) return (3 << 4) | 1;
+    if (n <= 8) return (3 << 4) | 2;
+    if (n <= 12) return (3 << 4) | 3;
+    if (n <= 16) return (3 << 4) | 4;
+    if (n <= 24) return (2 << 4) | 3;
+    if (n <= 32) return (2 << 4) | 4;
+    if (n <= 48) return (1 << 4) | 3;
+    if (n <= 64) return (1 << 4) | 4;
+    if (n <= 96) return 3;
+    return 4;
+}
+
 __device__ __forceinline__ uint32_t items_of(uint32_t cnt) {
     return cnt == 0 ? 0u : (cnt <= (uint32_t)kItemMax ? 1u : (cnt + kItemMax - 1) / kItemMax);
 }
@@ -233,15 +249,11 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
     uint32_t cnt = count[c];
     uint32_t it = (uint32_t)(p >> 32);
     if (cnt == 0) return;
-    if (cnt <= (uint32_t)kItemMax) {
-        items[it] = make_int4((int)c, (int)s, (int)cnt, (int)((cnt + 31) / 32));
-        return;
-    }
     uint32_t m = items_of(cnt);
     for (uint32_t q = 0; q < m; ++q) {
         uint32_t ni = cnt - q * kItemMax;
         ni = ni > (uint32_t)kItemMax ? (uint32_t)kItemMax : ni;
-        items[it + q] = make_int4((int)c, (int)(s + q * kItemMax), (int)ni, 4);
+        items[it + q] = make_int4((int)c, (int)(s + q * kItemMax), (int)ni, item_shape(ni));
     }
 }
 

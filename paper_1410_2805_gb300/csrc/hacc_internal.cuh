@@ -19,8 +19,8 @@ enum DeviceFlag : int {
 };
 
 // Chunking of a chaining-mesh cell into force work items: a cell of n
-// particles is one item of K = ceil(n/32) particles per lane when n <= 128,
-// else ceil(n/128) items of up to 128 particles (K = 4).
+// particles is one item when n <= 128, else ceil(n/128) items of up to 128
+// particles; each item is processed by one warp (see item_shape in bin.cu).
 constexpr int kItemMax = 128;
 
 struct Scratch {
@@ -170,7 +170,9 @@ cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const f
                         cudaStream_t s);
 
 // ---- PM (pm.cu) ------------------------------------------------------------
-hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, int64_t n, const float4 *pos,
+// Long-range acceleration G * a_PM at pos; stored to acc (if non-null) and/or
+// added as a kick vel += kick * a (if vel_kick is non-null).
+hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, double G, int64_t n, const float4 *pos,
                      float4 *acc, float4 *vel_kick, float kick, cudaStream_t s);
 void pm_destroy(hacc_ctx *ctx);
 

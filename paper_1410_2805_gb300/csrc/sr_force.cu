@@ -69,7 +69,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 // Accumulate the interaction of one staged j (already image-shifted) with
 // the K i-particles of this lane.
 template <int K, bool COUNT, bool POT, bool EPS0>
-__device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, int iself, const float (&xi)[K],
+__device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, int iself, int lpg, const float (&xi)[K],
                                          const float (&yi)[K], const float (&zi)[K], float (&ax)[K],
                                          float (&ay)[K], float (&az)[K], unsigned &cnt) {
 #pragma unroll
@@ -89,7 +89,7 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
             u = __fmaf_rn(u, t, P.u1);
             u = __fmaf_rn(u, t, P.u0);
             float ph = -r - u - P.phi0;
-            const bool self = jidx == iself + 32 * k;       // i's own row (sorted index)
+            const bool self = jidx == iself + lpg * k;   // i's own row (sorted index)
             ax[k] += (in && !self) ? ph * pj.w : 0.0f;
         } else {
             float r3 = r * r * r;
@@ -106,21 +106,25 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
             ay[k] = __fmaf_rn(fs, dy, ay[k]);
             az[k] = __fmaf_rn(fs, dz, az[k]);
         }
-        if (COUNT) cnt += (in && jidx != iself + 32 * k) ? 1u : 0u;   // j != i
+        if (COUNT) cnt += (in && jidx != iself + lpg * k) ? 1u : 0u;   // j != i
     }
 }
 
 // Stream one run [ja, jb) of consecutive sorted particles through the warp's
 // shared tile.  (sx, sy, sz): image shift added to the staged j coordinates;
-// (tx, ty, tz): image shift added to this lane's i coordinates.
+// (tx, ty, tz): image shift added to this lane's i coordinates.  The warp is
+// split into G = 2^lg lane groups; group g takes the staged entries g, g+G,
+// g+2G, ... (consecutive float4 addresses across groups: no bank conflicts).
 template <int K, bool COUNT, bool POT, bool EPS0>
 __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
-                                            float ty, float tz, int iself, const float (&xi)[K],
-                                            const float (&yi)[K], const float (&zi)[K], float (&ax)[K],
-                                            float (&ay)[K], float (&az)[K], unsigned &cnt, float4 *buf,
-                                            int lane) {
+                                            float ty, float tz, int iself, int lg, int grp,
+                                            const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
+                                            float (&ax)[K], float (&ay)[K], float (&az)[K], unsigned &cnt,
+                                            float4 *buf, int lane) {
     const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
+    const int G = 1 << lg;
+    const int lpg = 32 >> lg;
     float xs[K], ys[K], zs[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -130,25 +134,24 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
     }
     for (int j0 = ja; j0 < jb; j0 += 32) {
         const int nj = min(32, jb - j0);
+        // entries past the run are far away with zero mass: outside the cutoff
+        float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
         if (lane < nj) {
-            float4 v = P.pos[j0 + lane];
+            v = P.pos[j0 + lane];
             if (jshift) {
                 v.x = __fadd_rn(v.x, sx);
                 v.y = __fadd_rn(v.y, sy);
                 v.z = __fadd_rn(v.z, sz);
             }
-            buf[lane] = v;
         }
+        buf[lane] = v;
         __syncwarp();
-        if (nj == 32) {
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j)
-                interact<K, COUNT, POT, EPS0>(P, buf[j], j0 + j, iself, xs, ys, zs, ax, ay, az, cnt);
-        } else {
-#pragma unroll 2
-            for (int j = 0; j < nj; ++j)
-                interact<K, COUNT, POT, EPS0>(P, buf[j], j0 + j, iself, xs, ys, zs, ax, ay, az, cnt);
-        }
+        const int trips = (nj + G - 1) >> lg;
+        int e = grp;
+        constexpr int kUnroll = K >= 3 ? 2 : 4;   // bounded by registers
+#pragma unroll kUnroll
+        for (int t = 0; t < trips; ++t, e += G)
+            interact<K, COUNT, POT, EPS0>(P, buf[e], e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
         __syncwarp();
     }
 }
@@ -157,20 +160,25 @@ template <int K, bool COUNT, bool POT, bool EPS0>
 __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane) {
     const int nc = P.nc;
     const int c = item.x, i0 = item.y, ni = item.z;
+    const int lg = item.w >> 4;           // 2^lg lane groups
+    const int lpg = 32 >> lg;             // lanes per group
+    const int grp = lane >> (5 - lg);
+    const int slot = lane & (lpg - 1);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
     const float L = P.L;
 
+    // every group holds the same K x lpg particles of the cell
     float xi[K], yi[K], zi[K], mi[K];
     float ax[K], ay[K], az[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        int q = lane + 32 * k;
+        int q = slot + lpg * k;
         float4 p = q < ni ? P.pos[i0 + q] : make_float4(-1e30f, -1e30f, -1e30f, 0.0f);
         xi[k] = p.x; yi[k] = p.y; zi[k] = p.z; mi[k] = p.w;
         ax[k] = 0.0f; ay[k] = 0.0f; az[k] = 0.0f;
     }
     unsigned cnt = 0;
-    const int iself = i0 + lane;
+    const int iself = i0 + slot;          // sorted index of this lane's k = 0 particle
 
     for (int dz = -1; dz <= 1; ++dz) {
         int rz = cz + dz;
@@ -184,49 +192,67 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane)
             else if (ry >= nc) { ry -= nc; siy = -L; }
             const int32_t *row = P.cell_start + (rz * nc + ry) * nc;
             // cells (cx-1, cx, cx+1) of this row: one run, or two when it wraps in x
-            if (cx == 0) {
-                process_run<K, COUNT, POT, EPS0>(P, row[0], row[2], 0.f, sjy, sjz, 0.f, siy, siz, iself, xi, yi, zi,
-                                                 ax, ay, az, cnt, buf, lane);
-                process_run<K, COUNT, POT, EPS0>(P, row[nc - 1], row[nc], -L, sjy, sjz, 0.f, siy, siz, iself, xi, yi,
+            const int nruns = (cx == 0 || cx == nc - 1) ? 2 : 1;
+#pragma unroll 1
+            for (int r = 0; r < nruns; ++r) {
+                int ja, jb;
+                float sjx = 0.0f, six = 0.0f;
+                if (cx == 0) {
+                    ja = r ? row[nc - 1] : row[0];
+                    jb = r ? row[nc] : row[2];
+                    sjx = r ? -L : 0.0f;
+                } else if (cx == nc - 1) {
+                    ja = r ? row[0] : row[nc - 2];
+                    jb = r ? row[1] : row[nc];
+                    six = r ? -L : 0.0f;
+                } else {
+                    ja = row[cx - 1];
+                    jb = row[cx + 2];
+                }
+                process_run<K, COUNT, POT, EPS0>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, iself, lg, grp, xi, yi,
                                                  zi, ax, ay, az, cnt, buf, lane);
-            } else if (cx == nc - 1) {
-                process_run<K, COUNT, POT, EPS0>(P, row[nc - 2], row[nc], 0.f, sjy, sjz, 0.f, siy, siz, iself, xi, yi,
-                                                 zi, ax, ay, az, cnt, buf, lane);
-                process_run<K, COUNT, POT, EPS0>(P, row[0], row[1], 0.f, sjy, sjz, -L, siy, siz, iself, xi, yi, zi, ax,
-                                                 ay, az, cnt, buf, lane);
-            } else {
-                process_run<K, COUNT, POT, EPS0>(P, row[cx - 1], row[cx + 2], 0.f, sjy, sjz, 0.f, siy, siz, iself, xi,
-                                                 yi, zi, ax, ay, az, cnt, buf, lane);
             }
         }
     }
 
-    // epilogue
+    // sum the groups' partial forces (the groups saw disjoint j)
+    for (int o = 16; o >= lpg; o >>= 1) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        int q = lane + 32 * k;
-        if (q >= ni) continue;
-        int i = i0 + q;
-        if (POT) {
-            P.phi_out[i] = 0.5f * P.G * mi[k] * ax[k];
-            continue;
+        for (int k = 0; k < K; ++k) {
+            ax[k] += __shfl_xor_sync(0xffffffffu, ax[k], o);
+            ay[k] += __shfl_xor_sync(0xffffffffu, ay[k], o);
+            az[k] += __shfl_xor_sync(0xffffffffu, az[k], o);
         }
-        float gx = P.G * ax[k], gy = P.G * ay[k], gz = P.G * az[k];
-        if (P.mode == kModeForce) {
-            int o = P.perm ? P.perm[i] : i;
-            P.out[o] = make_float4(gx, gy, gz, 0.0f);
-        } else {
-            float4 v = P.vel[i];
-            v.x = __fmaf_rn(P.h_kick, gx, v.x);
-            v.y = __fmaf_rn(P.h_kick, gy, v.y);
-            v.z = __fmaf_rn(P.h_kick, gz, v.z);
-            P.vel[i] = v;
-            float4 p;
-            p.x = __fmaf_rn(P.h_drift, v.x, xi[k]);
-            p.y = __fmaf_rn(P.h_drift, v.y, yi[k]);
-            p.z = __fmaf_rn(P.h_drift, v.z, zi[k]);
-            p.w = mi[k];
-            P.pos_next[i] = p;
+    }
+
+    // epilogue (group 0 writes)
+    if (grp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            int q = slot + lpg * k;
+            if (q >= ni) continue;
+            int i = i0 + q;
+            if (POT) {
+                P.phi_out[i] = 0.5f * P.G * mi[k] * ax[k];
+                continue;
+            }
+            float gx = P.G * ax[k], gy = P.G * ay[k], gz = P.G * az[k];
+            if (P.mode == kModeForce) {
+                int o = P.perm ? P.perm[i] : i;
+                P.out[o] = make_float4(gx, gy, gz, 0.0f);
+            } else {
+                float4 v = P.vel[i];
+                v.x = __fmaf_rn(P.h_kick, gx, v.x);
+                v.y = __fmaf_rn(P.h_kick, gy, v.y);
+                v.z = __fmaf_rn(P.h_kick, gz, v.z);
+                P.vel[i] = v;
+                float4 p;
+                p.x = __fmaf_rn(P.h_drift, v.x, xi[k]);
+                p.y = __fmaf_rn(P.h_drift, v.y, yi[k]);
+                p.z = __fmaf_rn(P.h_drift, v.z, zi[k]);
+                p.w = mi[k];
+                P.pos_next[i] = p;
+            }
         }
     }
     if (COUNT) {
@@ -249,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_sr_force(KParams P) {
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
         int4 item = P.items[it];
-        switch (item.w) {
+        switch (item.w & 15) {
             case 1: process_item<1, COUNT, POT, EPS0>(P, item, buf, lane); break;
             case 2: process_item<2, COUNT, POT, EPS0>(P, item, buf, lane); break;
             case 3: process_item<3, COUNT, POT, EPS0>(P, item, buf, lane); break;
