@@ -189,6 +189,33 @@ hacc_status hacc_subcycle_host(hacc_ctx *ctx, const hacc_box *box, const hacc_sp
 hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                            int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
 
+/* Size of the fixed device scratch behind hacc_sr_force_noalloc (16 MiB). */
+#define HACC_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Short-range force without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not call
+ * cudaMalloc (their device memory is owned by another allocator or runtime,
+ * or allocation is forbidden after their set-up), and so cannot create a
+ * context.  It computes what hacc_sr_force computes (same kernels, no pair
+ * counts), with all scratch taken from one fixed device array of
+ * HACC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  The caller owns pos_m
+ * (n rows, not modified) and acc (n rows, receives (ax, ay, az, 0)).
+ *   - Limit: about 48 bytes per particle plus 32 bytes per chaining-mesh cell
+ *     must fit in the array (e.g. 262144 particles with up to 100000 cells);
+ *     larger problems return HACC_ENOMEM before anything is enqueued.
+ *   - Works on the current CUDA device.  Its first call on a device looks up
+ *     the array's device address (once per device); make that first call
+ *     before any stream capture.
+ *   - All calls share the array and leave their data in it; calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on it and
+ *     give wrong results, so serialise them.
+ *   - Coordinates outside [-L, 2L) are not reported (no context holds the
+ *     flag); the forces are then undefined but memory accesses stay in bounds.
+ * Other errors as for hacc_sr_force (HACC_EINVAL, HACC_EDOMAIN, HACC_ECUDA). */
+hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_split *split, int64_t n,
+                                  const float *pos_m, float *acc, hacc_stream_t stream);
+
 /* Run statistics kept by a context (instrumentation, not part of the method). */
 typedef struct {
     int64_t kernel_launches;  /* kernels this context launched */
