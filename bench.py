@@ -242,6 +242,7 @@ def run_ours(args):
     vel = torch.from_numpy(vel_np).cuda()
     use_pm = not args.no_pm
     dt, n_c = cfg["dt"], cfg["n_c"]
+    tuning = ctx.tune(box, split, pos, reps=3)
 
     def step(p, v):
         if use_pm:
@@ -351,7 +352,9 @@ def run_ours(args):
             "candidate_pairs_per_step": cand / args.steps,
             "replay_bitwise_equal": replay_ok,
             "gpu_launches": st["kernel_launches"],
-            "roofline": roofline, "e2e": e2e, "clocks": clk}
+            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "autotune": {"variant": tuning["chosen"], "force_ms_by_variant": tuning["times_ms"],
+                         "variants": "(blocks/SM, unroll) = (6,deep), (8,light), (6,light), (5,deep)"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import split as osplit
         sp = osplit.default_split()

@@ -216,6 +216,23 @@ hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split 
 hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_split *split, int64_t n,
                                   const float *pos_m, float *acc, hacc_stream_t stream);
 
+/* Number of pair-kernel variants (register budget x unroll depth). */
+#define HACC_FORCE_VARIANTS 4
+
+/* Autotuner (a tuning aid of the library; the paper has no counterpart):
+ * bins pos_m once, times every pair-kernel variant on it (reps launches each,
+ * CUDA events on `stream`), and keeps the fastest for this context's later
+ * calls.  times_ms (nullable, host, HACC_FORCE_VARIANTS doubles) receives
+ * each variant's mean launch time, *chosen (nullable) the variant kept.
+ * Synchronises `stream`.  Results of later calls do not depend on the
+ * variant (all variants sum the same pairs in the same order). */
+hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                      const float *pos_m, int32_t reps, double *times_ms, int32_t *chosen,
+                      hacc_stream_t stream);
+
+/* Select the pair-kernel variant by hand (0 <= variant < HACC_FORCE_VARIANTS). */
+hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant);
+
 /* Run statistics kept by a context (instrumentation, not part of the method). */
 typedef struct {
     int64_t kernel_launches;  /* kernels this context launched */

@@ -122,6 +122,9 @@ def lib():
             "hacc_step_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), ctypes.POINTER(_Pm), i64, p,
                                     p, d, i32, p]),
             "hacc_stats_enable": (st, [p, ctypes.c_int, ctypes.c_int]),
+            "hacc_tune": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, i32,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
+            "hacc_set_variant": (st, [p, i32]),
             "hacc_stats_read": (st, [p, ctypes.POINTER(_Stats), ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -199,6 +202,20 @@ class Context:
 
     def sync(self, stream=None):
         self._check(lib().hacc_ctx_sync(self._h, self._stream(stream)), "hacc_ctx_sync")
+
+    def tune(self, box: Box, split, pos, reps: int = 3, stream=None) -> dict:
+        """Time every pair-kernel variant on this machine and keep the fastest."""
+        _dev_rows(pos, "pos")
+        sp = _split_of(split)
+        nv = 4
+        times = (ctypes.c_double * nv)()
+        chosen = ctypes.c_int32(-1)
+        self._check(lib().hacc_tune(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0], _ptr(pos),
+                                    int(reps), times, ctypes.byref(chosen), self._stream(stream)), "hacc_tune")
+        return dict(chosen=int(chosen.value), times_ms=[float(t) for t in times])
+
+    def set_variant(self, variant: int):
+        self._check(lib().hacc_set_variant(self._h, int(variant)), "hacc_set_variant")
 
     def stats_enable(self, timing: bool = False, counting: bool = False):
         self._check(lib().hacc_stats_enable(self._h, int(timing), int(counting)), "hacc_stats_enable")

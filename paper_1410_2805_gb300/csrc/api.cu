@@ -225,6 +225,8 @@ hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts
     fl.h_drift = hd;
     fl.phi_out = w->phi;
     fl.within = within;
+    fl.mass_flag = w->b.mass_flag;
+    fl.variant = ctx->variant;
     if (ctx->counting && mode != kModePotential && !within) {
         HACC_CUDA(candidate_count(g, w->b.cell_start, ctx->d_pairs, s), "candidate count");
         fl.within = ctx->d_pairs + 1;
@@ -316,6 +318,65 @@ hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream) {
 }
 
 int32_t hacc_mesh_cells(double L, float r_cut) { return default_nc(L, r_cut); }
+
+hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant) {
+    HACC_TRY(enter(ctx));
+    if (variant < 0 || variant >= kForceVariants) return set_error(ctx, HACC_EINVAL, "variant out of range");
+    ctx->variant = variant;
+    return HACC_OK;
+}
+
+hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, const float *pos_m,
+                      int32_t reps, double *times_ms, int32_t *chosen, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (reps < 1) return set_error(ctx, HACC_EINVAL, "reps must be >= 1");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, pos_m, nullptr));
+    if (n == 0) return HACC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
+    HACC_CUDA(bin_build(g, n, reinterpret_cast<const float4 *>(pos_m), nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s),
+              "binning");
+    HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
+    cudaEvent_t e0, e1;
+    HACC_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    HACC_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    const int saved = ctx->variant;
+    const bool saved_timing = ctx->timing, saved_counting = ctx->counting;
+    ctx->timing = ctx->counting = false;
+    double best = 1e300;
+    int best_v = 0;
+    hacc_status st = HACC_OK;
+    for (int v = 0; v < kForceVariants && st == HACC_OK; ++v) {
+        ctx->variant = v;
+        // forces go to w.P in sorted order (P is free after the gather)
+        st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr, s);
+        if (st != HACC_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == HACC_OK; ++r)
+            st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { st = check_cuda(ctx, e, "cudaEventSynchronize"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double per = (double)ms / reps;
+        if (times_ms) times_ms[v] = per;
+        if (per < best) { best = per; best_v = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = saved_timing;
+    ctx->counting = saved_counting;
+    ctx->variant = st == HACC_OK ? best_v : saved;
+    if (chosen) *chosen = ctx->variant;
+    return st;
+}
 
 hacc_status hacc_stats_enable(hacc_ctx *ctx, int timing, int counting) {
     HACC_TRY(enter(ctx));

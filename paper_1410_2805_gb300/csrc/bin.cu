@@ -56,10 +56,11 @@ __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restr
                                                  const float4 *__restrict__ vel, float drift,
                                                  float4 *dst, float Lf, float inv_w, double Ld, int nc,
                                                  int32_t *__restrict__ key, int32_t *__restrict__ rank,
-                                                 uint32_t *__restrict__ count, int *flags) {
+                                                 uint32_t *__restrict__ count, int *flags, int *mass_flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = src[i];
+    if (p.w != src[0].w) atomicOr(mass_flag, 1);
     if (vel) {
         float4 v = vel[i];
         p.x = __fmaf_rn(drift, v.x, p.x);
@@ -345,15 +346,17 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
     b->perm = c.take<int32_t>(n);
     b->items = c.take<int4>(max_items(n, ncell));
     b->n_items = c.take<int32_t>(1);
+    b->mass_flag = c.take<int>(1);
 }
 
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
     if (n > 0) {
         k_key<<<blocks_for(n), kBlock, 0, s>>>(n, src, vel, drift, dst, g.Lf, g.inv_w, g.Ld, g.nc, b.key,
-                                               b.rank, b.count, d_flags);
+                                               b.rank, b.count, d_flags, b.mass_flag);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

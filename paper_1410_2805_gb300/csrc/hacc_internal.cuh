@@ -47,6 +47,7 @@ struct hacc_ctx {
     // statistics (hacc_stats_*)
     bool timing = false, counting = false;
     int64_t launches = 0, force_launches = 0;
+    int variant = 0;                          // pair-kernel variant (hacc_tune)
     double force_ms = 0.0;
     unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -115,6 +116,7 @@ struct BinBuffers {
     int32_t *perm;         // [n]
     int4 *items;           // [max_items]
     int32_t *n_items;      // [1] device
+    int *mass_flag;        // [1] device: nonzero if some mass differs from the first
 };
 
 size_t scan_tmp_elems(int64_t len);
@@ -160,7 +162,11 @@ struct ForceLaunch {
     // kModePotential: phi_out[i] = G m_i/2 sum_j m_j phi(s_ij) (sorted order)
     float *phi_out;
     unsigned long long *within; // non-null: count pairs inside the cutoff
+    const int *mass_flag;       // from the binning pass (null: masses differ)
+    int variant = 0;            // pair-kernel variant (autotuned), 0..kForceVariants-1
 };
+
+constexpr int kForceVariants = 4;
 
 cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
                             cudaStream_t s);

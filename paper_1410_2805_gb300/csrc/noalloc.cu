@@ -127,6 +127,7 @@ extern "C" hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_spl
     fl.h_drift = 0.f;
     fl.phi_out = nullptr;
     fl.within = nullptr;
+    fl.mass_flag = b.mass_flag;
     if (sr_force_launch(g, fc, fl, ds->num_sms, s) != cudaSuccess) return HACC_ECUDA;
     return HACC_OK;
 }

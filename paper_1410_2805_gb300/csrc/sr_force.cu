@@ -58,6 +58,7 @@ struct KParams {
     float h_kick, h_drift;
     float *phi_out;
     unsigned long long *within;
+    const int *mass_flag;
 };
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -68,7 +69,34 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 // Accumulate the interaction of one staged j (already image-shifted) with
 // the K i-particles of this lane.
-template <int K, bool COUNT, bool POT, bool EPS0>
+// Accumulate a += f * r on the pairs inside the cutoff only (predicated FMAs,
+// the select of Sec. 3.1): pairs outside never touch the sums, whatever f is.
+__device__ __forceinline__ void acc_if_inside(float &ax, float &ay, float &az, float t, float T, float f, float dx,
+                                              float dy, float dz) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.lt.f32 p, %3, %4;\n\t"
+        "@p fma.rn.f32 %0, %5, %6, %0;\n\t"
+        "@p fma.rn.f32 %1, %5, %7, %1;\n\t"
+        "@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
+        : "+f"(ax), "+f"(ay), "+f"(az)
+        : "f"(t), "f"(T), "f"(f), "f"(dx), "f"(dy), "f"(dz));
+}
+
+// Same, and also skip t == 0 (with eps = 0, a pair at zero separation).
+__device__ __forceinline__ void acc_if_inside_nonzero(float &ax, float &ay, float &az, float t, float T, float f,
+                                                      float dx, float dy, float dz) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.lt.f32 p, %3, %4;\n\t"
+        "setp.gt.and.f32 p, %3, 0f00000000, p;\n\t"
+        "@p fma.rn.f32 %0, %5, %6, %0;\n\t"
+        "@p fma.rn.f32 %1, %5, %7, %1;\n\t"
+        "@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
+        : "+f"(ax), "+f"(ay), "+f"(az)
+        : "f"(t), "f"(T), "f"(f), "f"(dx), "f"(dy), "f"(dz));
+}
+
+// UM: all masses equal (the mass is applied once in the epilogue).
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM>
 __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, int iself, int lpg, const float (&xi)[K],
                                          const float (&yi)[K], const float (&zi)[K], float (&ax)[K],
                                          float (&ay)[K], float (&az)[K], unsigned &cnt) {
@@ -92,19 +120,15 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
             const bool self = jidx == iself + lpg * k;   // i's own row (sorted index)
             ax[k] += (in && !self) ? ph * pj.w : 0.0f;
         } else {
-            float r3 = r * r * r;
             float q = __fmaf_rn(P.q5, t, P.q4);
             q = __fmaf_rn(q, t, P.q3);
             q = __fmaf_rn(q, t, P.q2);
             q = __fmaf_rn(q, t, P.q1);
             q = __fmaf_rn(q, t, P.q0);
-            float fm = (r3 - q) * pj.w;
-            // with eps = 0 a pair at zero separation (i itself) would give inf * 0
-            const bool use = EPS0 ? (in && t > 0.0f) : in;
-            float fs = use ? fm : 0.0f;
-            ax[k] = __fmaf_rn(fs, dx, ax[k]);
-            ay[k] = __fmaf_rn(fs, dy, ay[k]);
-            az[k] = __fmaf_rn(fs, dz, az[k]);
+            float f = __fmaf_rn(r * r, r, -q);          // t^(-3/2) - P5
+            if (!UM) f *= pj.w;
+            if (EPS0) acc_if_inside_nonzero(ax[k], ay[k], az[k], t, P.T, f, dx, dy, dz);
+            else acc_if_inside(ax[k], ay[k], az[k], t, P.T, f, dx, dy, dz);
         }
         if (COUNT) cnt += (in && jidx != iself + lpg * k) ? 1u : 0u;   // j != i
     }
@@ -115,7 +139,7 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
 // (tx, ty, tz): image shift added to this lane's i coordinates.  The warp is
 // split into G = 2^lg lane groups; group g takes the staged entries g, g+G,
 // g+2G, ... (consecutive float4 addresses across groups: no bank conflicts).
-template <int K, bool COUNT, bool POT, bool EPS0>
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U>
 __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
                                             float ty, float tz, int iself, int lg, int grp,
                                             const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
@@ -148,16 +172,17 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
         __syncwarp();
         const int trips = (nj + G - 1) >> lg;
         int e = grp;
-        constexpr int kUnroll = K >= 3 ? 2 : 4;   // bounded by registers
+        // unroll depth: policy U = 0 deep (2 for K >= 3, else 4), U = 1 light (1 / 2)
+        constexpr int kUnroll = U == 0 ? (K >= 3 ? 2 : 4) : (K >= 3 ? 1 : 2);
 #pragma unroll kUnroll
         for (int t = 0; t < trips; ++t, e += G)
-            interact<K, COUNT, POT, EPS0>(P, buf[e], e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
+            interact<K, COUNT, POT, EPS0, UM>(P, buf[e], e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
         __syncwarp();
     }
 }
 
-template <int K, bool COUNT, bool POT, bool EPS0>
-__device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane) {
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U>
+__device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane, float m_uniform) {
     const int nc = P.nc;
     const int c = item.x, i0 = item.y, ni = item.z;
     const int lg = item.w >> 4;           // 2^lg lane groups
@@ -209,7 +234,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane)
                     ja = row[cx - 1];
                     jb = row[cx + 2];
                 }
-                process_run<K, COUNT, POT, EPS0>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, iself, lg, grp, xi, yi,
+                process_run<K, COUNT, POT, EPS0, UM, U>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, iself, lg, grp, xi, yi,
                                                  zi, ax, ay, az, cnt, buf, lane);
             }
         }
@@ -236,7 +261,8 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane)
                 P.phi_out[i] = 0.5f * P.G * mi[k] * ax[k];
                 continue;
             }
-            float gx = P.G * ax[k], gy = P.G * ay[k], gz = P.G * az[k];
+            const float gm = UM ? P.G * m_uniform : P.G;
+            float gx = gm * ax[k], gy = gm * ay[k], gz = gm * az[k];
             if (P.mode == kModeForce) {
                 int o = P.perm ? P.perm[i] : i;
                 P.out[o] = make_float4(gx, gy, gz, 0.0f);
@@ -263,11 +289,8 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane)
     }
 }
 
-template <bool COUNT, bool POT, bool EPS0>
-__global__ void __launch_bounds__(kThreads, 6) k_sr_force(KParams P) {
-    __shared__ float4 tiles[kWarps][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float4 *buf = tiles[w];
+template <bool COUNT, bool POT, bool EPS0, bool UM, int U>
+__device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lane, float m_uniform) {
     const int n_items = *P.n_items;
     while (true) {
         int it = 0;
@@ -276,23 +299,49 @@ __global__ void __launch_bounds__(kThreads, 6) k_sr_force(KParams P) {
         if (it >= n_items) break;
         int4 item = P.items[it];
         switch (item.w & 15) {
-            case 1: process_item<1, COUNT, POT, EPS0>(P, item, buf, lane); break;
-            case 2: process_item<2, COUNT, POT, EPS0>(P, item, buf, lane); break;
-            case 3: process_item<3, COUNT, POT, EPS0>(P, item, buf, lane); break;
-            default: process_item<4, COUNT, POT, EPS0>(P, item, buf, lane); break;
+            case 1: process_item<1, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
+            case 2: process_item<2, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
+            case 3: process_item<3, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
+            default: process_item<4, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
         }
     }
 }
 
-template <bool COUNT, bool POT, bool EPS0>
-cudaError_t launch_variant(const KParams &P, int num_sms, cudaStream_t s) {
+// MINB: blocks per SM the register allocation must allow (6 -> 80, 8 -> 64,
+// 5 -> 96 registers per thread); U: unroll policy.  The autotuner picks.
+template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
+__global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
+    __shared__ float4 tiles[kWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *buf = tiles[w];
+    // equal masses (flag left 0 by the binning pass): apply the mass once per i
+    if (!POT && P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
+        work_loop<COUNT, POT, EPS0, true, U>(P, buf, lane, P.pos[0].w);
+    else
+        work_loop<COUNT, POT, EPS0, false, U>(P, buf, lane, 0.0f);
+}
+
+template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
+cudaError_t launch_one(const KParams &P, int num_sms, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_force<COUNT, POT, EPS0>, kThreads, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_force<COUNT, POT, EPS0, MINB, U>, kThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_sr_force<COUNT, POT, EPS0><<<num_sms * per_sm, kThreads, 0, s>>>(P);
+    k_sr_force<COUNT, POT, EPS0, MINB, U><<<num_sms * per_sm, kThreads, 0, s>>>(P);
     note_launch();
     return cudaGetLastError();
+}
+
+// Variants 0..kForceVariants-1: (MINB, U) = (6, 0), (8, 1), (6, 1), (5, 0).
+template <bool COUNT, bool POT, bool EPS0>
+cudaError_t launch_variant(const KParams &P, int variant, int num_sms, cudaStream_t s) {
+    switch (variant) {
+        case 1: return launch_one<COUNT, POT, EPS0, 8, 1>(P, num_sms, s);
+        case 2: return launch_one<COUNT, POT, EPS0, 6, 1>(P, num_sms, s);
+        case 3: return launch_one<COUNT, POT, EPS0, 5, 0>(P, num_sms, s);
+        default: return launch_one<COUNT, POT, EPS0, 6, 0>(P, num_sms, s);
+    }
 }
 
 }  // namespace
@@ -325,12 +374,14 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.h_drift = fl.h_drift;
     P.phi_out = fl.phi_out;
     P.within = fl.within;
+    P.mass_flag = fl.mass_flag;
     const bool eps0 = !(fc.eps > 0.0f);
     const bool pot = fl.mode == kModePotential;
     const bool count = fl.within != nullptr;
-    if (pot) return eps0 ? launch_variant<false, true, true>(P, num_sms, s) : launch_variant<false, true, false>(P, num_sms, s);
-    if (count) return eps0 ? launch_variant<true, false, true>(P, num_sms, s) : launch_variant<true, false, false>(P, num_sms, s);
-    return eps0 ? launch_variant<false, false, true>(P, num_sms, s) : launch_variant<false, false, false>(P, num_sms, s);
+    const int v = fl.variant;
+    if (pot) return eps0 ? launch_one<false, true, true, 6, 0>(P, num_sms, s) : launch_one<false, true, false, 6, 0>(P, num_sms, s);
+    if (count) return eps0 ? launch_variant<true, false, true>(P, v, num_sms, s) : launch_variant<true, false, false>(P, v, num_sms, s);
+    return eps0 ? launch_variant<false, false, true>(P, v, num_sms, s) : launch_variant<false, false, false>(P, v, num_sms, s);
 }
 
 // ---- FP64 diagnostics ------------------------------------------------------

@@ -232,3 +232,19 @@ def test_diagnostics_parity(torch, hacc, ctx, split_params):
     assert np.allclose(out[:3], mom, rtol=1e-12, atol=1e-9)
     assert out[3] == pytest.approx(ke, rel=1e-12)
     assert out[4] == pytest.approx(pe, rel=1e-4)
+
+
+def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_params):
+    pos = synth.blob_mixture(20000, 28.0, seed=61)
+    p = _dev(torch, pos)
+    box = hacc.Box(L=28.0)
+    res = ctx.tune(box, split_params, p, reps=1)
+    assert 0 <= res["chosen"] < 4 and all(t > 0 for t in res["times_ms"])
+    ref = None
+    for v in range(4):
+        ctx.set_variant(v)
+        a = ctx.sr_force(box, split_params, p).clone()
+        if ref is None:
+            ref = a
+        assert torch.equal(a, ref)
+    ctx.set_variant(res["chosen"])
