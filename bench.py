@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU oracle sample time")
     ap.add_argument("--no-pm", action="store_true", help="short-range sub-cycles only (no PM half kicks)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (200 boxes) segment")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson stream) segment")
+    ap.add_argument("--served-window", type=float, default=6.0, help="seconds of arrivals in the served segment")
+    ap.add_argument("--served-cap", type=float, default=20.0, help="wall-time cap of the served segment")
     return ap.parse_args()
 
 
@@ -215,6 +219,144 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
+    """200 independent blob-mixture boxes (half uniform, half in blobs of 256,
+    sigma 0.5), N log-uniform in [16^3, 128^3], box side N^(1/3), step 0.1 as
+    10 SR sub-cycles, one batched launch per sub-cycle, all 10 captured as
+    one CUDA graph."""
+    import numpy as np
+
+    import synth
+    specs = synth.batch_boxes(200, seed=seed)
+    pos, vel, boxes, off = [], [], [], 0
+    for sp_ in specs:
+        pos.append(synth.blob_mixture_scaled(sp_.n, sp_.L, seed=sp_.seed))
+        vel.append(synth.gaussian_velocities(sp_.n, seed=sp_.seed))
+        boxes.append(hacc.BatchBox(L=sp_.L, offset=off, n=sp_.n, dt=0.1))
+        off += sp_.n
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        P = torch.from_numpy(np.concatenate(pos)).cuda()
+        V = torch.from_numpy(np.concatenate(vel)).cuda()
+        for _ in range(warmup):
+            ctx.batch_subcycle(split, boxes, P, V, n_sub, use_graph=True, stream=stream)
+        stream.synchronize()
+        snap_p, snap_v = P.clone(), V.clone()
+        ctx.stats_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.batch_subcycle(split, boxes, P, V, n_sub, use_graph=True, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = ctx.stats_read(reset=True)
+        fin_p, fin_v = P.clone(), V.clone()
+        P.copy_(snap_p)
+        V.copy_(snap_v)
+        ctx.stats_enable(counting=True)
+        for _ in range(steps):
+            ctx.batch_subcycle(split, boxes, P, V, n_sub, use_graph=True, stream=stream)
+        stream.synchronize()
+        cnt = ctx.stats_read(reset=True)
+        ctx.stats_enable(counting=False)
+        same = bool(torch.equal(P, fin_p) and torch.equal(V, fin_v))
+    ctx.sync(stream)          # raises if a coordinate left [-L, 2L)
+    n = off
+    return {"workload": "200 blob-mixture boxes, N log-uniform 16^3..128^3 (total %d), 10 SR sub-cycles per "
+                        "step, one batched launch per sub-cycle, CUDA graph" % n,
+            "pair_interactions_per_s": cnt["within_pairs"] / (ms / 1e3),
+            "particle_steps_per_s": n * n_sub * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+            "gpu_launches": st["kernel_launches"], "replay_bitwise_equal": same}
+
+
+def run_served(torch, hacc, ctx, split, rate, window, cap_s, seed=5, max_active=64 << 20, pool_gb=150.0):
+    """Poisson arrivals (rate/s over `window` s) of runs with N in {32^3, 64^3,
+    128^3, 256^3} (blob mixture, blobs of 256) and 5-50 SR sub-cycles of step
+    0.01; continuous batching (admission in
+    arrival order against the pool and a cap of particles per tick, one
+    batched sub-cycle of every resident run per tick).  Step latency = wall
+    time of the tick that advanced the run; pair counts inline (counting
+    kernel variant, slightly slower)."""
+    import collections
+
+    import numpy as np
+
+    import synth
+    reqs = synth.request_stream(rate=rate, duration=window, seed=seed)
+    templates = {}
+    for side in (32, 64, 128, 256):
+        templates[side] = (synth.blob_mixture_scaled(side ** 3, float(side), seed=seed * 7 + side),
+                           synth.gaussian_velocities(side ** 3, seed=seed * 7 + side))
+    free_b = torch.cuda.mem_get_info()[0]
+    pool = int(min(pool_gb * 1e9, free_b - 24e9))
+    srv = hacc.Server(ctx, split, pool_bytes=pool, max_active_particles=max_active)
+
+    def buffers(r):
+        side = round(r.n ** (1.0 / 3.0))
+        p0, v0 = templates[side]
+        shift = np.random.default_rng(r.seed).uniform(0, r.L, 3)
+        p = p0.copy()
+        p[:, :3] = np.mod(p[:, :3] + shift, np.float32(r.L)).astype(np.float32)
+        p[:, :3][p[:, :3] >= np.float32(r.L)] = 0
+        return p, v0.copy()
+
+    pending = collections.deque(reqs)
+    arrived = collections.deque()
+    arrival, finished_at, lat, keep = {}, {}, [], {}
+    queued = 0
+    psteps = 0
+    busy = 0.0
+    ctx.stats_read(reset=True)
+    ctx.stats_enable(counting=True)
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        if now > cap_s:
+            break
+        while pending and pending[0].t_arrival <= now:
+            r = pending.popleft()
+            arrival[r.rid] = r.t_arrival
+            arrived.append(r)
+        while arrived and queued < 2:
+            r = arrived.popleft()
+            p, v = buffers(r)
+            keep[r.rid] = (p, v)
+            srv.submit(r.rid, r.L, p, v, h=0.01, steps=r.steps)
+            queued += 1
+        if queued == 0 and not keep:
+            if not pending and not arrived:
+                break
+            time.sleep(max(0.0, min(0.01, pending[0].t_arrival - now)) if pending else 0.001)
+            continue
+        ta = time.perf_counter()
+        t = srv.tick()
+        dt = time.perf_counter() - ta
+        busy += dt
+        queued = t["queued"]
+        lat += [dt] * t["active"]
+        psteps += t["particles"]
+        tf = time.perf_counter() - t0
+        for rid in t["finished_ids"]:
+            finished_at[rid] = tf
+            keep.pop(rid, None)
+    wall = time.perf_counter() - t0
+    ctx.stats_enable(counting=False)
+    ctx.sync()                # raises if a coordinate left [-L, 2L)
+    cnt = ctx.stats_read(reset=True)
+    srv.close()
+    lat_ms = np.array(lat) * 1e3 if lat else np.zeros(1)
+    resp = np.array([finished_at[k] - arrival[k] for k in finished_at]) if finished_at else np.zeros(1)
+    return {"rate_per_s": rate, "arrival_window_s": window, "wall_s": wall, "busy_s": busy,
+            "requests_arrived": len(arrival), "requests_finished": len(finished_at),
+            "run_steps": len(lat), "p50_step_ms": float(np.percentile(lat_ms, 50)),
+            "p99_step_ms": float(np.percentile(lat_ms, 99)),
+            "p50_request_s": float(np.percentile(resp, 50)), "p99_request_s": float(np.percentile(resp, 99)),
+            "pair_interactions_per_s": cnt["within_pairs"] / max(busy, 1e-9),
+            "particle_steps_per_s": psteps / max(busy, 1e-9),
+            "max_active_particles": max_active, "pool_gb": pool / 1e9}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -355,6 +497,16 @@ def run_ours(args):
             "roofline": roofline, "e2e": e2e, "clocks": clk,
             "autotune": {"variant": tuning["chosen"], "force_ms_by_variant": tuning["times_ms"],
                          "variants": "(blocks/SM, unroll) = (6,deep), (8,light), (6,light), (5,deep)"}}
+    if not args.no_batch:
+        line["batched"] = run_batched(torch, hacc, ctx, split)
+    if not args.no_served:
+        served = run_served(torch, hacc, ctx, split, rate=50.0, window=args.served_window, cap_s=args.served_cap)
+        served["vs_plain_pairs_per_s"] = served["pair_interactions_per_s"] / (within / secs)
+        line["served"] = served
+        low = run_served(torch, hacc, ctx, split, rate=5.0, window=args.served_window, cap_s=args.served_cap,
+                         seed=6)
+        low["vs_plain_pairs_per_s"] = low["pair_interactions_per_s"] / (within / secs)
+        line["served_low_rate"] = low
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import split as osplit
         sp = osplit.default_split()

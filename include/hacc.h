@@ -189,6 +189,82 @@ hacc_status hacc_subcycle_host(hacc_ctx *ctx, const hacc_box *box, const hacc_sp
 hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                            int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
 
+/* ---- Batches of independent boxes (serving / batching mode) --------------
+ * The paper advances one domain per rank; serving many small boxes is this
+ * library's extension.  Each box is an independent periodic cube whose rows
+ * [offset, offset + n) live in shared pool arrays pos_pool / vel_pool (device,
+ * caller-owned, same row layout as above).  All boxes of a call share one
+ * binning pass and ONE persistent pair-kernel launch per sub-cycle, fed by a
+ * single work queue of (box, cell) items; results are written back to the
+ * boxes' rows, positions wrapped into [0, L).  Each box's result is bitwise
+ * the same alone or in any mix.  One split for the whole batch.
+ * Rows of different boxes must not overlap; limits: 2^31 particles and cells
+ * per call. */
+#define HACC_TICK_FIRST 1  /* this tick is the first sub-cycle of the box's run */
+#define HACC_TICK_LAST 2   /* this tick is the last sub-cycle of the box's run */
+
+typedef struct {
+    double L;        /* box side (an FP32 value) */
+    int32_t nc;      /* chaining-mesh cells per side, 0 = default */
+    int32_t flags;   /* hacc_batch_tick only: HACC_TICK_FIRST | HACC_TICK_LAST */
+    int64_t offset;  /* first row of the box in the pool arrays */
+    int64_t n;       /* rows (0: box skipped) */
+    double dt;       /* hacc_batch_subcycle: full step, split into n_sub sub-cycles;
+                        hacc_batch_tick: the sub-cycle step h */
+} hacc_batch_box;
+
+/* n_sub SKS sub-cycles (as hacc_subcycle) of every box, dt / n_sub each.
+ * use_graph != 0 captures the n_sub ticks as one CUDA graph, cached in the
+ * context and replayed while the batch's geometry, rows, pool pointers and
+ * split are unchanged (step sizes may change); the legacy default stream
+ * (NULL) cannot be captured and runs the ticks directly. */
+hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                                const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,
+                                int32_t n_sub, int32_t use_graph, hacc_stream_t stream);
+
+/* One sub-cycle of step boxes[b].dt for every box: stream h/2 first only if
+ * HACC_TICK_FIRST (earlier ticks left positions streamed by h/2), kick h,
+ * then stream h/2 if HACC_TICK_LAST, else h (fusing the next tick's opening
+ * half stream).  A run of k ticks with FIRST on the first and LAST on the
+ * last equals hacc_batch_subcycle with n_sub = k. */
+hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                            const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,
+                            hacc_stream_t stream);
+
+/* ---- Serving: continuous batching of short-range runs -------------------
+ * A server owns a device pool of `pool_bytes` (32 bytes per particle: one pos
+ * and one vel row) and queues runs (a box of n particles, sub-cycle step h,
+ * `steps` sub-cycles).  Each hacc_server_tick admits queued runs in arrival
+ * order while their rows fit in the pool (first-fit, coalescing free list)
+ * and, if max_active_particles > 0, while the particles advanced per tick stay
+ * within it; copies admitted inputs to the device; advances every resident run
+ * by one sub-cycle with hacc_batch_tick; copies finished runs back into their
+ * host arrays (in place) and releases their rows; then waits for `stream`.
+ * The host arrays passed to hacc_server_submit must stay valid until the run
+ * has finished.  Server calls must not overlap other calls on its context. */
+typedef struct hacc_server hacc_server;
+
+typedef struct {
+    int32_t admitted;   /* runs admitted this tick */
+    int32_t finished;   /* runs retired this tick */
+    int32_t active;     /* runs advanced this tick */
+    int32_t queued;     /* runs still waiting */
+    int64_t particles;  /* particles advanced this tick */
+    int64_t free_rows;  /* pool rows free after the tick */
+} hacc_server_tick_info;
+
+hacc_status hacc_server_create(hacc_server **out, hacc_ctx *ctx, const hacc_split *split, size_t pool_bytes,
+                               int64_t max_active_particles);
+void hacc_server_destroy(hacc_server *sv);
+/* Queue a run.  pos_host / vel_host: n rows each (host memory; page-locked
+ * memory copies fastest), read at admission and overwritten with the result. */
+hacc_status hacc_server_submit(hacc_server *sv, int64_t id, double L, int64_t n, float *pos_host, float *vel_host,
+                               double h, int32_t steps);
+/* One tick (see above).  finished_ids (nullable, host, finished_cap entries)
+ * receives the ids of the runs retired by this tick. */
+hacc_status hacc_server_tick(hacc_server *sv, hacc_stream_t stream, hacc_server_tick_info *info,
+                             int64_t *finished_ids, int32_t finished_cap);
+
 /* Size of the fixed device scratch behind hacc_sr_force_noalloc (16 MiB). */
 #define HACC_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 

@@ -47,6 +47,39 @@ class _Stats(ctypes.Structure):
                 ("within_pairs", ctypes.c_uint64)]
 
 
+class _BatchBox(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("nc", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("offset", ctypes.c_int64), ("n", ctypes.c_int64), ("dt", ctypes.c_double)]
+
+
+TICK_FIRST, TICK_LAST = 1, 2
+
+
+@dataclass
+class BatchBox:
+    """One box of a batch: side L, rows [offset, offset + n) of the pool
+    arrays, step dt (the full step for batch_subcycle, the sub-cycle step
+    for batch_tick), tick flags TICK_FIRST / TICK_LAST."""
+    L: float
+    offset: int
+    n: int
+    dt: float
+    nc: int = 0
+    flags: int = 0
+
+
+def _boxes_c(boxes):
+    arr = (_BatchBox * max(1, len(boxes)))()
+    for i, b in enumerate(boxes):
+        arr[i] = _BatchBox(float(b.L), int(b.nc), int(b.flags), int(b.offset), int(b.n), float(b.dt))
+    return arr
+
+
+class _TickInfo(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int32), ("finished", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("particles", ctypes.c_int64), ("free_rows", ctypes.c_int64)]
+
+
 class _Pm(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("ns", ctypes.c_int32)]
 
@@ -125,6 +158,13 @@ def lib():
             "hacc_tune": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, i32,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
             "hacc_set_variant": (st, [p, i32]),
+            "hacc_batch_subcycle": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, i32, i32,
+                                         p]),
+            "hacc_batch_tick": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, p]),
+            "hacc_server_create": (st, [ctypes.POINTER(p), p, ctypes.POINTER(_Split), ctypes.c_size_t, i64]),
+            "hacc_server_destroy": (None, [p]),
+            "hacc_server_submit": (st, [p, i64, d, i64, p, p, d, i32]),
+            "hacc_server_tick": (st, [p, p, ctypes.POINTER(_TickInfo), ctypes.POINTER(i64), i32]),
             "hacc_stats_read": (st, [p, ctypes.POINTER(_Stats), ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -213,6 +253,26 @@ class Context:
         self._check(lib().hacc_tune(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0], _ptr(pos),
                                     int(reps), times, ctypes.byref(chosen), self._stream(stream)), "hacc_tune")
         return dict(chosen=int(chosen.value), times_ms=[float(t) for t in times])
+
+    def batch_subcycle(self, split, boxes, pos_pool, vel_pool, n_sub: int, use_graph: bool = False, stream=None):
+        """n_sub SKS sub-cycles of every box of `boxes` (list of BatchBox) in one
+        batched pass per sub-cycle; use_graph captures them as a CUDA graph."""
+        _dev_rows(pos_pool, "pos_pool")
+        _dev_rows(vel_pool, "vel_pool")
+        sp = _split_of(split)
+        arr = _boxes_c(boxes)
+        self._check(lib().hacc_batch_subcycle(self._h, ctypes.byref(sp._c()), len(boxes), arr, _ptr(pos_pool),
+                                              _ptr(vel_pool), int(n_sub), int(bool(use_graph)),
+                                              self._stream(stream)), "hacc_batch_subcycle")
+
+    def batch_tick(self, split, boxes, pos_pool, vel_pool, stream=None):
+        """One sub-cycle of every box (dt = its sub-cycle step, flags TICK_FIRST/LAST)."""
+        _dev_rows(pos_pool, "pos_pool")
+        _dev_rows(vel_pool, "vel_pool")
+        sp = _split_of(split)
+        arr = _boxes_c(boxes)
+        self._check(lib().hacc_batch_tick(self._h, ctypes.byref(sp._c()), len(boxes), arr, _ptr(pos_pool),
+                                          _ptr(vel_pool), self._stream(stream)), "hacc_batch_tick")
 
     def set_variant(self, variant: int):
         self._check(lib().hacc_set_variant(self._h, int(variant)), "hacc_set_variant")
@@ -327,3 +387,44 @@ class Context:
         self._check(lib().hacc_step_host(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()),
                                          ctypes.byref(pm._c()), len(pos), self._host_ptr(pos), self._host_ptr(vel),
                                          float(dt), int(n_c), self._stream(stream)), "hacc_step_host")
+
+
+class Server:
+    """Continuous-batching server over one Context (see hacc_server_* in include/hacc.h)."""
+
+    def __init__(self, ctx: Context, split, pool_bytes: int, max_active_particles: int = 0):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        sp = _split_of(split)
+        ctx._check(lib().hacc_server_create(ctypes.byref(self._h), ctx._h, ctypes.byref(sp._c()), int(pool_bytes),
+                                            int(max_active_particles)), "hacc_server_create")
+        self._keep = {}
+        self._ids = (ctypes.c_int64 * 4096)()
+
+    def close(self):
+        if self._h:
+            lib().hacc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, rid: int, L: float, pos_host, vel_host, h: float, steps: int):
+        """Queue a run on host arrays (n, 4) float32 (numpy or pinned torch), updated in place when done."""
+        self._keep[int(rid)] = (pos_host, vel_host)
+        self.ctx._check(lib().hacc_server_submit(self._h, int(rid), float(L), len(pos_host),
+                                                 Context._host_ptr(pos_host), Context._host_ptr(vel_host),
+                                                 float(h), int(steps)), "hacc_server_submit")
+
+    def tick(self, stream=None) -> dict:
+        info = _TickInfo()
+        self.ctx._check(lib().hacc_server_tick(self._h, self.ctx._stream(stream), ctypes.byref(info), self._ids,
+                                               len(self._ids)), "hacc_server_tick")
+        done = [int(self._ids[i]) for i in range(min(info.finished, len(self._ids)))]
+        for rid in done:
+            self._keep.pop(rid, None)
+        return dict(admitted=info.admitted, finished=info.finished, active=info.active, queued=info.queued,
+                    particles=info.particles, free_rows=info.free_rows, finished_ids=done)

@@ -148,7 +148,9 @@ hacc_status ensure_io(hacc_ctx *ctx, size_t bytes, cudaStream_t s) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-hacc_status enter(hacc_ctx *ctx) {
+}  // namespace
+
+hacc_status hacc::hacc_enter(hacc_ctx *ctx) {
     if (!ctx) return HACC_EINVAL;
     ctx->last_error.clear();
     tl_launches = &ctx->launches;
@@ -156,6 +158,10 @@ hacc_status enter(hacc_ctx *ctx) {
     if (e != cudaSuccess) return check_cuda(ctx, e, "cudaSetDevice");
     return HACC_OK;
 }
+
+namespace {
+
+hacc_status enter(hacc_ctx *ctx) { return hacc_enter(ctx); }
 
 #define HACC_TRY(x)                      \
     do {                                 \
@@ -286,6 +292,7 @@ void hacc_ctx_destroy(hacc_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     pm_destroy(ctx);
+    batch_destroy(ctx);
     if (ctx->scratch.base) cudaFree(ctx->scratch.base);
     if (ctx->io_base) cudaFree(ctx->io_base);
     if (ctx->d_flags) cudaFree(ctx->d_flags);

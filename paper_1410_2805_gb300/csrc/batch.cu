@@ -1,0 +1,317 @@
+// Batches of independent boxes in one pass (the serving / batching mode).
+//
+// Every box of a batch is advanced by the same short-range SKS sub-cycle as
+// hacc_subcycle (Sec. 2.5), but all boxes share one binning pass (global cell
+// ids = the box's cell base + its local id, so one counting sort covers them
+// all) and ONE persistent pair-kernel launch whose warps take work items of
+// every box from a single atomic queue (the work queue of Sec. 3.1, one item
+// per cell or 128-particle slice of a cell).  The pair kernel writes kicked
+// and streamed particles straight back to their pool rows, wrapped.
+//
+// Within a cell the particles are ordered by pool row, and a box's items only
+// read its own cells, so each box's result is bitwise the same whether it runs
+// alone or in any mix (and whatever warp takes which item).
+//
+// hacc_batch_subcycle can capture its n_sub ticks as one CUDA graph; the per-tick
+// box tables live in device memory that the graph reads at replay, so a replay
+// with new step sizes needs no re-capture.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hacc_internal.cuh"
+
+namespace hacc {
+namespace {
+
+struct BatchWork {
+    float4 *P, *Ps, *Vs;
+    int32_t *ID, *IDs;
+    int *counter;
+    BoxDev *tables;  // n_tables x nbox
+    BinBuffers b;
+};
+
+size_t carve_batch(char *base, int64_t n, int64_t ncell, int64_t table_entries, BatchWork *w) {
+    Carver c(base);
+    w->P = c.take<float4>(n);
+    w->Ps = c.take<float4>(n);
+    w->Vs = c.take<float4>(n);
+    w->ID = c.take<int32_t>(n);
+    w->IDs = c.take<int32_t>(n);
+    w->counter = c.take<int>(1);
+    w->tables = c.take<BoxDev>(table_entries);
+    carve_bin(c, n, ncell, &w->b);
+    return c.off + 256;
+}
+
+struct Plan {
+    int nbox = 0;                 // non-empty boxes
+    int64_t n_total = 0, ncell_total = 0;
+    std::vector<BoxDev> base;     // geometry and offsets (h, pre, post filled per tick)
+};
+
+hacc_status make_plan(hacc_ctx *ctx, const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes, Plan *pl) {
+    if (nbox < 0 || (nbox > 0 && !boxes)) return set_error(ctx, HACC_EINVAL, "bad box list");
+    pl->base.clear();
+    int64_t n_total = 0, ncell_total = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const hacc_batch_box &bb = boxes[b];
+        if (bb.n < 0 || bb.offset < 0) return set_error(ctx, HACC_EINVAL, "box with negative size or offset");
+        if (bb.n == 0) continue;
+        hacc_box hb{bb.L, bb.nc, 0};
+        Geometry g;
+        HACC_STATUS_RETURN(make_geometry(ctx, &hb, split->r_cut, &g));
+        BoxDev d;
+        std::memset(&d, 0, sizeof d);
+        d.L = g.Lf;
+        d.inv_w = g.inv_w;
+        d.Ld = g.Ld;
+        d.nc = g.nc;
+        d.cell_base = (int)ncell_total;
+        d.part_base = (int)n_total;
+        d.n = (int)bb.n;
+        d.row_off = bb.offset;
+        n_total += bb.n;
+        ncell_total += g.ncell;
+        if (n_total >= ((int64_t)1 << 31) || ncell_total >= ((int64_t)1 << 31) || bb.offset + bb.n >= ((int64_t)1 << 31))
+            return set_error(ctx, HACC_EINVAL, "batch too large (2^31 particles, cells or rows)");
+        pl->base.push_back(d);
+    }
+    pl->nbox = (int)pl->base.size();
+    pl->n_total = n_total;
+    pl->ncell_total = ncell_total;
+    if (pl->nbox >= (1 << 23)) return set_error(ctx, HACC_EINVAL, "too many boxes");
+    return HACC_OK;
+}
+
+hacc_status ensure_staging(hacc_ctx *ctx, size_t bytes) {
+    if (ctx->stage_cap >= bytes) {
+        if (ctx->stage_event) cudaEventSynchronize(ctx->stage_event);  // last upload done reading it
+        return HACC_OK;
+    }
+    if (ctx->stage_event) cudaEventSynchronize(ctx->stage_event);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_cap = 0;
+    if (cudaHostAlloc(&ctx->stage, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, HACC_ENOMEM, "cudaHostAlloc of the box-table staging failed");
+    }
+    ctx->stage_cap = bytes;
+    if (!ctx->stage_event && cudaEventCreateWithFlags(&ctx->stage_event, cudaEventDisableTiming) != cudaSuccess)
+        return set_error(ctx, HACC_ECUDA, "cudaEventCreate failed");
+    return HACC_OK;
+}
+
+// One tick on the device tables `tab` (nbox entries).
+hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const BoxDev *tab, float4 *pos_pool,
+                     float4 *vel_pool, const BatchWork &w, cudaStream_t s) {
+    HACC_CUDA_RETURN(bin_build_batch(pl.nbox, tab, pl.n_total, pl.ncell_total, pos_pool, vel_pool, w.P, w.ID, w.b,
+                                     ctx->d_flags, s),
+                     "batched binning");
+    HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.b.perm, w.P, w.Ps, nullptr, nullptr, w.ID, w.IDs, s), "gather");
+    HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.IDs, vel_pool, w.Vs, nullptr, nullptr, nullptr, nullptr, s),
+                     "gather velocities");
+    ForceLaunch fl;
+    fl.pos = w.Ps;
+    fl.items = w.b.items;
+    fl.n_items = w.b.n_items;
+    fl.cell_start = w.b.cell_start;
+    fl.work_counter = w.counter;
+    fl.mode = kModeBatch;
+    fl.out = nullptr;
+    fl.perm = nullptr;
+    fl.vel = w.Vs;
+    fl.pos_next = nullptr;
+    fl.h_kick = 0.f;
+    fl.h_drift = 0.f;
+    fl.phi_out = nullptr;
+    fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
+    fl.mass_flag = w.b.mass_flag;
+    fl.variant = ctx->variant;
+    fl.boxes = tab;
+    fl.ids = w.IDs;
+    fl.pos_pool = pos_pool;
+    fl.vel_pool = vel_pool;
+    fl.flags = ctx->d_flags;
+    Geometry g;  // unused by the batched kernel (per-item geometry comes from the table)
+    g.Lf = 1.f;
+    g.Ld = 1.0;
+    g.nc = 3;
+    g.ncell = 27;
+    g.inv_w = 3.f;
+    HACC_CUDA_RETURN(sr_force_launch(g, fc, fl, ctx->num_sms, s), "batched pair force");
+    ctx->force_launches++;
+    return HACC_OK;
+}
+
+uint64_t mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+}  // namespace
+
+void batch_destroy(hacc_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->graph_exec));
+    ctx->graph_exec = nullptr;
+    if (ctx->stage_event) cudaEventSynchronize(ctx->stage_event);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_cap = 0;
+    if (ctx->stage_event) cudaEventDestroy(ctx->stage_event);
+    ctx->stage_event = nullptr;
+}
+
+}  // namespace hacc
+
+using namespace hacc;
+
+extern "C" hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                                       const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,
+                                       hacc_stream_t stream) {
+    HACC_STATUS_RETURN(hacc_enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    Plan pl;
+    HACC_STATUS_RETURN(make_plan(ctx, split, nbox, boxes, &pl));
+    if (pl.nbox == 0) return HACC_OK;
+    if (!pos_pool || !vel_pool || ((uintptr_t)pos_pool & 15u) || ((uintptr_t)vel_pool & 15u))
+        return set_error(ctx, HACC_EINVAL, "pool arrays NULL or not 16-byte aligned");
+    Geometry g0;  // the force constants do not depend on the box
+    g0.Lf = pl.base[0].L;
+    g0.Ld = pl.base[0].Ld;
+    g0.nc = pl.base[0].nc;
+    g0.ncell = (int64_t)g0.nc * g0.nc * g0.nc;
+    g0.inv_w = pl.base[0].inv_w;
+    ForceConsts fc;
+    HACC_STATUS_RETURN(make_force_consts(ctx, split, g0, &fc));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BatchWork w;
+    size_t need = carve_batch(nullptr, pl.n_total, pl.ncell_total, pl.nbox, &w);
+    HACC_STATUS_RETURN(ensure_scratch(ctx, need, s));
+    carve_batch(ctx->scratch.base, pl.n_total, pl.ncell_total, pl.nbox, &w);
+    HACC_STATUS_RETURN(ensure_staging(ctx, sizeof(BoxDev) * pl.nbox));
+    BoxDev *st = static_cast<BoxDev *>(ctx->stage);
+    for (int b = 0, k = 0; b < nbox; ++b) {
+        if (boxes[b].n == 0) continue;
+        BoxDev d = pl.base[k];
+        const float h = (float)boxes[b].dt;
+        d.h = h;
+        d.pre = (boxes[b].flags & HACC_TICK_FIRST) ? 0.5f * h : 0.0f;
+        d.post = (boxes[b].flags & HACC_TICK_LAST) ? 0.5f * h : h;
+        st[k++] = d;
+    }
+    HACC_CUDA_RETURN(cudaMemcpyAsync(w.tables, st, sizeof(BoxDev) * pl.nbox, cudaMemcpyHostToDevice, s),
+                     "box table upload");
+    HACC_CUDA_RETURN(cudaEventRecord(ctx->stage_event, s), "cudaEventRecord");
+    return run_tick(ctx, fc, pl, w.tables, reinterpret_cast<float4 *>(pos_pool), reinterpret_cast<float4 *>(vel_pool),
+                    w, s);
+}
+
+extern "C" hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                                           const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,
+                                           int32_t n_sub, int32_t use_graph, hacc_stream_t stream) {
+    HACC_STATUS_RETURN(hacc_enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (n_sub < 1) return set_error(ctx, HACC_EINVAL, "n_sub must be >= 1");
+    Plan pl;
+    HACC_STATUS_RETURN(make_plan(ctx, split, nbox, boxes, &pl));
+    if (pl.nbox == 0) return HACC_OK;
+    if (!pos_pool || !vel_pool || ((uintptr_t)pos_pool & 15u) || ((uintptr_t)vel_pool & 15u))
+        return set_error(ctx, HACC_EINVAL, "pool arrays NULL or not 16-byte aligned");
+    for (int b = 0; b < nbox; ++b)
+        if (!std::isfinite(boxes[b].dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
+    Geometry g0;  // the force constants do not depend on the box
+    g0.Lf = pl.base[0].L;
+    g0.Ld = pl.base[0].Ld;
+    g0.nc = pl.base[0].nc;
+    g0.ncell = (int64_t)g0.nc * g0.nc * g0.nc;
+    g0.inv_w = pl.base[0].inv_w;
+    ForceConsts fc;
+    HACC_STATUS_RETURN(make_force_consts(ctx, split, g0, &fc));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t entries = (int64_t)pl.nbox * n_sub;
+    BatchWork w;
+    size_t need = carve_batch(nullptr, pl.n_total, pl.ncell_total, entries, &w);
+    HACC_STATUS_RETURN(ensure_scratch(ctx, need, s));
+    carve_batch(ctx->scratch.base, pl.n_total, pl.ncell_total, entries, &w);
+    // per-tick tables: SKS with the outer half streams fused into the binning
+    // of the first tick and the epilogue of the last
+    HACC_STATUS_RETURN(ensure_staging(ctx, sizeof(BoxDev) * entries));
+    BoxDev *st = static_cast<BoxDev *>(ctx->stage);
+    for (int k = 0; k < n_sub; ++k)
+        for (int b = 0, q = 0; b < nbox; ++b) {
+            if (boxes[b].n == 0) continue;
+            BoxDev d = pl.base[q];
+            const float h = (float)(boxes[b].dt / n_sub);
+            d.h = h;
+            d.pre = k == 0 ? 0.5f * h : 0.0f;
+            d.post = k == n_sub - 1 ? 0.5f * h : h;
+            st[(int64_t)k * pl.nbox + q++] = d;
+        }
+    HACC_CUDA_RETURN(cudaMemcpyAsync(w.tables, st, sizeof(BoxDev) * entries, cudaMemcpyHostToDevice, s),
+                     "box table upload");
+    HACC_CUDA_RETURN(cudaEventRecord(ctx->stage_event, s), "cudaEventRecord");
+    float4 *pp = reinterpret_cast<float4 *>(pos_pool);
+    float4 *vp = reinterpret_cast<float4 *>(vel_pool);
+    // the legacy default stream cannot be captured: run directly there
+    if (!use_graph || s == nullptr) {
+        for (int k = 0; k < n_sub; ++k)
+            HACC_STATUS_RETURN(run_tick(ctx, fc, pl, w.tables + (int64_t)k * pl.nbox, pp, vp, w, s));
+        return HACC_OK;
+    }
+    uint64_t key = 0x51ed27ull;
+    key = mix(key, (uint64_t)pl.nbox);
+    key = mix(key, (uint64_t)n_sub);
+    for (const BoxDev &d : pl.base) {
+        uint32_t lb;
+        std::memcpy(&lb, &d.L, 4);
+        key = mix(key, lb);
+        key = mix(key, (uint64_t)d.nc);
+        key = mix(key, (uint64_t)d.n);
+        key = mix(key, (uint64_t)d.row_off);
+    }
+    uint32_t fcb[sizeof(ForceConsts) / 4];
+    std::memcpy(fcb, &fc, sizeof fcb);
+    for (uint32_t v : fcb) key = mix(key, v);
+    key = mix(key, (uint64_t)(uintptr_t)pp);
+    key = mix(key, (uint64_t)(uintptr_t)vp);
+    key = mix(key, (uint64_t)(uintptr_t)ctx->scratch.base);
+    key = mix(key, (uint64_t)ctx->variant);
+    key = mix(key, (uint64_t)ctx->counting);
+    key = mix(key, (uint64_t)(uintptr_t)s);
+    if (!ctx->graph_exec || ctx->graph_key != key) {
+        if (ctx->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->graph_exec));
+        ctx->graph_exec = nullptr;
+        const int64_t launches0 = ctx->launches, forces0 = ctx->force_launches;
+        HACC_CUDA_RETURN(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        hacc_status r = HACC_OK;
+        for (int k = 0; k < n_sub && r == HACC_OK; ++k)
+            r = run_tick(ctx, fc, pl, w.tables + (int64_t)k * pl.nbox, pp, vp, w, s);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (r != HACC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (ce != cudaSuccess) return check_cuda(ctx, ce, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return check_cuda(ctx, ce, "cudaGraphInstantiate");
+        ctx->graph_exec = exec;
+        ctx->graph_key = key;
+        ctx->graph_launches = ctx->launches - launches0;
+        ctx->graph_forces = ctx->force_launches - forces0;
+        ctx->launches = launches0;
+        ctx->force_launches = forces0;
+    }
+    HACC_CUDA_RETURN(cudaGraphLaunch(static_cast<cudaGraphExec_t>(ctx->graph_exec), s), "cudaGraphLaunch");
+    ctx->launches += ctx->graph_launches;
+    ctx->force_launches += ctx->graph_forces;
+    return HACC_OK;
+}

@@ -20,21 +20,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Wrap one FP32 coordinate into [0, L): x<0 -> x+L, x>=L -> x-L, a sum that
-// rounds to L becomes 0.  Returns false (and leaves 0) outside [-L, 2L).
-__device__ __forceinline__ bool wrap1(float &x, float Lf) {
-    float v = x;
-    if (!(v >= -Lf && v < 2.0f * Lf)) {
-        x = 0.0f;
-        return false;
-    }
-    if (v < 0.0f) v = __fadd_rn(v, Lf);
-    else if (v >= Lf) v = __fsub_rn(v, Lf);
-    if (v >= Lf) v = 0.0f;
-    x = v;
-    return true;
-}
-
 // Largest k with k*L <= x*nc, for x in [0, L).  The FP32 product is within
 // 2e-4 of the exact quotient for nc <= 1024, so away from a cell face its
 // floor is exact; near a face the decision is made with exact FP64 products
@@ -201,15 +186,23 @@ __global__ void __launch_bounds__(kBlock) k_place(int64_t n, const int32_t *__re
 // One warp per cell: the arrival order from the atomics is arbitrary, so each
 // element's final slot is the number of smaller input rows in its cell (the
 // rows are distinct), which gives ascending input row within the cell.
+// Cells of more than kBigCell particles go to a list sorted by k_order_big.
+constexpr uint32_t kBigCell = 512;
+
 __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t *__restrict__ count,
                                                    const unsigned long long *__restrict__ packed,
                                                    const int32_t *__restrict__ perm_tmp,
-                                                   int32_t *__restrict__ perm) {
+                                                   int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
+                                                   int *__restrict__ big_count) {
     int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (c >= ncell) return;
     uint32_t cnt = count[c];
     if (cnt == 0) return;
+    if (cnt > kBigCell) {
+        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)c;
+        return;
+    }
     uint32_t s = (uint32_t)(packed[c] & 0xffffffffull);
     const int32_t *seg = perm_tmp + s;
     if (cnt <= 32) {
@@ -230,10 +223,82 @@ __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t 
     }
 }
 
+// Big cells, one block per cell (grid-stride over the list): sort chunks of
+// kChunk input rows with a shared-memory bitonic network, then merge runs of
+// doubling width between the two segment buffers, each output element placed
+// by its merge-path co-rank.  O(m log^2 m) work per cell of m particles.
+constexpr int kOrderThreads = 1024;
+constexpr int kChunk = 2048;
+
+__global__ void __launch_bounds__(kOrderThreads) k_order_big(const uint32_t *__restrict__ count,
+                                                              const unsigned long long *__restrict__ packed,
+                                                              int32_t *__restrict__ perm_tmp,
+                                                              int32_t *__restrict__ perm,
+                                                              const int32_t *__restrict__ big_list,
+                                                              const int *__restrict__ big_count) {
+    __shared__ int32_t sh[kChunk];
+    const int nbig = *big_count;
+    const int tid = threadIdx.x;
+    for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+        const int32_t c = big_list[q];
+        const int m = (int)count[c];
+        const uint32_t s = (uint32_t)(packed[c] & 0xffffffffull);
+        int32_t *A = perm_tmp + s, *B = perm + s;
+        // 1. sorted chunks, in place in A
+        for (int base = 0; base < m; base += kChunk) {
+            for (int t = tid; t < kChunk; t += kOrderThreads) sh[t] = base + t < m ? A[base + t] : 0x7fffffff;
+            __syncthreads();
+            for (int k = 2; k <= kChunk; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int t = tid; t < kChunk; t += kOrderThreads) {
+                        int o = t ^ j;
+                        if (o > t) {
+                            int32_t a = sh[t], b = sh[o];
+                            if ((a > b) == ((t & k) == 0)) {
+                                sh[t] = b;
+                                sh[o] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            for (int t = tid; t < kChunk && base + t < m; t += kOrderThreads) A[base + t] = sh[t];
+            __syncthreads();
+        }
+        // 2. merge passes, ping-pong A <-> B
+        int32_t *src = A, *dst = B;
+        for (int width = kChunk; width < m; width <<= 1) {
+            for (int k = tid; k < m; k += kOrderThreads) {
+                const int base = (k / (2 * width)) * (2 * width);
+                const int lenA = min(width, m - base);
+                const int lenB = max(0, min(width, m - base - width));
+                const int32_t *a = src + base, *b = src + base + width;
+                const int qk = k - base;
+                int lo = max(0, qk - lenB), hi = min(qk, lenA);
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (a[mid] < b[qk - mid - 1]) lo = mid + 1;
+                    else hi = mid;
+                }
+                const int i = lo, j = qk - lo;
+                dst[k] = (i < lenA && (j >= lenB || a[i] < b[j])) ? a[i] : b[j];
+            }
+            __syncthreads();
+            int32_t *tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+        if (src != B)
+            for (int t = tid; t < m; t += kOrderThreads) B[t] = src[t];
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, const uint32_t *__restrict__ count,
                                                    const unsigned long long *__restrict__ packed,
                                                    int32_t *__restrict__ cell_start, int4 *__restrict__ items,
-                                                   int32_t *__restrict__ n_items, int make_items) {
+                                                   int32_t *__restrict__ n_items, int make_items,
+                                                   const BoxDev *__restrict__ boxes, int nbox) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) {
         cell_start[ncell] = (int32_t)n;
@@ -250,12 +315,60 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
     uint32_t cnt = count[c];
     uint32_t it = (uint32_t)(p >> 32);
     if (cnt == 0) return;
+    int box = 0;
+    if (boxes) {  // last box whose first cell is <= c
+        int lo = 0, hi = nbox - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (boxes[mid].cell_base <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        box = lo;
+    }
     uint32_t m = items_of(cnt);
     for (uint32_t q = 0; q < m; ++q) {
         uint32_t ni = cnt - q * kItemMax;
         ni = ni > (uint32_t)kItemMax ? (uint32_t)kItemMax : ni;
-        items[it + q] = make_int4((int)c, (int)(s + q * kItemMax), (int)ni, item_shape(ni));
+        items[it + q] = make_int4((int)c, (int)(s + q * kItemMax), (int)ni, (box << 8) | item_shape(ni));
     }
+}
+
+// Batched key pass: box of scratch index t by binary search over part_base.
+__global__ void __launch_bounds__(kBlock) k_bkey(int64_t n_total, int nbox, const BoxDev *__restrict__ boxes,
+                                                  const float4 *__restrict__ pos_pool,
+                                                  const float4 *__restrict__ vel_pool, float4 *__restrict__ dst,
+                                                  int32_t *__restrict__ id, int32_t *__restrict__ key,
+                                                  int32_t *__restrict__ rank, uint32_t *__restrict__ count, int *flags,
+                                                  int *mass_flag) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_total) return;
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].part_base <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const BoxDev bx = boxes[lo];
+    const long long row = bx.row_off + (t - bx.part_base);
+    float4 p = pos_pool[row];
+    if (bx.pre != 0.0f) {
+        float4 v = vel_pool[row];
+        p.x = __fmaf_rn(bx.pre, v.x, p.x);
+        p.y = __fmaf_rn(bx.pre, v.y, p.y);
+        p.z = __fmaf_rn(bx.pre, v.z, p.z);
+    }
+    bool ok = wrap1(p.x, bx.L);
+    ok &= wrap1(p.y, bx.L);
+    ok &= wrap1(p.z, bx.L);
+    if (!ok) atomicOr(flags, kFlagDomain);
+    if (p.w != pos_pool[boxes[0].row_off].w) atomicOr(mass_flag, 1);
+    const int nc = bx.nc;
+    int cx = cell1(p.x, bx.inv_w, bx.Ld, nc), cy = cell1(p.y, bx.inv_w, bx.Ld, nc), cz = cell1(p.z, bx.inv_w, bx.Ld, nc);
+    int32_t c = bx.cell_base + (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
+    dst[t] = p;
+    id[t] = (int32_t)row;
+    key[t] = c;
+    rank[t] = (int32_t)atomicAdd(&count[c], 1u);
 }
 
 __global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__restrict__ perm,
@@ -347,7 +460,40 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
     b->items = c.take<int4>(max_items(n, ncell));
     b->n_items = c.take<int32_t>(1);
     b->mass_flag = c.take<int>(1);
+    b->big_list = c.take<int32_t>(n / (kBigCell + 1) + 1);
+    b->big_count = c.take<int>(1);
 }
+
+namespace {
+// Counting sort by key and work items, shared by the single-box and batched passes.
+cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_items, const BoxDev *boxes, int nbox,
+                     cudaStream_t s) {
+    cudaError_t e;
+    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, b.packed);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(b.packed, ncell, b.scan_tmp, s)) != cudaSuccess) return e;
+    if (n > 0) {
+        k_place<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, b.rank, b.packed, b.perm_tmp);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(b.big_count, 0, sizeof(int), s)) != cudaSuccess) return e;
+        k_order<<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list,
+                                                          b.big_count);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (n > (int64_t)kBigCell) {
+            k_order_big<<<256, kOrderThreads, 0, s>>>(b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count);
+            note_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    k_items<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items,
+                                                 make_items ? 1 : 0, boxes, nbox);
+    note_launch();
+    return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s) {
@@ -360,22 +506,22 @@ cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const flo
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_pack<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, b.count, b.packed);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = scan_exclusive(b.packed, g.ncell, b.scan_tmp, s)) != cudaSuccess) return e;
-    if (n > 0) {
-        k_place<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, b.rank, b.packed, b.perm_tmp);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_order<<<blocks_for(g.ncell * 32), kBlock, 0, s>>>(g.ncell, b.count, b.packed, b.perm_tmp, b.perm);
+    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s);
+}
+
+cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int64_t ncell_total,
+                            const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
+                            const BinBuffers &b, int *d_flags, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * ncell_total, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if (n_total > 0) {
+        k_bkey<<<blocks_for(n_total), kBlock, 0, s>>>(n_total, nbox, boxes, pos_pool, vel_pool, dst, id, b.key,
+                                                      b.rank, b.count, d_flags, b.mass_flag);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_items<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, n, b.count, b.packed, b.cell_start, b.items,
-                                                   b.n_items, make_items ? 1 : 0);
-    note_launch();
-    return cudaGetLastError();
+    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s);
 }
 
 cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, const float4 *v_in,

@@ -51,6 +51,13 @@ struct hacc_ctx {
     double force_ms = 0.0;
     unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+    // batches (batch.cu): pinned staging of box tables, cached CUDA graph
+    void *stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t stage_event = nullptr;
+    void *graph_exec = nullptr;
+    uint64_t graph_key = 0;
+    int64_t graph_launches = 0, graph_forces = 0;
 };
 
 namespace hacc {
@@ -77,6 +84,19 @@ inline void note_launch(int k = 1) {
 }
 
 hacc_status set_error(hacc_ctx *ctx, hacc_status st, const std::string &msg);
+
+// Start of every entry point on a context: clear the message, make the
+// context's device current, count kernel launches into the context.
+hacc_status hacc_enter(hacc_ctx *ctx);
+
+#define HACC_STATUS_RETURN(x)                 \
+    do {                                      \
+        hacc_status st_r_ = (x);              \
+        if (st_r_ != HACC_OK) return st_r_;   \
+    } while (0)
+#define HACC_CUDA_RETURN(x, what) HACC_STATUS_RETURN(::hacc::check_cuda(ctx, (x), what))
+
+void batch_destroy(hacc_ctx *ctx);
 hacc_status check_cuda(hacc_ctx *ctx, cudaError_t e, const char *what);
 hacc_status ensure_scratch(hacc_ctx *ctx, size_t bytes, cudaStream_t stream);
 
@@ -103,6 +123,38 @@ struct ForceConsts {
 
 hacc_status make_force_consts(hacc_ctx *ctx, const hacc_split *split, const Geometry &g, ForceConsts *fc);
 
+// Wrap one FP32 coordinate into [0, L): x<0 -> x+L, x>=L -> x-L, a sum that
+// rounds to L becomes 0.  Returns false (and leaves 0) outside [-L, 2L).
+__device__ __forceinline__ bool wrap1(float &x, float Lf) {
+    float v = x;
+    if (!(v >= -Lf && v < 2.0f * Lf)) {
+        x = 0.0f;
+        return false;
+    }
+    if (v < 0.0f) v = __fadd_rn(v, Lf);
+    else if (v >= Lf) v = __fsub_rn(v, Lf);
+    if (v >= Lf) v = 0.0f;
+    x = v;
+    return true;
+}
+
+// ---- batches of boxes (batch.cu) -----------------------------------------
+// One box of a batched tick, as the kernels see it.
+struct BoxDev {
+    float L;             // side (FP32 value)
+    float inv_w;         // fl(nc / L)
+    double Ld;           // side in FP64 (same value)
+    int nc;              // chaining-mesh cells per side
+    int cell_base;       // first global cell id of this box
+    int part_base;       // first tick-scratch index of this box
+    int n;               // particles
+    long long row_off;   // first row of this box in the pool arrays
+    float h;             // kick factor of this tick
+    float pre;           // stream applied before binning (h/2 on a run's first sub-cycle, else 0)
+    float post;          // stream after the kick (h, or h/2 on a run's last sub-cycle)
+    float pad;
+};
+
 // ---- binning (bin.cu) ----------------------------------------------------
 struct BinBuffers {
     int32_t *key;          // [n]
@@ -117,6 +169,8 @@ struct BinBuffers {
     int4 *items;           // [max_items]
     int32_t *n_items;      // [1] device
     int *mass_flag;        // [1] device: nonzero if some mass differs from the first
+    int32_t *big_list;     // cells too large for the warp-level ordering
+    int *big_count;
 };
 
 size_t scan_tmp_elems(int64_t len);
@@ -128,6 +182,15 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b);
 // vel may be null (no drift).  dst may equal src.
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s);
+
+// Batched binning of nbox boxes (table `boxes` on the device, ascending
+// part_base and cell_base): for every tick-scratch index t the particle at
+// pool row boxes[b].row_off + t - part_base is streamed by pre, wrapped,
+// binned into global cell cell_base + local id; dst[t] = its position,
+// id[t] = its pool row.  Work items carry the box in item.w >> 8.
+cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int64_t ncell_total,
+                            const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
+                            const BinBuffers &b, int *d_flags, cudaStream_t s);
 
 // Gather rows into sorted order: out[k] = in[perm[k]] for float4, int ids.
 cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out,
@@ -143,7 +206,7 @@ cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsign
                             cudaStream_t s);
 
 // ---- pair force (sr_force.cu) -------------------------------------------
-enum ForceMode : int { kModeForce = 0, kModeKickDrift = 1, kModePotential = 2 };
+enum ForceMode : int { kModeForce = 0, kModeKickDrift = 1, kModePotential = 2, kModeBatch = 3 };
 
 struct ForceLaunch {
     const float4 *pos;          // sorted, wrapped
@@ -163,6 +226,12 @@ struct ForceLaunch {
     float *phi_out;
     unsigned long long *within; // non-null: count pairs inside the cutoff
     const int *mass_flag;       // from the binning pass (null: masses differ)
+    // kModeBatch: geometry and kick/stream factors per box, write-back to the pool
+    const BoxDev *boxes = nullptr;
+    const int32_t *ids = nullptr;     // pool row of each sorted particle
+    float4 *pos_pool = nullptr;
+    float4 *vel_pool = nullptr;
+    int *flags = nullptr;             // device status word (wrap errors)
     int variant = 0;            // pair-kernel variant (autotuned), 0..kForceVariants-1
 };
 

@@ -59,6 +59,11 @@ struct KParams {
     float *phi_out;
     unsigned long long *within;
     const int *mass_flag;
+    const BoxDev *boxes;
+    const int32_t *ids;
+    float4 *pos_pool;
+    float4 *vel_pool;
+    int *flags;
 };
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -183,14 +188,25 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
 
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U>
 __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane, float m_uniform) {
-    const int nc = P.nc;
-    const int c = item.x, i0 = item.y, ni = item.z;
-    const int lg = item.w >> 4;           // 2^lg lane groups
+    // geometry: the single box of the call, or this item's box of a batch
+    int nc = P.nc;
+    float L = P.L;
+    int cbase = 0;
+    float h_kick = P.h_kick, h_drift = P.h_drift;
+    if (P.boxes) {
+        const BoxDev &bx = P.boxes[item.w >> 8];
+        nc = bx.nc;
+        L = bx.L;
+        cbase = bx.cell_base;
+        h_kick = bx.h;
+        h_drift = bx.post;
+    }
+    const int c = item.x - cbase, i0 = item.y, ni = item.z;
+    const int lg = (item.w >> 4) & 15;    // 2^lg lane groups
     const int lpg = 32 >> lg;             // lanes per group
     const int grp = lane >> (5 - lg);
     const int slot = lane & (lpg - 1);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-    const float L = P.L;
 
     // every group holds the same K x lpg particles of the cell
     float xi[K], yi[K], zi[K], mi[K];
@@ -215,7 +231,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
             float sjy = 0.0f, siy = 0.0f;
             if (ry < 0) { ry += nc; sjy = -L; }
             else if (ry >= nc) { ry -= nc; siy = -L; }
-            const int32_t *row = P.cell_start + (rz * nc + ry) * nc;
+            const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
             // cells (cx-1, cx, cx+1) of this row: one run, or two when it wraps in x
             const int nruns = (cx == 0 || cx == nc - 1) ? 2 : 1;
 #pragma unroll 1
@@ -268,16 +284,27 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
                 P.out[o] = make_float4(gx, gy, gz, 0.0f);
             } else {
                 float4 v = P.vel[i];
-                v.x = __fmaf_rn(P.h_kick, gx, v.x);
-                v.y = __fmaf_rn(P.h_kick, gy, v.y);
-                v.z = __fmaf_rn(P.h_kick, gz, v.z);
-                P.vel[i] = v;
+                v.x = __fmaf_rn(h_kick, gx, v.x);
+                v.y = __fmaf_rn(h_kick, gy, v.y);
+                v.z = __fmaf_rn(h_kick, gz, v.z);
                 float4 p;
-                p.x = __fmaf_rn(P.h_drift, v.x, xi[k]);
-                p.y = __fmaf_rn(P.h_drift, v.y, yi[k]);
-                p.z = __fmaf_rn(P.h_drift, v.z, zi[k]);
+                p.x = __fmaf_rn(h_drift, v.x, xi[k]);
+                p.y = __fmaf_rn(h_drift, v.y, yi[k]);
+                p.z = __fmaf_rn(h_drift, v.z, zi[k]);
                 p.w = mi[k];
-                P.pos_next[i] = p;
+                if (P.mode == kModeBatch) {
+                    // back to the box's pool row, wrapped into [0, L)
+                    bool ok = wrap1(p.x, L);
+                    ok &= wrap1(p.y, L);
+                    ok &= wrap1(p.z, L);
+                    if (!ok) atomicOr(P.flags, kFlagDomain);
+                    const int row = P.ids[i];
+                    P.vel_pool[row] = v;
+                    P.pos_pool[row] = p;
+                } else {
+                    P.vel[i] = v;
+                    P.pos_next[i] = p;
+                }
             }
         }
     }
@@ -375,6 +402,11 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.phi_out = fl.phi_out;
     P.within = fl.within;
     P.mass_flag = fl.mass_flag;
+    P.boxes = fl.boxes;
+    P.ids = fl.ids;
+    P.pos_pool = fl.pos_pool;
+    P.vel_pool = fl.vel_pool;
+    P.flags = fl.flags;
     const bool eps0 = !(fc.eps > 0.0f);
     const bool pot = fl.mode == kModePotential;
     const bool count = fl.within != nullptr;

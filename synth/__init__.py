@@ -68,6 +68,13 @@ def blob_mixture(n: int, L: float, seed: int, n_blobs: int = 64, sigma: float = 
     return as_pos4(_wrap_f32(x, L))
 
 
+def blob_mixture_scaled(n: int, L: float, seed: int, per_blob: int = 256, sigma: float = 0.5) -> np.ndarray:
+    """The 32^3 blob mixture's statistics at any n: half uniform, half in
+    Gaussian blobs of `per_blob` particles (n_blobs = n / (2 per_blob), at
+    least 1), so that blob density does not grow with the box."""
+    return blob_mixture(n, L, seed, n_blobs=max(1, int(round(n / (2.0 * per_blob)))), sigma=sigma)
+
+
 def gaussian_velocities(n: int, seed: int, sigma: float = 0.1) -> np.ndarray:
     """n x 4 FP32 velocities, each component N(0, sigma^2), w = 0."""
     g = _rng(seed + 0x5eed)

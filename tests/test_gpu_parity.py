@@ -248,3 +248,11 @@ def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_para
             ref = a
         assert torch.equal(a, ref)
     ctx.set_variant(res["chosen"])
+
+
+def test_bin_crowded_cells_bit_exact(torch, hacc, ctx, split_params):
+    # cells of several thousand particles take the block-level chunk + merge ordering
+    pos = synth.blob_mixture(30000, 24.0, seed=71, n_blobs=3, sigma=0.3)
+    _check_bin(torch, hacc, ctx, pos, 24.0, np.float32(split_params["r_cut"]))
+    _, cell_o, _ = oracle.wrap_cell(pos, 24.0, hacc.mesh_cells(24.0, np.float32(split_params["r_cut"])))
+    assert np.bincount(cell_o).max() > 4096
