@@ -189,6 +189,28 @@ hacc_status hacc_subcycle_host(hacc_ctx *ctx, const hacc_box *box, const hacc_sp
 hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                            int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
 
+/* ---- Precision variant: positions as (cell, in-cell offset) --------------
+ * The paper's runs keep absolute positions in single precision; at box sides
+ * of hundreds of cells FP32 rounds positions to ~3e-5 cells and every stream
+ * adds that much again.  Here a position is stored as the int32 chaining-mesh
+ * cell id of the box (nc from the box, as for hacc_bin) plus an FP32 offset in
+ * [-w/2, w/2] from the cell's centre (w = L/nc), with the mass as the fourth float
+ * of off_m: resolution ~1e-7 cells at any L.  Pair arithmetic and accumulation
+ * stay FP32 (a j's offset is moved into i's cell frame by whole cell steps);
+ * FP64 is used only inside the stream, on the global position c w + off.
+ * pos64: n x 3 doubles (x, y, z); mass: n floats or NULL (all 1). */
+hacc_status hacc_ci_from_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, const double *pos64,
+                             const float *mass, int32_t *cell, float *off_m, hacc_stream_t stream);
+hacc_status hacc_ci_to_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, const int32_t *cell,
+                           const float *off_m, double *pos64, hacc_stream_t stream);
+/* Eq. (force) as hacc_sr_force, from (cell, offset) positions; acc in input order. */
+hacc_status hacc_sr_force_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                             const int32_t *cell, const float *off_m, float *acc, hacc_stream_t stream);
+/* SKS sub-cycles as hacc_subcycle on (cell, offset) positions, updated in place
+ * (streams in FP64, kicks in FP32). */
+hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, int32_t *cell,
+                             float *off_m, float *vel, double dt, int32_t n_sub, hacc_stream_t stream);
+
 /* ---- Batches of independent boxes (serving / batching mode) --------------
  * The paper advances one domain per rank; serving many small boxes is this
  * library's extension.  Each box is an independent periodic cube whose rows

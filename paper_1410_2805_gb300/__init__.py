@@ -155,6 +155,10 @@ def lib():
             "hacc_step_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), ctypes.POINTER(_Pm), i64, p,
                                     p, d, i32, p]),
             "hacc_stats_enable": (st, [p, ctypes.c_int, ctypes.c_int]),
+            "hacc_ci_from_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p, p]),
+            "hacc_ci_to_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p]),
+            "hacc_sr_force_ci": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, p]),
+            "hacc_subcycle_ci": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, d, i32, p]),
             "hacc_tune": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, i32,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
             "hacc_set_variant": (st, [p, i32]),
@@ -273,6 +277,41 @@ class Context:
         arr = _boxes_c(boxes)
         self._check(lib().hacc_batch_tick(self._h, ctypes.byref(sp._c()), len(boxes), arr, _ptr(pos_pool),
                                           _ptr(vel_pool), self._stream(stream)), "hacc_batch_tick")
+
+    # ---- precision variant: positions as (cell id, FP32 in-cell offset) -----
+    def ci_from_f64(self, box: Box, r_cut: float, pos64, mass=None, stream=None):
+        """(n, 3) float64 CUDA positions -> (cell int32 (n,), off_m float32 (n, 4))."""
+        import torch
+        assert pos64.is_cuda and pos64.dtype == torch.float64 and pos64.is_contiguous() and pos64.shape[1] == 3
+        n = pos64.shape[0]
+        cell = torch.empty(n, dtype=torch.int32, device=pos64.device)
+        off = torch.empty((n, 4), dtype=torch.float32, device=pos64.device)
+        self._check(lib().hacc_ci_from_f64(self._h, ctypes.byref(box._c()), float(r_cut), n, _ptr(pos64),
+                                           _ptr(mass), _ptr(cell), _ptr(off), self._stream(stream)),
+                    "hacc_ci_from_f64")
+        return cell, off
+
+    def ci_to_f64(self, box: Box, r_cut: float, cell, off, stream=None):
+        import torch
+        out = torch.empty((cell.shape[0], 3), dtype=torch.float64, device=cell.device)
+        self._check(lib().hacc_ci_to_f64(self._h, ctypes.byref(box._c()), float(r_cut), cell.shape[0], _ptr(cell),
+                                         _ptr(off), _ptr(out), self._stream(stream)), "hacc_ci_to_f64")
+        return out
+
+    def sr_force_ci(self, box: Box, split, cell, off, stream=None):
+        import torch
+        sp = _split_of(split)
+        acc = torch.empty_like(off)
+        self._check(lib().hacc_sr_force_ci(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), cell.shape[0],
+                                           _ptr(cell), _ptr(off), _ptr(acc), self._stream(stream)),
+                    "hacc_sr_force_ci")
+        return acc
+
+    def subcycle_ci(self, box: Box, split, cell, off, vel, dt: float, n_sub: int, stream=None):
+        sp = _split_of(split)
+        self._check(lib().hacc_subcycle_ci(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), cell.shape[0],
+                                           _ptr(cell), _ptr(off), _ptr(vel), float(dt), int(n_sub),
+                                           self._stream(stream)), "hacc_subcycle_ci")
 
     def set_variant(self, variant: int):
         self._check(lib().hacc_set_variant(self._h, int(variant)), "hacc_set_variant")

@@ -515,6 +515,114 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
     return HACC_OK;
 }
 
+hacc_status hacc_ci_from_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, const double *pos64,
+                             const float *mass, int32_t *cell, float *off_m, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, r_cut, &g));
+    HACC_TRY(check_particles(ctx, n, off_m, nullptr));
+    if (n > 0 && (!pos64 || !cell)) return set_error(ctx, HACC_EINVAL, "pos64 or cell is NULL");
+    HACC_CUDA(ci_from_f64(g, n, pos64, mass, cell, reinterpret_cast<float4 *>(off_m), ctx->d_flags,
+                          reinterpret_cast<cudaStream_t>(stream)),
+              "cell/offset split");
+    return HACC_OK;
+}
+
+hacc_status hacc_ci_to_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, const int32_t *cell,
+                           const float *off_m, double *pos64, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, r_cut, &g));
+    HACC_TRY(check_particles(ctx, n, off_m, nullptr));
+    if (n > 0 && (!pos64 || !cell)) return set_error(ctx, HACC_EINVAL, "pos64 or cell is NULL");
+    HACC_CUDA(ci_to_f64(g, n, cell, reinterpret_cast<const float4 *>(off_m), pos64,
+                        reinterpret_cast<cudaStream_t>(stream)),
+              "cell/offset join");
+    return HACC_OK;
+}
+
+namespace {
+hacc_status ci_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, Work *w, int mode, float4 *out,
+                     float4 *vel, float hk, cudaStream_t s) {
+    ForceLaunch fl;
+    fl.pos = w->Ps;
+    fl.items = w->b.items;
+    fl.n_items = w->b.n_items;
+    fl.cell_start = w->b.cell_start;
+    fl.work_counter = w->counter;
+    fl.mode = mode;
+    fl.out = out;
+    fl.perm = w->b.perm;
+    fl.vel = w->Vs;
+    fl.pos_next = nullptr;
+    fl.h_kick = hk;
+    fl.h_drift = 0.f;
+    fl.phi_out = nullptr;
+    fl.within = nullptr;
+    fl.mass_flag = w->b.mass_flag;
+    fl.ids = w->b.perm;
+    fl.vel_pool = vel;
+    fl.flags = ctx->d_flags;
+    fl.cell_offset = true;
+    fl.w = (float)(g.Ld / g.nc);
+    fl.w_lo = (float)(g.Ld / g.nc - (double)fl.w);
+    HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch (cell/offset)");
+    ctx->force_launches++;
+    return HACC_OK;
+}
+}  // namespace
+
+hacc_status hacc_sr_force_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                             const int32_t *cell, const float *off_m, float *acc, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, off_m, acc));
+    if (n > 0 && (!cell || !acc)) return set_error(ctx, HACC_EINVAL, "cell or acc is NULL");
+    if (n == 0) return HACC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
+    // no stream: the cell ids are the keys as stored (cell and off_m are not written)
+    HACC_CUDA(bin_build_ci(g, n, const_cast<int32_t *>(cell), reinterpret_cast<float4 *>(const_cast<float *>(off_m)),
+                           nullptr, 0.0, w.P, w.b, ctx->d_flags, s),
+              "binning");
+    HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
+    return ci_force(ctx, g, fc, &w, kModeForce, reinterpret_cast<float4 *>(acc), nullptr, 0.f, s);
+}
+
+hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, int32_t *cell,
+                             float *off_m, float *vel, double dt, int32_t n_sub, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (n_sub < 1 || !std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "n_sub >= 1 and finite dt required");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, off_m, vel));
+    if (n > 0 && (!cell || !vel)) return set_error(ctx, HACC_EINVAL, "cell or vel is NULL");
+    if (n == 0) return HACC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
+    float4 *off = reinterpret_cast<float4 *>(off_m);
+    float4 *v = reinterpret_cast<float4 *>(vel);
+    const double h = dt / n_sub;
+    for (int k = 0; k < n_sub; ++k) {
+        // stream (FP64 on the global position: h/2 opening, then h fusing two halves), rebin
+        HACC_CUDA(bin_build_ci(g, n, cell, off, v, k == 0 ? 0.5 * h : h, w.P, w.b, ctx->d_flags, s), "binning");
+        HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, v, w.Vs, nullptr, nullptr, s), "gather");
+        // kick h (FP32), velocities back to input order
+        HACC_TRY(ci_force(ctx, g, fc, &w, kModeKick, nullptr, v, (float)h, s));
+    }
+    HACC_CUDA(drift_ci(g, n, cell, off, v, 0.5 * h, ctx->d_flags, s), "closing stream");
+    return HACC_OK;
+}
+
 hacc_status hacc_diagnostics(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
                              const float *pos_m, const float *vel, double *out, hacc_stream_t stream) {
     HACC_TRY(enter(ctx));

@@ -431,6 +431,95 @@ __global__ void __launch_bounds__(kBlock) k_candidates(int nc, const int32_t *__
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
 }
 
+// ---- positions as (cell, in-cell offset): the precision variant ------------
+// Cell of a global FP64 coordinate x in [0, L) and its FP32 offset from the
+// cell centre, x - (c + 1/2) w, in [-w/2, w/2].
+__device__ __forceinline__ int ci_split(double x, double inv_w, double w, int nc, float &off) {
+    int c = (int)floor(x * inv_w);
+    c = c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
+    off = (float)(x - ((double)c + 0.5) * w);
+    return c;
+}
+
+__device__ __forceinline__ bool wrap64(double &x, double L) {
+    if (!(x >= -L && x < 2.0 * L)) {
+        x = 0.0;
+        return false;
+    }
+    if (x < 0.0) x += L;
+    else if (x >= L) x -= L;
+    if (x >= L) x = 0.0;
+    return true;
+}
+
+// Optional stream x += drift * v in FP64 on the global position (c w + off),
+// then re-split into (cell, offset) in place; with key != null also the
+// counting-sort keys (the cell) and the sorted-copy source dst = (off, m).
+__global__ void __launch_bounds__(kBlock) k_key_ci(int64_t n, int32_t *__restrict__ cell, float4 *__restrict__ off,
+                                                    const float4 *__restrict__ vel, double drift, int nc, double L,
+                                                    double w, double inv_w, float4 *__restrict__ dst,
+                                                    int32_t *__restrict__ key, int32_t *__restrict__ rank,
+                                                    uint32_t *__restrict__ count, int *flags, int *mass_flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = cell[i];
+    float4 o = off[i];
+    if (vel) {
+        const float4 v = vel[i];
+        int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+        double x = fma((double)cx + 0.5, w, (double)o.x), y = fma((double)cy + 0.5, w, (double)o.y),
+               z = fma((double)cz + 0.5, w, (double)o.z);
+        x = fma(drift, (double)v.x, x);
+        y = fma(drift, (double)v.y, y);
+        z = fma(drift, (double)v.z, z);
+        bool ok = wrap64(x, L);
+        ok &= wrap64(y, L);
+        ok &= wrap64(z, L);
+        if (!ok) atomicOr(flags, kFlagDomain);
+        cx = ci_split(x, inv_w, w, nc, o.x);
+        cy = ci_split(y, inv_w, w, nc, o.y);
+        cz = ci_split(z, inv_w, w, nc, o.z);
+        c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
+        cell[i] = c;
+        off[i] = o;
+    }
+    if (!key) return;
+    if (o.w != off[0].w) atomicOr(mass_flag, 1);
+    dst[i] = o;
+    key[i] = c;
+    rank[i] = (int32_t)atomicAdd(&count[c], 1u);
+}
+
+__global__ void __launch_bounds__(kBlock) k_ci_from_f64(int64_t n, const double *__restrict__ x64,
+                                                         const float *__restrict__ mass, int nc, double L, double w,
+                                                         double inv_w, int32_t *__restrict__ cell,
+                                                         float4 *__restrict__ off, int *flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = x64[3 * i], y = x64[3 * i + 1], z = x64[3 * i + 2];
+    bool ok = wrap64(x, L);
+    ok &= wrap64(y, L);
+    ok &= wrap64(z, L);
+    if (!ok) atomicOr(flags, kFlagDomain);
+    float4 o;
+    int cx = ci_split(x, inv_w, w, nc, o.x), cy = ci_split(y, inv_w, w, nc, o.y), cz = ci_split(z, inv_w, w, nc, o.z);
+    o.w = mass ? mass[i] : 1.0f;
+    cell[i] = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
+    off[i] = o;
+}
+
+__global__ void __launch_bounds__(kBlock) k_ci_to_f64(int64_t n, const int32_t *__restrict__ cell,
+                                                       const float4 *__restrict__ off, int nc, double w,
+                                                       double *__restrict__ x64) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t c = cell[i];
+    const float4 o = off[i];
+    x64[3 * i] = fma((double)(c % nc) + 0.5, w, (double)o.x);
+    x64[3 * i + 1] = fma((double)((c / nc) % nc) + 0.5, w, (double)o.y);
+    x64[3 * i + 2] = fma((double)(c / (nc * nc)) + 0.5, w, (double)o.z);
+}
+
 inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
@@ -522,6 +611,48 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s);
+}
+
+cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,
+                         float4 *dst, const BinBuffers &b, int *d_flags, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if (n > 0) {
+        const double w = g.Ld / g.nc;
+        k_key_ci<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, vel, drift, g.nc, g.Ld, w, g.nc / g.Ld, dst, b.key,
+                                                  b.rank, b.count, d_flags, b.mass_flag);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return bin_sort(n, g.ncell, b, true, nullptr, 1, s);
+}
+
+cudaError_t drift_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,
+                     int *d_flags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const double w = g.Ld / g.nc;
+    k_key_ci<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, vel, drift, g.nc, g.Ld, w, g.nc / g.Ld, nullptr, nullptr,
+                                              nullptr, nullptr, d_flags, nullptr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t ci_from_f64(const Geometry &g, int64_t n, const double *x64, const float *mass, int32_t *cell,
+                        float4 *off, int *d_flags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const double w = g.Ld / g.nc;
+    k_ci_from_f64<<<blocks_for(n), kBlock, 0, s>>>(n, x64, mass, g.nc, g.Ld, w, g.nc / g.Ld, cell, off, d_flags);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t ci_to_f64(const Geometry &g, int64_t n, const int32_t *cell, const float4 *off, double *x64,
+                      cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_ci_to_f64<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, g.nc, g.Ld / g.nc, x64);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, const float4 *v_in,

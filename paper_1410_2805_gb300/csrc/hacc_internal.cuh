@@ -192,6 +192,17 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
                             const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
                             const BinBuffers &b, int *d_flags, cudaStream_t s);
 
+// Precision variant: positions as (cell id, FP32 in-cell offset, mass).
+// bin_build_ci optionally streams (FP64 on the global position) first.
+cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,
+                         float4 *dst, const BinBuffers &b, int *d_flags, cudaStream_t s);
+cudaError_t drift_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,
+                     int *d_flags, cudaStream_t s);
+cudaError_t ci_from_f64(const Geometry &g, int64_t n, const double *x64, const float *mass, int32_t *cell,
+                        float4 *off, int *d_flags, cudaStream_t s);
+cudaError_t ci_to_f64(const Geometry &g, int64_t n, const int32_t *cell, const float4 *off, double *x64,
+                      cudaStream_t s);
+
 // Gather rows into sorted order: out[k] = in[perm[k]] for float4, int ids.
 cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out,
                           const float4 *v_in, float4 *v_out, const int32_t *id_in, int32_t *id_out,
@@ -206,7 +217,7 @@ cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsign
                             cudaStream_t s);
 
 // ---- pair force (sr_force.cu) -------------------------------------------
-enum ForceMode : int { kModeForce = 0, kModeKickDrift = 1, kModePotential = 2, kModeBatch = 3 };
+enum ForceMode : int { kModeForce = 0, kModeKickDrift = 1, kModePotential = 2, kModeBatch = 3, kModeKick = 4 };
 
 struct ForceLaunch {
     const float4 *pos;          // sorted, wrapped
@@ -232,6 +243,10 @@ struct ForceLaunch {
     float4 *pos_pool = nullptr;
     float4 *vel_pool = nullptr;
     int *flags = nullptr;             // device status word (wrap errors)
+    // positions are in-cell offsets (precision variant); w = fl(L / nc)
+    bool cell_offset = false;
+    float w = 0.0f;
+    float w_lo = 0.0f;                // (L / nc) - w, the FP32 remainder of the cell width
     int variant = 0;            // pair-kernel variant (autotuned), 0..kForceVariants-1
 };
 

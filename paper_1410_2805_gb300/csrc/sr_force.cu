@@ -59,6 +59,7 @@ struct KParams {
     float *phi_out;
     unsigned long long *within;
     const int *mass_flag;
+    float w, w_lo, w_ratio;   // cell width w = w + w_lo (FP32 pair), w_ratio = w_lo / w
     const BoxDev *boxes;
     const int32_t *ids;
     float4 *pos_pool;
@@ -144,9 +145,9 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
 // (tx, ty, tz): image shift added to this lane's i coordinates.  The warp is
 // split into G = 2^lg lane groups; group g takes the staged entries g, g+G,
 // g+2G, ... (consecutive float4 addresses across groups: no bank conflicts).
-template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U>
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
-                                            float ty, float tz, int iself, int lg, int grp,
+                                            float ty, float tz, int b1, int b2, int d0, int iself, int lg, int grp,
                                             const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
                                             float (&ax)[K], float (&ay)[K], float (&az)[K], unsigned &cnt,
                                             float4 *buf, int lane) {
@@ -167,7 +168,16 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
         float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
         if (lane < nj) {
             v = P.pos[j0 + lane];
-            if (jshift) {
+            if (CI) {
+                // in-cell offsets: move j into the frame of i's cell (cell steps of w;
+                // the x step depends on which of the run's cells j sits in)
+                // w = w_hi + w_lo exactly: the step is applied in two adds
+                const int j = j0 + lane;
+                const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
+                v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
+                v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
+                v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
+            } else if (jshift) {
                 v.x = __fadd_rn(v.x, sx);
                 v.y = __fadd_rn(v.y, sy);
                 v.z = __fadd_rn(v.z, sz);
@@ -186,7 +196,7 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
     }
 }
 
-template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U>
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane, float m_uniform) {
     // geometry: the single box of the call, or this item's box of a batch
     int nc = P.nc;
@@ -226,11 +236,13 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
         float sjz = 0.0f, siz = 0.0f;
         if (rz < 0) { rz += nc; sjz = -L; }
         else if (rz >= nc) { rz -= nc; siz = -L; }
+        if (CI) { sjz = (float)dz * P.w; siz = 0.0f; }
         for (int dy = -1; dy <= 1; ++dy) {
             int ry = cy + dy;
             float sjy = 0.0f, siy = 0.0f;
             if (ry < 0) { ry += nc; sjy = -L; }
             else if (ry >= nc) { ry -= nc; siy = -L; }
+            if (CI) { sjy = (float)dy * P.w; siy = 0.0f; }
             const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
             // cells (cx-1, cx, cx+1) of this row: one run, or two when it wraps in x
             const int nruns = (cx == 0 || cx == nc - 1) ? 2 : 1;
@@ -238,20 +250,31 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
             for (int r = 0; r < nruns; ++r) {
                 int ja, jb;
                 float sjx = 0.0f, six = 0.0f;
+                // with in-cell offsets: x cell step of the run's entries is
+                // d0 + (j >= b1) + (j >= b2)
+                int b1, b2, d0;
                 if (cx == 0) {
                     ja = r ? row[nc - 1] : row[0];
                     jb = r ? row[nc] : row[2];
                     sjx = r ? -L : 0.0f;
+                    b1 = r ? jb : row[1];
+                    d0 = r ? -1 : 0;
                 } else if (cx == nc - 1) {
                     ja = r ? row[0] : row[nc - 2];
                     jb = r ? row[1] : row[nc];
                     six = r ? -L : 0.0f;
+                    b1 = r ? jb : row[nc - 1];
+                    d0 = r ? 1 : -1;
                 } else {
                     ja = row[cx - 1];
                     jb = row[cx + 2];
+                    b1 = row[cx];
+                    d0 = -1;
                 }
-                process_run<K, COUNT, POT, EPS0, UM, U>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, iself, lg, grp, xi, yi,
-                                                 zi, ax, ay, az, cnt, buf, lane);
+                b2 = (cx == 0 || cx == nc - 1) ? jb : row[cx + 1];
+                if (CI) six = 0.0f;
+                process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
+                                                            lg, grp, xi, yi, zi, ax, ay, az, cnt, buf, lane);
             }
         }
     }
@@ -282,6 +305,13 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
             if (P.mode == kModeForce) {
                 int o = P.perm ? P.perm[i] : i;
                 P.out[o] = make_float4(gx, gy, gz, 0.0f);
+            } else if (P.mode == kModeKick) {
+                const int row = P.ids[i];
+                float4 v = P.vel[i];
+                v.x = __fmaf_rn(h_kick, gx, v.x);
+                v.y = __fmaf_rn(h_kick, gy, v.y);
+                v.z = __fmaf_rn(h_kick, gz, v.z);
+                P.vel_pool[row] = v;
             } else {
                 float4 v = P.vel[i];
                 v.x = __fmaf_rn(h_kick, gx, v.x);
@@ -316,7 +346,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
     }
 }
 
-template <bool COUNT, bool POT, bool EPS0, bool UM, int U>
+template <bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI = false>
 __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lane, float m_uniform) {
     const int n_items = *P.n_items;
     while (true) {
@@ -326,10 +356,10 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lan
         if (it >= n_items) break;
         int4 item = P.items[it];
         switch (item.w & 15) {
-            case 1: process_item<1, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
-            case 2: process_item<2, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
-            case 3: process_item<3, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
-            default: process_item<4, COUNT, POT, EPS0, UM, U>(P, item, buf, lane, m_uniform); break;
+            case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
+            case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
+            case 3: process_item<3, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
+            default: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
         }
     }
 }
@@ -346,6 +376,18 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
         work_loop<COUNT, POT, EPS0, true, U>(P, buf, lane, P.pos[0].w);
     else
         work_loop<COUNT, POT, EPS0, false, U>(P, buf, lane, 0.0f);
+}
+
+// Positions as (cell, in-cell offset): the precision variant.
+template <bool EPS0>
+__global__ void __launch_bounds__(kThreads, 6) k_sr_force_ci(KParams P) {
+    __shared__ float4 tiles[kWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *buf = tiles[w];
+    if (P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
+        work_loop<false, false, EPS0, true, 0, true>(P, buf, lane, P.pos[0].w);
+    else
+        work_loop<false, false, EPS0, false, 0, true>(P, buf, lane, 0.0f);
 }
 
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
@@ -407,10 +449,24 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.pos_pool = fl.pos_pool;
     P.vel_pool = fl.vel_pool;
     P.flags = fl.flags;
+    P.w = fl.w;
+    P.w_lo = fl.w_lo;
+    P.w_ratio = fl.w != 0.0f ? fl.w_lo / fl.w : 0.0f;
     const bool eps0 = !(fc.eps > 0.0f);
     const bool pot = fl.mode == kModePotential;
     const bool count = fl.within != nullptr;
     const int v = fl.variant;
+    if (fl.cell_offset) {
+        int per_sm = 0;
+        cudaError_t e = eps0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_force_ci<true>, kThreads, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_force_ci<false>, kThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        if (eps0) k_sr_force_ci<true><<<num_sms * per_sm, kThreads, 0, s>>>(P);
+        else k_sr_force_ci<false><<<num_sms * per_sm, kThreads, 0, s>>>(P);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (pot) return eps0 ? launch_one<false, true, true, 6, 0>(P, num_sms, s) : launch_one<false, true, false, 6, 0>(P, num_sms, s);
     if (count) return eps0 ? launch_variant<true, false, true>(P, v, num_sms, s) : launch_variant<true, false, false>(P, v, num_sms, s);
     return eps0 ? launch_variant<false, false, true>(P, v, num_sms, s) : launch_variant<false, false, false>(P, v, num_sms, s);
