@@ -63,6 +63,10 @@ def lib():
             L.hacc_oracle_subcycle.argtypes = [i64, p, p, p, d, d, d, p, d, d, i32]
             L.hacc_oracle_diagnostics.restype = None
             L.hacc_oracle_diagnostics.argtypes = [i64, p, p, p, d, d, d, p, d, p]
+            L.hacc_oracle_ml_levels.restype = None
+            L.hacc_oracle_ml_levels.argtypes = [i64, p, d, i32, i32, i32, p]
+            L.hacc_oracle_subcycle_ml.restype = None
+            L.hacc_oracle_subcycle_ml.argtypes = [i64, p, p, p, d, d, d, p, d, d, i32, p]
             L.hacc_oracle_threads.restype = i32
             L.hacc_oracle_set_threads.argtypes = [i32]
             _lib = L
@@ -197,4 +201,25 @@ def step(pos, vel, L, split_params, dt, n_c, ng=None, sigma=0.8, ns=3):
     p1 = np.concatenate([x, m[:, None]], axis=1)
     x, v = subcycle(p1, v, L, split_params, dt, n_c)
     v += 0.5 * dt * G * pm.pm_accel(x, m, L, ng, sigma=sigma, ns=ns)
+    return x, v
+
+
+def ml_levels(pos32, L, nc, d, lmax):
+    """Kick counts of Eq. (kicks) from the chaining-mesh densities of the FP32 start positions."""
+    p = np.ascontiguousarray(pos32, dtype=np.float32)
+    lev = np.empty(p.shape[0], dtype=np.int32)
+    lib().hacc_oracle_ml_levels(p.shape[0], _ptr(p), float(L), int(nc), int(d), int(lmax), _ptr(lev))
+    return lev
+
+
+def subcycle_ml(pos, vel, L, split_params, dt, lmax, level):
+    """One FP64 multi-level step with fixed kick counts; returns (x, v)."""
+    x, m = _xm(pos)
+    x = x.copy()
+    v = np.ascontiguousarray(np.asarray(vel)[:, :3], dtype=np.float64).copy()
+    c = _c(split_params["poly"])
+    lev = np.ascontiguousarray(level, dtype=np.int32)
+    lib().hacc_oracle_subcycle_ml(x.shape[0], _ptr(x), _ptr(v), _ptr(m), float(L), float(split_params["r_cut"]),
+                                  float(split_params["eps"]), _ptr(c), float(split_params["G"]), float(dt),
+                                  int(lmax), _ptr(lev))
     return x, v

@@ -395,3 +395,87 @@ void hacc_oracle_diagnostics(int64_t n, const double *x, const double *v, const 
     }
     out[0] = px; out[1] = py; out[2] = pz; out[3] = ke; out[4] = pe;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Multi-level short-range step (Sec. 3.1, Eq. (kicks)).
+ *
+ * Levels: with the chaining mesh of hacc_oracle_wrap_cell on the FP32 start
+ * positions, a cell holding count particles has density rho / rho0 =
+ * count nc^3 / n; its particles get l = floor(floor(rho/rho0) / d) + 1 kicks
+ * (integer arithmetic), capped at lmax.  d <= 0 gives every particle lmax.
+ * pos32: n x 4 floats (wrapped copy is made internally); level: n ints out. */
+void hacc_oracle_ml_levels(int64_t n, const float *pos32, double L, int nc, int d, int lmax, int32_t *level) {
+    int64_t ncell = (int64_t)nc * nc * nc;
+    float *p = (float *)malloc(sizeof(float) * 4 * (size_t)(n ? n : 1));
+    memcpy(p, pos32, sizeof(float) * 4 * (size_t)n);
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    hacc_oracle_wrap_cell(n, p, L, nc, cell);
+    int64_t *count = (int64_t *)calloc((size_t)ncell, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) count[cell[i]]++;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t l = lmax;
+        if (d > 0) {
+            int64_t ratio = count[cell[i]] * ncell / n;   /* floor(rho / rho0) */
+            l = ratio / d + 1;
+            if (l > lmax) l = lmax;
+        }
+        level[i] = (int32_t)l;
+    }
+    free(count);
+    free(cell);
+    free(p);
+}
+
+/* One multi-level step of length dt with fixed per-particle kick counts
+ * level[i] in [1, lmax]: a particle with l kicks is kicked by dt/l at the
+ * times (2k+1)/(2l) dt, k = 0..l-1 (the midpoints of its own SKS steps); all
+ * particles stream together between consecutive event times (the union of
+ * those times over the levels present), so each is streamed by the same
+ * total dt.  FP64. */
+void hacc_oracle_subcycle_ml(int64_t n, double *x, double *v, const double *m, double L, double rcut, double eps,
+                             const double *c, double G, double dt, int lmax, const int32_t *level) {
+    /* event times, as reduced fractions num/den of dt, of the levels present */
+    int cap = lmax * (lmax + 1) / 2, ne = 0;
+    int64_t *num = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t *den = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    char *present = (char *)calloc((size_t)lmax + 1, 1);
+    for (int64_t i = 0; i < n; ++i)
+        if (level[i] >= 1 && level[i] <= lmax) present[level[i]] = 1;
+    for (int l = 1; l <= lmax; ++l)
+        for (int k = 0; k < l && present[l]; ++k) {
+            int64_t a = 2 * k + 1, b = 2 * l, g = a, h = b;
+            while (h) { int64_t t = g % h; g = h; h = t; }
+            a /= g; b /= g;
+            int dup = 0;
+            for (int e = 0; e < ne; ++e) if (num[e] == a && den[e] == b) dup = 1;
+            if (!dup) { num[ne] = a; den[ne] = b; ++ne; }
+        }
+    for (int i = 1; i < ne; ++i)          /* insertion sort by value (exact cross products) */
+        for (int j = i; j > 0 && num[j] * den[j - 1] < num[j - 1] * den[j]; --j) {
+            int64_t t = num[j]; num[j] = num[j - 1]; num[j - 1] = t;
+            t = den[j]; den[j] = den[j - 1]; den[j - 1] = t;
+        }
+    int64_t *sel = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    double *a = (double *)malloc(sizeof(double) * 3 * (size_t)(n ? n : 1));
+    double t_prev = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        double te = dt * (double)num[e] / (double)den[e];
+        for (int64_t i = 0; i < 3 * n; ++i) x[i] = wrap64(x[i] + (te - t_prev) * v[i], L);
+        t_prev = te;
+        int64_t ns = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t l = level[i];
+            /* kicked now iff 2 l num / den is an odd integer */
+            if ((2 * l * num[e]) % den[e] == 0 && ((2 * l * num[e]) / den[e]) % 2 == 1) sel[ns++] = i;
+        }
+        if (ns == 0) continue;
+        hacc_oracle_force_mesh(n, x, m, L, rcut, eps, c, G, ns, sel, a, NULL);
+        for (int64_t q = 0; q < ns; ++q) {
+            int64_t i = sel[q];
+            double h = dt / level[i];
+            v[3 * i] += h * a[3 * q]; v[3 * i + 1] += h * a[3 * q + 1]; v[3 * i + 2] += h * a[3 * q + 2];
+        }
+    }
+    for (int64_t i = 0; i < 3 * n; ++i) x[i] = wrap64(x[i] + (dt - t_prev) * v[i], L);
+    free(a); free(sel); free(num); free(den); free(present);
+}
