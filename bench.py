@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson stream) segment")
     ap.add_argument("--served-window", type=float, default=6.0, help="seconds of arrivals in the served segment")
     ap.add_argument("--served-cap", type=float, default=20.0, help="wall-time cap of the served segment")
+    ap.add_argument("--precision", action="store_true",
+                    help="precision study instead: 512^3 Zel'dovich, FP32 absolute vs cell + offset positions")
+    ap.add_argument("--precision-side", type=int, default=512)
+    ap.add_argument("--precision-sample", type=int, default=1 << 20)
     return ap.parse_args()
 
 
@@ -133,6 +137,23 @@ def measured_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+def measured_traffic(n_particles: int):
+    """DRAM bytes of one pair-kernel launch from the committed ncu capture,
+    scaled by particles (traffic is ~34 B per particle per launch), or None
+    when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "sr_force_traffic_zeldovich256.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, "paper_1410_2805_gb300", "csrc", "sr_force.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if sha != rec.get("kernel_source_sha256_16"):
+        return None
+    return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * n_particles / rec["particles"]
 
 
 def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
@@ -474,7 +495,7 @@ def run_ours(args):
     force_s = st["force_ms"] / 1e3
     achieved = cand * FLOPS_PER_PAIR / force_s / 1e12 if force_s > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(n),
                 "kernel": "k_sr_force (pair force + kick + stream)",
                 "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (sm_max_mhz of measured peaks)"
                               % (num_sms, smax),
@@ -526,8 +547,99 @@ def run_ours(args):
     return 0
 
 
+def run_precision(args):
+    """Precision study: the same FP64 Zel'dovich positions (side^3 particles,
+    box `side`, seed 3) as FP32 absolute coordinates and as (cell id, FP32
+    in-cell offset); pair forces of both against the FP64 oracle on a seeded
+    random sample of particles (all particles as sources); device times of
+    the force and of 5 SKS sub-cycles in both forms."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1410_2805_gb300 as hacc
+    import synth
+    from oracle import split as osplit
+    from paper_1410_2805_gb300 import build as hbuild
+
+    hbuild.build()
+    side = args.precision_side
+    L = float(side)
+    x64 = synth.zeldovich(side, seed=3, L=L, return_f64=True)
+    n = len(x64)
+    p32 = np.ones((n, 4), np.float32)
+    p32[:, :3] = x64.astype(np.float32)
+    p32[:, :3][p32[:, :3] >= np.float32(L)] = 0
+    vel = synth.gaussian_velocities(n, seed=3, sigma=0.1)
+    ctx = hacc.Context(0)
+    split = hacc.default_split()
+    box = hacc.Box(L=L)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    P = torch.from_numpy(p32).cuda()
+    X = torch.from_numpy(x64).cuda()
+    cell, off = ctx.ci_from_f64(box, split.r_cut, X)
+    out = {}
+    acc32 = ctx.sr_force(box, split, P)
+    out["force_ms_fp32_abs"] = timed(lambda: ctx.sr_force(box, split, P, acc=acc32), 3)
+    acc_ci = ctx.sr_force_ci(box, split, cell, off)
+    out["force_ms_cell_offset"] = timed(lambda: ctx.sr_force_ci(box, split, cell, off), 3)
+    ctx.sync()
+    a32 = acc32.cpu().numpy()[:, :3].astype(np.float64)
+    aci = acc_ci.cpu().numpy()[:, :3].astype(np.float64)
+    # 5 sub-cycles of step 0.1 in both forms (copies, so the positions above stay)
+    P2, V2 = P.clone(), torch.from_numpy(vel).cuda()
+    C2, O2, V3 = cell.clone(), off.clone(), torch.from_numpy(vel).cuda()
+    out["subcycle5_ms_fp32_abs"] = timed(lambda: ctx.subcycle(box, split, P2, V2, 0.5, 5), 1)
+    out["subcycle5_ms_cell_offset"] = timed(lambda: ctx.subcycle_ci(box, split, C2, O2, V3, 0.5, 5), 1)
+    ctx.sync()
+    ctx.close()
+    del P, X, P2, V2, C2, O2, V3, acc32, acc_ci
+    sp = osplit.default_split()
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    sel = np.sort(np.random.default_rng(33).choice(n, size=min(n, args.precision_sample), replace=False))
+    t0 = time.perf_counter()
+    pos64 = np.concatenate([x64, np.ones((n, 1))], axis=1)
+    del x64
+    ref, _ = oracle.force_mesh(pos64, L, sp, sel=sel)
+    t_or = time.perf_counter() - t0
+    rms = float(np.sqrt((ref ** 2).sum(1).mean()))
+
+    amag = np.sqrt((ref ** 2).sum(1))
+
+    def errs(a):
+        d = np.sqrt(((a[sel] - ref) ** 2).sum(1))
+        worst = int(np.argmax(d))
+        big = amag > 0.01 * rms
+        return {"max_rel_to_rms": float(d.max() / rms), "rms_rel_to_rms": float(np.sqrt((d ** 2).mean()) / rms),
+                "worst_particle_abs_a_over_rms": float(amag[worst] / rms),
+                "worst_particle_own_rel_err": float(d[worst] / max(amag[worst], 1e-300)),
+                "max_own_rel_err_abs_a_over_1pct_rms": float((d[big] / amag[big]).max()),
+                "p99_own_rel_err": float(np.percentile(d[big] / amag[big], 99))}
+
+    out.update({"particles": n, "box": L, "sample": int(len(sel)), "oracle_s": t_or, "oracle_threads": oracle.threads(),
+                "error_fp32_abs": errs(a32), "error_cell_offset": errs(aci)})
+    print(json.dumps({"precision_study": out, "workload": "%d^3 Zel'dovich, box %d, seed 3" % (side, side)}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.precision:
+        return run_precision(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -163,6 +163,19 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
 hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                       int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
 
+/* Multi-level short-range step (Sec. 3.1, Eq. (kicks)): the density of each
+ * particle's chaining-mesh cell at the start of the step, rho / rho0 =
+ * count nc^3 / n, sets its kick count l = floor(floor(rho/rho0) / d) + 1
+ * (integers; d <= 0 gives every particle lmax), capped at lmax (1..16).  A
+ * particle with l kicks is kicked by dt/l at times (2k+1)/(2l) dt, k < l; all
+ * particles stream together between the union of those times over the counts
+ * that occur (one host synchronisation per step reads which occur), so each
+ * streams by dt in total.  At an event only the cells holding a kicked particle
+ * get work items.  level_out (nullable, device, n) receives the kick counts. */
+hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
+                             float *vel, double dt, int32_t d, int32_t lmax, int32_t *level_out,
+                             hacc_stream_t stream);
+
 /* Long-range PM acceleration alone (with G = 1): acc[n] receives (ax, ay, az, 0).
  * ng = 0 in the box means ng = round(L); ng must be even, 4 <= ng <= 2048.
  * The grid, its FFT plans and buffers are kept by the context between calls. */

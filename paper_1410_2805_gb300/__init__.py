@@ -155,6 +155,7 @@ def lib():
             "hacc_step_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), ctypes.POINTER(_Pm), i64, p,
                                     p, d, i32, p]),
             "hacc_stats_enable": (st, [p, ctypes.c_int, ctypes.c_int]),
+            "hacc_subcycle_ml": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, d, i32, i32, p, p]),
             "hacc_ci_from_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p, p]),
             "hacc_ci_to_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p]),
             "hacc_sr_force_ci": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, p]),
@@ -369,6 +370,15 @@ class Context:
         self._check(lib().hacc_subcycle(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
                                         _ptr(pos), _ptr(vel), float(dt), int(n_sub), self._stream(stream)),
                     "hacc_subcycle")
+
+    def subcycle_ml(self, box: Box, split, pos, vel, dt: float, d: int, lmax: int, levels=None, stream=None):
+        """One multi-level short-range step (kick counts from cell densities, Eq. (kicks))."""
+        _dev_rows(pos, "pos")
+        _dev_rows(vel, "vel")
+        sp = _split_of(split)
+        self._check(lib().hacc_subcycle_ml(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
+                                           _ptr(pos), _ptr(vel), float(dt), int(d), int(lmax), _ptr(levels),
+                                           self._stream(stream)), "hacc_subcycle_ml")
 
     def step(self, box: Box, split, pm: PM, pos, vel, dt: float, n_c: int, stream=None):
         _dev_rows(pos, "pos")

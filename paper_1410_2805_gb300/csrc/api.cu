@@ -4,10 +4,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "hacc_internal.cuh"
 
@@ -178,6 +180,8 @@ struct Work {
     unsigned long long *within;
     float *phi;
     double *diag;
+    int *cell_active;   // multi-level: cells with a particle kicked at this event
+    int *present;       // multi-level: kick counts that occur
     BinBuffers b;
 };
 
@@ -193,6 +197,8 @@ size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w) {
     w->within = c.take<unsigned long long>(1);
     w->phi = c.take<float>(n);
     w->diag = c.take<double>(5);
+    w->cell_active = c.take<int>(ncell);
+    w->present = c.take<int>(kMaxLevels + 1);
     carve_bin(c, n, ncell, &w->b);
     return c.off + 256;
 }
@@ -620,6 +626,97 @@ hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         HACC_TRY(ci_force(ctx, g, fc, &w, kModeKick, nullptr, v, (float)h, s));
     }
     HACC_CUDA(drift_ci(g, n, cell, off, v, 0.5 * h, ctx->d_flags, s), "closing stream");
+    return HACC_OK;
+}
+
+hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
+                             float *vel, double dt, int32_t d, int32_t lmax, int32_t *level_out,
+                             hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (lmax < 1 || lmax > kMaxLevels) return set_error(ctx, HACC_EINVAL, "lmax must be in [1, 16]");
+    if (!std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, pos_m, vel));
+    if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
+    if (n == 0) return HACC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
+    float4 *pos_in = reinterpret_cast<float4 *>(pos_m);
+    float4 *V = reinterpret_cast<float4 *>(vel);
+    int32_t *level = w.ID;   // kick count per particle, input order
+    // kick counts from the cell densities at the start of the step
+    HACC_CUDA(bin_build(g, n, pos_in, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
+    HACC_CUDA(cudaMemsetAsync(w.present, 0, sizeof(int) * (kMaxLevels + 1), s), "memset");
+    HACC_CUDA(ml_levels(g, n, w.b, d, lmax, level, w.present, s), "kick counts");
+    if (level_out)
+        HACC_CUDA(cudaMemcpyAsync(level_out, level, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "levels out");
+    int present[kMaxLevels + 1];
+    HACC_CUDA(cudaMemcpyAsync(present, w.present, sizeof present, cudaMemcpyDeviceToHost, s), "levels present");
+    HACC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    // event times (2k+1)/(2l) dt of the counts present, as reduced fractions
+    std::vector<std::pair<int64_t, int64_t>> ev;
+    for (int l = 1; l <= lmax; ++l) {
+        if (!present[l]) continue;
+        for (int k = 0; k < l; ++k) {
+            int64_t a = 2 * k + 1, b = 2 * l, x = a, y = b;
+            while (y) { int64_t t = x % y; x = y; y = t; }
+            a /= x;
+            b /= x;
+            bool dup = false;
+            for (auto &e : ev) dup |= (e.first == a && e.second == b);
+            if (!dup) ev.emplace_back(a, b);
+        }
+    }
+    std::sort(ev.begin(), ev.end(), [](const std::pair<int64_t, int64_t> &p, const std::pair<int64_t, int64_t> &q) {
+        return p.first * q.second < q.first * p.second;
+    });
+    double t_prev = 0.0;
+    for (auto &e : ev) {
+        const double te = dt * (double)e.first / (double)e.second;
+        KickTable kt;
+        for (int l = 0; l <= kMaxLevels; ++l) {
+            kt.h[l] = 0.0f;
+            if (l >= 1 && l <= lmax && present[l] && (2 * l * e.first) % e.second == 0 &&
+                ((2 * l * e.first) / e.second) % 2 == 1)
+                kt.h[l] = (float)(dt / l);
+        }
+        // stream everyone to te, rebin, items for cells with a particle kicked now
+        HACC_CUDA(bin_build_ml(g, n, w.P, V, (float)(te - t_prev), level, kt, w.cell_active, w.b, ctx->d_flags, s),
+                  "binning");
+        t_prev = te;
+        HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, V, w.Vs, level, w.IDs, s), "gather");
+        ForceLaunch fl;
+        fl.pos = w.Ps;
+        fl.items = w.b.items;
+        fl.n_items = w.b.n_items;
+        fl.cell_start = w.b.cell_start;
+        fl.work_counter = w.counter;
+        fl.mode = kModeKickLevels;
+        fl.out = nullptr;
+        fl.perm = nullptr;
+        fl.vel = w.Vs;
+        fl.pos_next = nullptr;
+        fl.h_kick = 0.f;
+        fl.h_drift = 0.f;
+        fl.phi_out = nullptr;
+        fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
+        fl.mass_flag = w.b.mass_flag;
+        fl.variant = ctx->variant;
+        fl.ids = w.b.perm;
+        fl.vel_pool = V;
+        fl.levels = w.IDs;
+        fl.kick = kt;
+        fl.flags = ctx->d_flags;
+        HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch (multi-level)");
+        ctx->force_launches++;
+    }
+    // last stream, wrapped, into the caller's positions
+    HACC_CUDA(drift_wrap(n, w.P, V, (float)(dt - t_prev), pos_in, g.Lf, ctx->d_flags, s), "closing stream");
     return HACC_OK;
 }
 

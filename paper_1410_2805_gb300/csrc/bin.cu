@@ -84,11 +84,13 @@ __device__ __forceinline__ uint32_t items_of(uint32_t cnt) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_pack(int64_t ncell, const uint32_t *__restrict__ count,
+                                                  const int *__restrict__ cell_active,
                                                   unsigned long long *__restrict__ packed) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     uint32_t k = count[c];
-    packed[c] = (unsigned long long)k | ((unsigned long long)items_of(k) << 32);
+    const uint32_t it = (cell_active && !cell_active[c]) ? 0u : items_of(k);
+    packed[c] = (unsigned long long)k | ((unsigned long long)it << 32);
 }
 
 // ---- exclusive scan of uint64, reduce-then-scan, 2048 values per block ----
@@ -298,13 +300,15 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
                                                    const unsigned long long *__restrict__ packed,
                                                    int32_t *__restrict__ cell_start, int4 *__restrict__ items,
                                                    int32_t *__restrict__ n_items, int make_items,
-                                                   const BoxDev *__restrict__ boxes, int nbox) {
+                                                   const BoxDev *__restrict__ boxes, int nbox,
+                                                   const int *__restrict__ cell_active) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) {
         cell_start[ncell] = (int32_t)n;
         if (make_items) {
             unsigned long long last = packed[ncell - 1];
-            *n_items = (int32_t)((last >> 32) + items_of(count[ncell - 1]));
+            const bool on = !cell_active || cell_active[ncell - 1];
+            *n_items = (int32_t)((last >> 32) + (on ? items_of(count[ncell - 1]) : 0u));
         }
     }
     if (c >= ncell) return;
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
     if (!make_items) return;
     uint32_t cnt = count[c];
     uint32_t it = (uint32_t)(p >> 32);
-    if (cnt == 0) return;
+    if (cnt == 0 || (cell_active && !cell_active[c])) return;
     int box = 0;
     if (boxes) {  // last box whose first cell is <= c
         int lo = 0, hi = nbox - 1;
@@ -520,6 +524,51 @@ __global__ void __launch_bounds__(kBlock) k_ci_to_f64(int64_t n, const int32_t *
     x64[3 * i + 2] = fma((double)(c / (nc * nc)) + 0.5, w, (double)o.z);
 }
 
+// ---- multi-level stepping ------------------------------------------------
+// Kick count of every particle from its cell's density (Eq. (kicks)):
+// l = floor(floor(count nc^3 / n) / d) + 1, capped at lmax (d <= 0: lmax);
+// present[l] = 1 for the counts that occur.
+__global__ void __launch_bounds__(kBlock) k_levels(int64_t n, int64_t ncell, const int32_t *__restrict__ key,
+                                                    const uint32_t *__restrict__ count, int d, int lmax,
+                                                    int32_t *__restrict__ level, int *__restrict__ present) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t l = lmax;
+    if (d > 0) {
+        const int64_t ratio = (int64_t)count[key[i]] * ncell / n;
+        l = ratio / d + 1;
+        if (l > lmax) l = lmax;
+    }
+    level[i] = (int32_t)l;
+    present[l] = 1;
+}
+
+// Cells that hold a particle kicked at this event.
+__global__ void __launch_bounds__(kBlock) k_mark_active(int64_t n, const int32_t *__restrict__ key,
+                                                         const int32_t *__restrict__ level, KickTable kt,
+                                                         int *__restrict__ cell_active) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (kt.h[level[i]] != 0.0f) cell_active[key[i]] = 1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_drift_wrap(int64_t n, const float4 *__restrict__ src,
+                                                        const float4 *__restrict__ vel, float drift,
+                                                        float4 *__restrict__ dst, float Lf, int *flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = src[i];
+    const float4 v = vel[i];
+    p.x = __fmaf_rn(drift, v.x, p.x);
+    p.y = __fmaf_rn(drift, v.y, p.y);
+    p.z = __fmaf_rn(drift, v.z, p.z);
+    bool ok = wrap1(p.x, Lf);
+    ok &= wrap1(p.y, Lf);
+    ok &= wrap1(p.z, Lf);
+    if (!ok) atomicOr(flags, kFlagDomain);
+    dst[i] = p;
+}
+
 inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
@@ -556,9 +605,9 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
 namespace {
 // Counting sort by key and work items, shared by the single-box and batched passes.
 cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_items, const BoxDev *boxes, int nbox,
-                     cudaStream_t s) {
+                     cudaStream_t s, const int *cell_active = nullptr) {
     cudaError_t e;
-    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, b.packed);
+    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, cell_active, b.packed);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(b.packed, ncell, b.scan_tmp, s)) != cudaSuccess) return e;
@@ -578,7 +627,7 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
         }
     }
     k_items<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items,
-                                                 make_items ? 1 : 0, boxes, nbox);
+                                                 make_items ? 1 : 0, boxes, nbox, cell_active);
     note_launch();
     return cudaGetLastError();
 }
@@ -596,6 +645,41 @@ cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const flo
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s);
+}
+
+cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmax, int32_t *level,
+                      int *present, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_levels<<<blocks_for(n), kBlock, 0, s>>>(n, g.ncell, b.key, b.count, d, lmax, level, present);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t bin_build_ml(const Geometry &g, int64_t n, float4 *pos, const float4 *vel, float drift,
+                         const int32_t *level, const KickTable &kt, int *cell_active, const BinBuffers &b,
+                         int *d_flags, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cell_active, 0, sizeof(int) * g.ncell, s)) != cudaSuccess) return e;
+    if (n > 0) {
+        k_key<<<blocks_for(n), kBlock, 0, s>>>(n, pos, vel, drift, pos, g.Lf, g.inv_w, g.Ld, g.nc, b.key, b.rank,
+                                               b.count, d_flags, b.mass_flag);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_mark_active<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, level, kt, cell_active);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return bin_sort(n, g.ncell, b, true, nullptr, 1, s, cell_active);
+}
+
+cudaError_t drift_wrap(int64_t n, const float4 *src, const float4 *vel, float drift, float4 *dst, float Lf,
+                       int *d_flags, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_drift_wrap<<<blocks_for(n), kBlock, 0, s>>>(n, src, vel, drift, dst, Lf, d_flags);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int64_t ncell_total,

@@ -138,6 +138,13 @@ __device__ __forceinline__ bool wrap1(float &x, float Lf) {
     return true;
 }
 
+// Kick factor per kick count l (index 1..kMaxLevels) at one event of a
+// multi-level step: dt / l if particles with l kicks are kicked now, else 0.
+constexpr int kMaxLevels = 16;
+struct KickTable {
+    float h[kMaxLevels + 1];
+};
+
 // ---- batches of boxes (batch.cu) -----------------------------------------
 // One box of a batched tick, as the kernels see it.
 struct BoxDev {
@@ -192,6 +199,18 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
                             const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
                             const BinBuffers &b, int *d_flags, cudaStream_t s);
 
+// Multi-level stepping: kick counts from the cell densities of the last
+// binning (keys/counts in b), and a binning pass that streams pos in place by
+// `drift` and builds work items only for cells holding a particle that the
+// kick table kicks now.
+cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmax, int32_t *level,
+                      int *present, cudaStream_t s);
+cudaError_t bin_build_ml(const Geometry &g, int64_t n, float4 *pos, const float4 *vel, float drift,
+                         const int32_t *level, const KickTable &kt, int *cell_active, const BinBuffers &b,
+                         int *d_flags, cudaStream_t s);
+cudaError_t drift_wrap(int64_t n, const float4 *src, const float4 *vel, float drift, float4 *dst, float Lf,
+                       int *d_flags, cudaStream_t s);
+
 // Precision variant: positions as (cell id, FP32 in-cell offset, mass).
 // bin_build_ci optionally streams (FP64 on the global position) first.
 cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,
@@ -217,7 +236,14 @@ cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsign
                             cudaStream_t s);
 
 // ---- pair force (sr_force.cu) -------------------------------------------
-enum ForceMode : int { kModeForce = 0, kModeKickDrift = 1, kModePotential = 2, kModeBatch = 3, kModeKick = 4 };
+enum ForceMode : int {
+    kModeForce = 0,      // store the force (out[perm[i]])
+    kModeKickDrift = 1,  // kick + stream in sorted order
+    kModePotential = 2,  // per-particle pair potential
+    kModeBatch = 3,      // kick + stream, write back to pool rows (batches)
+    kModeKick = 4,       // kick only, velocities back to ids[i]
+    kModeKickLevels = 5  // kick by the table entry of the particle's kick count (multi-level)
+};
 
 struct ForceLaunch {
     const float4 *pos;          // sorted, wrapped
@@ -243,6 +269,9 @@ struct ForceLaunch {
     float4 *pos_pool = nullptr;
     float4 *vel_pool = nullptr;
     int *flags = nullptr;             // device status word (wrap errors)
+    // kModeKickLevels: kick count of each sorted particle, kick table
+    const int32_t *levels = nullptr;
+    KickTable kick{};
     // positions are in-cell offsets (precision variant); w = fl(L / nc)
     bool cell_offset = false;
     float w = 0.0f;

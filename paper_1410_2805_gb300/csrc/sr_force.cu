@@ -60,6 +60,8 @@ struct KParams {
     unsigned long long *within;
     const int *mass_flag;
     float w, w_lo, w_ratio;   // cell width w = w + w_lo (FP32 pair), w_ratio = w_lo / w
+    const int32_t *levels;
+    KickTable kick;
     const BoxDev *boxes;
     const int32_t *ids;
     float4 *pos_pool;
@@ -305,6 +307,16 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
             if (P.mode == kModeForce) {
                 int o = P.perm ? P.perm[i] : i;
                 P.out[o] = make_float4(gx, gy, gz, 0.0f);
+            } else if (P.mode == kModeKickLevels) {
+                const float hk = P.kick.h[P.levels[i]];
+                if (hk != 0.0f) {
+                    const int row = P.ids[i];
+                    float4 v = P.vel[i];
+                    v.x = __fmaf_rn(hk, gx, v.x);
+                    v.y = __fmaf_rn(hk, gy, v.y);
+                    v.z = __fmaf_rn(hk, gz, v.z);
+                    P.vel_pool[row] = v;
+                }
             } else if (P.mode == kModeKick) {
                 const int row = P.ids[i];
                 float4 v = P.vel[i];
@@ -450,6 +462,8 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.vel_pool = fl.vel_pool;
     P.flags = fl.flags;
     P.w = fl.w;
+    P.levels = fl.levels;
+    P.kick = fl.kick;
     P.w_lo = fl.w_lo;
     P.w_ratio = fl.w != 0.0f ? fl.w_lo / fl.w : 0.0f;
     const bool eps0 = !(fc.eps > 0.0f);

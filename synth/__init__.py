@@ -84,13 +84,14 @@ def gaussian_velocities(n: int, seed: int, sigma: float = 0.1) -> np.ndarray:
 
 
 def zeldovich(ng: int, seed: int, L: float | None = None, sigma_delta: float = 1.0,
-              index: float = -2.0, return_stats: bool = False):
+              index: float = -2.0, return_stats: bool = False, return_f64: bool = False):
     """ng^3 particles displaced from the lattice q = (i + 1/2) dx by the
     Zel'dovich field psi of a Gaussian random density delta with power
     spectrum P(k) ~ k^index (k = 0 mode zero), normalised so that delta has
     standard deviation sigma_delta on the ng^3 grid:
         psi(k) = i k delta(k) / k^2,   x = q + psi(q)   (so div psi = -delta).
-    Returns n x 4 FP32 positions (and optionally a stats dict)."""
+    Returns n x 4 FP32 positions (and optionally a stats dict); with
+    return_f64, the FP64 positions (n x 3, wrapped into [0, L)) instead."""
     try:
         import scipy.fft as fft
         kw = dict(workers=-1)
@@ -129,6 +130,10 @@ def zeldovich(ng: int, seed: int, L: float | None = None, sigma_delta: float = 1
         shape[a] = ng
         x[..., a] = q1.reshape(shape) + psi
         del psi
+    if return_f64:
+        x = np.mod(x.reshape(-1, 3), L)
+        x[x >= L] = 0.0
+        return x
     pos = as_pos4(_wrap_f32(x.reshape(-1, 3), L))
     if return_stats:
         return pos, dict(rms_displacement=math.sqrt(rms), sigma_delta=sigma_delta, L=L)
