@@ -517,7 +517,7 @@ def run_ours(args):
             "gpu_launches": st["kernel_launches"],
             "roofline": roofline, "e2e": e2e, "clocks": clk,
             "autotune": {"variant": tuning["chosen"], "force_ms_by_variant": tuning["times_ms"],
-                         "variants": "(blocks/SM, unroll) = (6,deep), (8,light), (6,light), (5,deep)"}}
+                         "variants": "(blocks/SM, inner loop) = (5,indexed), (4,indexed), (5,pointer-stepped), (4,pointer-stepped)"}}
     if not args.no_batch:
         line["batched"] = run_batched(torch, hacc, ctx, split)
     if not args.no_served:

@@ -71,12 +71,16 @@ __device__ __forceinline__ int item_shape(uint32_t n) {
     if (n <= 8) return (3 << 4) | 2;
     if (n <= 12) return (3 << 4) | 3;
     if (n <= 16) return (3 << 4) | 4;
+    if (n <= 20) return (3 << 4) | 5;
     if (n <= 24) return (2 << 4) | 3;
     if (n <= 32) return (2 << 4) | 4;
+    if (n <= 40) return (2 << 4) | 5;
     if (n <= 48) return (1 << 4) | 3;
     if (n <= 64) return (1 << 4) | 4;
+    if (n <= 80) return (1 << 4) | 5;
     if (n <= 96) return 3;
-    return 4;
+    if (n <= 128) return 4;
+    return 5;
 }
 
 __device__ __forceinline__ uint32_t items_of(uint32_t cnt) {

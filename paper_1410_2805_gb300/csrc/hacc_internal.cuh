@@ -19,9 +19,9 @@ enum DeviceFlag : int {
 };
 
 // Chunking of a chaining-mesh cell into force work items: a cell of n
-// particles is one item when n <= 128, else ceil(n/128) items of up to 128
+// particles is one item when n <= 160, else ceil(n/160) items of up to 160
 // particles; each item is processed by one warp (see item_shape in bin.cu).
-constexpr int kItemMax = 128;
+constexpr int kItemMax = 160;
 
 struct Scratch {
     char *base = nullptr;

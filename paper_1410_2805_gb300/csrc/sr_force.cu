@@ -7,8 +7,8 @@
 // cut at s < r_cut^2 with a select instead of a branch (the paper folds the
 // cutoff test into the force evaluation the same way, with fsel).
 //
-// GPU mapping.  Work item = up to 128 particles of one cell (one warp; K of
-// them per lane, K = 1..4 by cell occupancy).  Because cells are numbered
+// GPU mapping.  Work item = up to 160 particles of one cell (one warp; K of
+// them per lane, K = 1..5, in 1-8 lane groups, by cell occupancy).  Because cells are numbered
 // x-fastest, the three cells (ix-1, ix, ix+1) of each of the 9 (dy, dz) rows
 // are one contiguous run of the cell-sorted particle array, so an item
 // streams 9 runs (a second run when the row wraps in x).  Each run is staged
@@ -77,6 +77,11 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 // Accumulate the interaction of one staged j (already image-shifted) with
 // the K i-particles of this lane.
+// The pair-force constants, held in registers for the whole item.
+struct PairConsts {
+    float eps, T, q0, q1, q2, q3, q4, q5;
+};
+
 // Accumulate a += f * r on the pairs inside the cutoff only (predicated FMAs,
 // the select of Sec. 3.1): pairs outside never touch the sums, whatever f is.
 __device__ __forceinline__ void acc_if_inside(float &ax, float &ay, float &az, float t, float T, float f, float dx,
@@ -105,7 +110,8 @@ __device__ __forceinline__ void acc_if_inside_nonzero(float &ax, float &ay, floa
 
 // UM: all masses equal (the mass is applied once in the epilogue).
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM>
-__device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, int iself, int lpg, const float (&xi)[K],
+__device__ __forceinline__ void interact(const KParams &P, const PairConsts &C, float4 pj, int jidx, int iself, int lpg,
+                                         const float (&xi)[K],
                                          const float (&yi)[K], const float (&zi)[K], float (&ax)[K],
                                          float (&ay)[K], float (&az)[K], unsigned &cnt) {
 #pragma unroll
@@ -113,9 +119,9 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
         float dx = pj.x - xi[k];
         float dy = pj.y - yi[k];
         float dz = pj.z - zi[k];
-        float t = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, P.eps)));
+        float t = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, C.eps)));
         float r = rsqrt_approx(t);
-        const bool in = t < P.T;
+        const bool in = t < C.T;
         if (POT) {
             // phi(s) = -(t)^(-1/2) - U(t) - phi0, U in t = s + eps
             float u = __fmaf_rn(P.u6, t, P.u5);
@@ -128,15 +134,21 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
             const bool self = jidx == iself + lpg * k;   // i's own row (sorted index)
             ax[k] += (in && !self) ? ph * pj.w : 0.0f;
         } else {
-            float q = __fmaf_rn(P.q5, t, P.q4);
-            q = __fmaf_rn(q, t, P.q3);
-            q = __fmaf_rn(q, t, P.q2);
-            q = __fmaf_rn(q, t, P.q1);
-            q = __fmaf_rn(q, t, P.q0);
+            float q = __fmaf_rn(C.q5, t, C.q4);
+            q = __fmaf_rn(q, t, C.q3);
+            q = __fmaf_rn(q, t, C.q2);
+            q = __fmaf_rn(q, t, C.q1);
+            q = __fmaf_rn(q, t, C.q0);
             float f = __fmaf_rn(r * r, r, -q);          // t^(-3/2) - P5
             if (!UM) f *= pj.w;
-            if (EPS0) acc_if_inside_nonzero(ax[k], ay[k], az[k], t, P.T, f, dx, dy, dz);
-            else acc_if_inside(ax[k], ay[k], az[k], t, P.T, f, dx, dy, dz);
+            // the cutoff as a predicate on the accumulating FMAs (the paper's
+            // fsel select, without the select): pairs outside never touch the sums
+            const bool use = EPS0 ? (t < C.T && t > 0.0f) : (t < C.T);
+            if (use) {
+                ax[k] = __fmaf_rn(f, dx, ax[k]);
+                ay[k] = __fmaf_rn(f, dy, ay[k]);
+                az[k] = __fmaf_rn(f, dz, az[k]);
+            }
         }
         if (COUNT) cnt += (in && jidx != iself + lpg * k) ? 1u : 0u;   // j != i
     }
@@ -147,7 +159,12 @@ __device__ __forceinline__ void interact(const KParams &P, float4 pj, int jidx, 
 // (tx, ty, tz): image shift added to this lane's i coordinates.  The warp is
 // split into G = 2^lg lane groups; group g takes the staged entries g, g+G,
 // g+2G, ... (consecutive float4 addresses across groups: no bank conflicts).
-template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
+// U selects the inner-loop form (the autotuner picks): 0 deep-unrolled and
+// 1 light-unrolled indexed loops, 2 pointer-stepped loop, 3 the lane-group
+// count as a compile-time constant (LGC >= 0; four times the code, which
+// measured 2x slower from instruction-cache misses, so not among the variants).
+// Every form visits the same entries in the same order: bitwise equal sums.
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI, int LGC = -1>
 __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
                                             float ty, float tz, int b1, int b2, int d0, int iself, int lg, int grp,
                                             const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
@@ -155,8 +172,10 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
                                             float4 *buf, int lane) {
     const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
+    if (LGC >= 0) lg = LGC;
     const int G = 1 << lg;
     const int lpg = 32 >> lg;
+    (void)G;
     float xs[K], ys[K], zs[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -164,36 +183,56 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
         ys[k] = ishift ? __fadd_rn(yi[k], ty) : yi[k];
         zs[k] = ishift ? __fadd_rn(zi[k], tz) : zi[k];
     }
-    for (int j0 = ja; j0 < jb; j0 += 32) {
-        const int nj = min(32, jb - j0);
-        // entries past the run are far away with zero mass: outside the cutoff
-        float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-        if (lane < nj) {
-            v = P.pos[j0 + lane];
-            if (CI) {
-                // in-cell offsets: move j into the frame of i's cell (cell steps of w;
-                // the x step depends on which of the run's cells j sits in)
-                // w = w_hi + w_lo exactly: the step is applied in two adds
-                const int j = j0 + lane;
-                const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
-                v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
-                v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
-                v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
-            } else if (jshift) {
-                v.x = __fadd_rn(v.x, sx);
-                v.y = __fadd_rn(v.y, sy);
-                v.z = __fadd_rn(v.z, sz);
+    const PairConsts C{P.eps, P.T, P.q0, P.q1, P.q2, P.q3, P.q4, P.q5};
+    // tiles of up to 32 G entries (each lane stages G of them)
+    const int tile = 32 << lg;
+    for (int j0 = ja; j0 < jb; j0 += tile) {
+        const int nj = min(tile, jb - j0);
+        const int tg = (nj + G - 1) >> lg;   // entries per group (interleaved)
+        for (int e = lane; e < tile; e += 32) {
+            // entries past the run are far away with zero mass: outside the cutoff
+            float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+            if (e < nj) {
+                v = P.pos[j0 + e];
+                if (CI) {
+                    // in-cell offsets: move j into the frame of i's cell (cell steps
+                    // of w = w_hi + w_lo, applied in two adds; the x step depends on
+                    // which of the run's cells j sits in)
+                    const int j = j0 + e;
+                    const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
+                    v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
+                    v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
+                    v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
+                } else if (jshift) {
+                    v.x = __fadd_rn(v.x, sx);
+                    v.y = __fadd_rn(v.y, sy);
+                    v.z = __fadd_rn(v.z, sz);
+                }
+            }
+            buf[e] = v;
+        }
+        __syncwarp();
+        constexpr int kUnroll = U == 1 ? (K >= 3 ? 1 : 2) : (K >= 5 ? 1 : (K >= 3 ? 2 : 4));
+        if (U == 2) {
+            // pointer-stepped loop over the group's entries g, g+G, ...
+            const float4 *q = buf + grp;
+            int e = grp;
+#pragma unroll kUnroll
+            for (int t = 0; t < tg; ++t) {
+                interact<K, COUNT, POT, EPS0, UM>(P, C, *q, e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax, ay, az,
+                                                  cnt);
+                q += G;
+                e += G;
+            }
+        } else {
+            const float4 *bp = buf + grp;
+#pragma unroll kUnroll
+            for (int t = 0; t < tg; ++t) {
+                const int e = grp + (t << lg);
+                interact<K, COUNT, POT, EPS0, UM>(P, C, bp[t << lg], e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax,
+                                                  ay, az, cnt);
             }
         }
-        buf[lane] = v;
-        __syncwarp();
-        const int trips = (nj + G - 1) >> lg;
-        int e = grp;
-        // unroll depth: policy U = 0 deep (2 for K >= 3, else 4), U = 1 light (1 / 2)
-        constexpr int kUnroll = U == 0 ? (K >= 3 ? 2 : 4) : (K >= 3 ? 1 : 2);
-#pragma unroll kUnroll
-        for (int t = 0; t < trips; ++t, e += G)
-            interact<K, COUNT, POT, EPS0, UM>(P, buf[e], e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
         __syncwarp();
     }
 }
@@ -275,8 +314,33 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
                 }
                 b2 = (cx == 0 || cx == nc - 1) ? jb : row[cx + 1];
                 if (CI) six = 0.0f;
-                process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
-                                                            lg, grp, xi, yi, zi, ax, ay, az, cnt, buf, lane);
+                if (U == 3) {
+                    switch (lg) {
+                        case 0:
+                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 0>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
+                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
+                                                                           cnt, buf, lane);
+                            break;
+                        case 1:
+                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 1>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
+                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
+                                                                           cnt, buf, lane);
+                            break;
+                        case 2:
+                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 2>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
+                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
+                                                                           cnt, buf, lane);
+                            break;
+                        default:
+                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 3>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
+                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
+                                                                           cnt, buf, lane);
+                            break;
+                    }
+                } else {
+                    process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0,
+                                                                iself, lg, grp, xi, yi, zi, ax, ay, az, cnt, buf, lane);
+                }
             }
         }
     }
@@ -371,7 +435,8 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lan
             case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
             case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
             case 3: process_item<3, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
-            default: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
+            case 4: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
+            default: process_item<5, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
         }
     }
 }
@@ -380,7 +445,7 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lan
 // 5 -> 96 registers per thread); U: unroll policy.  The autotuner picks.
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
 __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
-    __shared__ float4 tiles[kWarps][32];
+    __shared__ float4 tiles[kWarps][32 * 8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
     // equal masses (flag left 0 by the binning pass): apply the mass once per i
@@ -392,8 +457,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
 
 // Positions as (cell, in-cell offset): the precision variant.
 template <bool EPS0>
-__global__ void __launch_bounds__(kThreads, 6) k_sr_force_ci(KParams P) {
-    __shared__ float4 tiles[kWarps][32];
+__global__ void __launch_bounds__(kThreads, 5) k_sr_force_ci(KParams P) {
+    __shared__ float4 tiles[kWarps][32 * 8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
     if (P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
@@ -414,14 +479,16 @@ cudaError_t launch_one(const KParams &P, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Variants 0..kForceVariants-1: (MINB, U) = (6, 0), (8, 1), (6, 1), (5, 0).
+// Variants 0..kForceVariants-1: (MINB, U) = (5, 0), (4, 0), (5, 2), (4, 2).
+// (A blocked tile layout, each group's entries contiguous at a padded stride,
+// measured 5% slower than these and changes the summation order.)
 template <bool COUNT, bool POT, bool EPS0>
 cudaError_t launch_variant(const KParams &P, int variant, int num_sms, cudaStream_t s) {
     switch (variant) {
-        case 1: return launch_one<COUNT, POT, EPS0, 8, 1>(P, num_sms, s);
-        case 2: return launch_one<COUNT, POT, EPS0, 6, 1>(P, num_sms, s);
-        case 3: return launch_one<COUNT, POT, EPS0, 5, 0>(P, num_sms, s);
-        default: return launch_one<COUNT, POT, EPS0, 6, 0>(P, num_sms, s);
+        case 1: return launch_one<COUNT, POT, EPS0, 4, 0>(P, num_sms, s);
+        case 2: return launch_one<COUNT, POT, EPS0, 5, 2>(P, num_sms, s);
+        case 3: return launch_one<COUNT, POT, EPS0, 4, 2>(P, num_sms, s);
+        default: return launch_one<COUNT, POT, EPS0, 5, 0>(P, num_sms, s);
     }
 }
 
@@ -481,7 +548,7 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
         note_launch();
         return cudaGetLastError();
     }
-    if (pot) return eps0 ? launch_one<false, true, true, 6, 0>(P, num_sms, s) : launch_one<false, true, false, 6, 0>(P, num_sms, s);
+    if (pot) return eps0 ? launch_one<false, true, true, 5, 0>(P, num_sms, s) : launch_one<false, true, false, 5, 0>(P, num_sms, s);
     if (count) return eps0 ? launch_variant<true, false, true>(P, v, num_sms, s) : launch_variant<true, false, false>(P, v, num_sms, s);
     return eps0 ? launch_variant<false, false, true>(P, v, num_sms, s) : launch_variant<false, false, false>(P, v, num_sms, s);
 }
