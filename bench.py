@@ -131,6 +131,25 @@ class ClockSampler:
                 "power_w_max": max(r["power"] for r in rows)}
 
 
+def reduce_over_ranks(value: float, dist, op: str = "max", device: str = "cuda") -> float:
+    """Max (the timing rule) or sum of a per-rank number over all ranks; the
+    identity without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_rate(local_work: float, local_ms: float, dist, device: str = "cuda") -> dict:
+    """Whole-job rate of independent replicas: work summed over ranks divided
+    by the slowest rank's time (weak scaling, no data-path collective)."""
+    ms = reduce_over_ranks(local_ms, dist, "max", device)
+    work = reduce_over_ranks(local_work, dist, "sum", device)
+    return {"ms": ms, "work": work, "rate": work / (ms / 1e3) if ms > 0 else 0.0}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -291,6 +310,47 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
             "gpu_launches": st["kernel_launches"], "replay_bitwise_equal": same}
 
 
+def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7):
+    """One 128^3 blob-mixture box (blobs of 256), step 0.04: 4 uniform SKS
+    sub-cycles per step against the multi-level step with kick counts
+    l = floor(floor(rho/rho0)/d) + 1 <= 4 (Eq. (kicks)); device time per step."""
+    import numpy as np
+
+    import synth
+    L = 128.0
+    pos0 = synth.blob_mixture_scaled(128 ** 3, L, seed=seed)
+    vel0 = synth.gaussian_velocities(128 ** 3, seed=seed)
+    box = hacc.Box(L=L)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for mode in ("plain", "multilevel"):
+        P, V = torch.from_numpy(pos0).cuda(), torch.from_numpy(vel0).cuda()
+        lev = torch.zeros(len(pos0), dtype=torch.int32, device="cuda")
+
+        def one():
+            if mode == "plain":
+                ctx.subcycle(box, split, P, V, 0.04, lmax)
+            else:
+                ctx.subcycle_ml(box, split, P, V, 0.04, d, lmax, levels=lev)
+        one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["ms_per_step_" + mode] = e0.elapsed_time(e1) / steps
+        if mode == "multilevel":
+            h = np.bincount(lev.cpu().numpy(), minlength=lmax + 1)[1:]
+            out["kick_count_fractions"] = [float(x) for x in h / h.sum()]
+            out["force_evaluations_per_particle"] = float((np.arange(1, lmax + 1) * h).sum() / h.sum())
+    ctx.sync()
+    out["speedup"] = out["ms_per_step_plain"] / out["ms_per_step_multilevel"]
+    out["workload"] = "128^3 blob mixture (blobs of 256, sigma 0.5), box 128, d = %d, l_max = %d" % (d, lmax)
+    return out
+
+
 def run_served(torch, hacc, ctx, split, rate, window, cap_s, seed=5, max_active=64 << 20, pool_gb=150.0):
     """Poisson arrivals (rate/s over `window` s) of runs with N in {32^3, 64^3,
     128^3, 256^3} (blob mixture, blobs of 256) and 5-50 SR sub-cycles of step
@@ -442,11 +502,7 @@ def run_ours(args):
     st = ctx.stats_read(reset=True)
     ctx.stats_enable(timing=False, counting=False)
     final_p, final_v = pos.clone(), vel.clone()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = reduce_over_ranks(ms, dist, "max")
 
     # ---- deterministic replay with pair counting (untimed) ----
     pos.copy_(snap_p)
@@ -474,11 +530,7 @@ def run_ours(args):
             else:
                 ctx.subcycle_host(box, split, hp, hv, dt, n_c)
         barrier()
-        t_e2e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = reduce_over_ranks(time.perf_counter() - t0, dist, "max")
         e2e_same = bool(torch.equal(hp.cuda(), final_p) and torch.equal(hv.cuda(), final_v))
         e2e = {"value": world * within / t_e2e, "unit": "pair interactions/s",
                "h2d_bytes_per_step": 2 * n * 16, "d2h_bytes_per_step": 2 * n * 16,
@@ -486,7 +538,7 @@ def run_ours(args):
 
     # ---- numbers ----
     secs = ms_max / 1e3
-    value = world * within / secs
+    value = replica_rate(within, ms, dist)["rate"]
     psteps = world * n * n_c * args.steps / secs
     peaks = measured_peaks()
     num_sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -520,6 +572,7 @@ def run_ours(args):
                          "variants": "(blocks/SM, inner loop) = (5,indexed), (4,indexed), (5,pointer-stepped), (4,pointer-stepped)"}}
     if not args.no_batch:
         line["batched"] = run_batched(torch, hacc, ctx, split)
+        line["multilevel"] = run_multilevel(torch, hacc, ctx, split)
     if not args.no_served:
         served = run_served(torch, hacc, ctx, split, rate=50.0, window=args.served_window, cap_s=args.served_cap)
         served["vs_plain_pairs_per_s"] = served["pair_interactions_per_s"] / (within / secs)
