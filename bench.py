@@ -310,15 +310,20 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
             "gpu_launches": st["kernel_launches"], "replay_bitwise_equal": same}
 
 
-def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7):
-    """One 128^3 blob-mixture box (blobs of 256), step 0.04: 4 uniform SKS
-    sub-cycles per step against the multi-level step with kick counts
-    l = floor(floor(rho/rho0)/d) + 1 <= 4 (Eq. (kicks)); device time per step."""
+def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, workload="blob128", dt=0.04, skin=0.05):
+    """One 128^3 box: lmax uniform SKS sub-cycles per step against the
+    multi-level step with kick counts l = floor(floor(rho/rho0)/d) + 1 <= lmax
+    (Eq. (kicks)); device time per step, and the pair-kernel share of it."""
     import numpy as np
 
     import synth
     L = 128.0
-    pos0 = synth.blob_mixture_scaled(128 ** 3, L, seed=seed)
+    if workload == "blob128":
+        pos0 = synth.blob_mixture_scaled(128 ** 3, L, seed=seed)
+        desc = "128^3 blob mixture (blobs of 256, sigma 0.5), box 128"
+    else:
+        pos0 = synth.zeldovich(128, seed=seed, L=L)
+        desc = "128^3 Zel'dovich (P(k)~k^-2, sigma_delta=1), box 128"
     vel0 = synth.gaussian_velocities(128 ** 3, seed=seed)
     box = hacc.Box(L=L)
     stream = torch.cuda.current_stream()
@@ -329,11 +334,12 @@ def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7):
 
         def one():
             if mode == "plain":
-                ctx.subcycle(box, split, P, V, 0.04, lmax)
+                ctx.subcycle(box, split, P, V, dt, lmax)
             else:
-                ctx.subcycle_ml(box, split, P, V, 0.04, d, lmax, levels=lev)
+                ctx.subcycle_ml(box, split, P, V, dt, d, lmax, skin=skin, levels=lev)
         one()
         torch.cuda.synchronize()
+        ctx.stats_read(reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
@@ -341,13 +347,23 @@ def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7):
         e1.record(stream)
         torch.cuda.synchronize()
         out["ms_per_step_" + mode] = e0.elapsed_time(e1) / steps
+        st = ctx.stats_read(reset=True)
+        out["kernel_launches_per_step_" + mode] = st["kernel_launches"] / steps
+        # one more step with the pair launches timed (events around each)
+        ctx.stats_enable(timing=True)
+        one()
+        st = ctx.stats_read(reset=True)
+        ctx.stats_enable()
+        out["force_ms_per_step_" + mode] = st["force_ms"]
         if mode == "multilevel":
+            out["rebins_per_step"] = st["ml_rebins"]
             h = np.bincount(lev.cpu().numpy(), minlength=lmax + 1)[1:]
             out["kick_count_fractions"] = [float(x) for x in h / h.sum()]
             out["force_evaluations_per_particle"] = float((np.arange(1, lmax + 1) * h).sum() / h.sum())
     ctx.sync()
     out["speedup"] = out["ms_per_step_plain"] / out["ms_per_step_multilevel"]
-    out["workload"] = "128^3 blob mixture (blobs of 256, sigma 0.5), box 128, d = %d, l_max = %d" % (d, lmax)
+    out["workload"] = "%s, step %g, d = %d, l_max = %d, skin %g r_cut (%d^3 cells)" % (
+        desc, dt, d, lmax, skin, hacc.ml_mesh_cells(L, split.r_cut, skin))
     return out
 
 

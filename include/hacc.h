@@ -163,18 +163,30 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
 hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                       int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream);
 
-/* Multi-level short-range step (Sec. 3.1, Eq. (kicks)): the density of each
- * particle's chaining-mesh cell at the start of the step, rho / rho0 =
- * count nc^3 / n, sets its kick count l = floor(floor(rho/rho0) / d) + 1
- * (integers; d <= 0 gives every particle lmax), capped at lmax (1..16).  A
- * particle with l kicks is kicked by dt/l at times (2k+1)/(2l) dt, k < l; all
- * particles stream together between the union of those times over the counts
- * that occur (one host synchronisation per step reads which occur), so each
- * streams by dt in total.  At an event only the cells holding a kicked particle
- * get work items.  level_out (nullable, device, n) receives the kick counts. */
+/* Multi-level short-range step (Sec. 3.1, Eq. (kicks)).  The step bins the
+ * particles on a chaining mesh of nc_ml^3 cells, nc_ml = hacc_ml_mesh_cells(L,
+ * r_cut, skin) (box->nc instead when that is nonzero), whose cells are at
+ * least r_cut (1 + skin) wide.  The density of each particle's cell at the
+ * start of the step, rho / rho0 = count nc_ml^3 / n, sets its kick count
+ * l = floor(floor(rho/rho0) / d) + 1 (integers; d <= 0 gives every particle
+ * lmax), capped at lmax (1..16).  A particle with l kicks is kicked by dt/l at
+ * times (2k+1)/(2l) dt, k < l; all particles stream together between the union
+ * of those times over the counts that occur, so each streams by dt in total.
+ * The mesh is kept while the particles move (as the paper keeps its tree):
+ * at each event the largest per-axis drift from the binned positions is read
+ * (one host synchronisation per event), and only when it passes half the
+ * cell's excess width over r_cut are the particles rebinned.  At an event only
+ * the cells holding a kicked particle get work items.  skin must be finite
+ * and >= 0.  level_out (nullable, device, n) receives the kick counts. */
 hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
-                             float *vel, double dt, int32_t d, int32_t lmax, int32_t *level_out,
+                             float *vel, double dt, int32_t d, int32_t lmax, float skin, int32_t *level_out,
                              hacc_stream_t stream);
+
+/* Cells per side of the multi-level step's chaining mesh for box->nc = 0:
+ * hacc_mesh_cells(L, r_cut (1 + skin)) when that gives at least 3 cells and
+ * fewer than hacc_mesh_cells(L, r_cut), else hacc_mesh_cells(L, r_cut).
+ * Returns -1 where hacc_mesh_cells(L, r_cut) does. */
+int32_t hacc_ml_mesh_cells(double L, float r_cut, float skin);
 
 /* Long-range PM acceleration alone (with G = 1): acc[n] receives (ax, ay, az, 0).
  * ng = 0 in the box means ng = round(L); ng must be even, 4 <= ng <= 2048.
@@ -351,6 +363,7 @@ typedef struct {
     double force_ms;          /* summed CUDA-event durations of those launches (timing on) */
     uint64_t candidate_pairs; /* 27-cell candidate pairs of those launches (counting on) */
     uint64_t within_pairs;    /* ordered pairs (i, j != i) inside the cutoff (counting on) */
+    int64_t ml_rebins;        /* rebinnings inside multi-level steps after their first binning */
 } hacc_stats;
 
 /* timing != 0: record a CUDA event pair on the call's stream around every

@@ -44,7 +44,7 @@ class _Split(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("force_launches", ctypes.c_int64),
                 ("force_ms", ctypes.c_double), ("candidate_pairs", ctypes.c_uint64),
-                ("within_pairs", ctypes.c_uint64)]
+                ("within_pairs", ctypes.c_uint64), ("ml_rebins", ctypes.c_int64)]
 
 
 class _BatchBox(ctypes.Structure):
@@ -155,7 +155,9 @@ def lib():
             "hacc_step_host": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), ctypes.POINTER(_Pm), i64, p,
                                     p, d, i32, p]),
             "hacc_stats_enable": (st, [p, ctypes.c_int, ctypes.c_int]),
-            "hacc_subcycle_ml": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, d, i32, i32, p, p]),
+            "hacc_subcycle_ml": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, d, i32, i32,
+                                      ctypes.c_float, p, p]),
+            "hacc_ml_mesh_cells": (i32, [d, ctypes.c_float, ctypes.c_float]),
             "hacc_ci_from_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p, p]),
             "hacc_ci_to_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p]),
             "hacc_sr_force_ci": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, p]),
@@ -191,6 +193,11 @@ def default_split() -> Split:
 
 def mesh_cells(L: float, r_cut: float) -> int:
     return int(lib().hacc_mesh_cells(float(L), float(r_cut)))
+
+
+def ml_mesh_cells(L: float, r_cut: float, skin: float = 0.05) -> int:
+    """Cells per side of the multi-level step's chaining mesh (box nc = 0)."""
+    return int(lib().hacc_ml_mesh_cells(float(L), float(r_cut), float(skin)))
 
 
 def _split_of(split) -> Split:
@@ -324,7 +331,7 @@ class Context:
         st = _Stats()
         self._check(lib().hacc_stats_read(self._h, ctypes.byref(st), int(reset)), "hacc_stats_read")
         return dict(kernel_launches=st.kernel_launches, force_launches=st.force_launches, force_ms=st.force_ms,
-                    candidate_pairs=st.candidate_pairs, within_pairs=st.within_pairs)
+                    candidate_pairs=st.candidate_pairs, within_pairs=st.within_pairs, ml_rebins=st.ml_rebins)
 
     def scratch_bytes(self) -> int:
         return int(lib().hacc_ctx_scratch_bytes(self._h))
@@ -371,14 +378,16 @@ class Context:
                                         _ptr(pos), _ptr(vel), float(dt), int(n_sub), self._stream(stream)),
                     "hacc_subcycle")
 
-    def subcycle_ml(self, box: Box, split, pos, vel, dt: float, d: int, lmax: int, levels=None, stream=None):
-        """One multi-level short-range step (kick counts from cell densities, Eq. (kicks))."""
+    def subcycle_ml(self, box: Box, split, pos, vel, dt: float, d: int, lmax: int, skin: float = 0.05,
+                    levels=None, stream=None):
+        """One multi-level short-range step (kick counts from cell densities, Eq. (kicks)) on a
+        chaining mesh of ml_mesh_cells(L, r_cut, skin) cells per side."""
         _dev_rows(pos, "pos")
         _dev_rows(vel, "vel")
         sp = _split_of(split)
         self._check(lib().hacc_subcycle_ml(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
-                                           _ptr(pos), _ptr(vel), float(dt), int(d), int(lmax), _ptr(levels),
-                                           self._stream(stream)), "hacc_subcycle_ml")
+                                           _ptr(pos), _ptr(vel), float(dt), int(d), int(lmax), float(skin),
+                                           _ptr(levels), self._stream(stream)), "hacc_subcycle_ml")
 
     def step(self, box: Box, split, pm: PM, pos, vel, dt: float, n_c: int, stream=None):
         _dev_rows(pos, "pos")

@@ -182,11 +182,20 @@ struct Work {
     double *diag;
     int *cell_active;   // multi-level: cells with a particle kicked at this event
     int *present;       // multi-level: kick counts that occur
+    // multi-level: binned reference positions, a second velocity buffer,
+    // input rows (two buffers) and cell ids in sorted order
+    float4 *R, *V2;
+    int32_t *I1, *I2, *Ks;
     BinBuffers b;
 };
 
-size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w) {
+size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w, bool ml = false) {
     Carver c(base);
+    w->R = ml ? c.take<float4>(n) : nullptr;
+    w->V2 = ml ? c.take<float4>(n) : nullptr;
+    w->I1 = ml ? c.take<int32_t>(n) : nullptr;
+    w->I2 = ml ? c.take<int32_t>(n) : nullptr;
+    w->Ks = ml ? c.take<int32_t>(n) : nullptr;
     w->P = c.take<float4>(n);
     w->Ps = c.take<float4>(n);
     w->V = dyn ? c.take<float4>(n) : nullptr;
@@ -198,15 +207,16 @@ size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w) {
     w->phi = c.take<float>(n);
     w->diag = c.take<double>(5);
     w->cell_active = c.take<int>(ncell);
-    w->present = c.take<int>(kMaxLevels + 1);
+    w->present = c.take<int>(kMaxLevels + 3);
     carve_bin(c, n, ncell, &w->b);
     return c.off + 256;
 }
 
-hacc_status prepare_work(hacc_ctx *ctx, int64_t n, const Geometry &g, bool dyn, cudaStream_t s, Work *w) {
-    size_t need = carve_work(nullptr, n, g.ncell, dyn, w);
+hacc_status prepare_work(hacc_ctx *ctx, int64_t n, const Geometry &g, bool dyn, cudaStream_t s, Work *w,
+                         bool ml = false) {
+    size_t need = carve_work(nullptr, n, g.ncell, dyn, w, ml);
     HACC_TRY(ensure_scratch(ctx, need, s));
-    carve_work(ctx->scratch.base, n, g.ncell, dyn, w);
+    carve_work(ctx->scratch.base, n, g.ncell, dyn, w, ml);
     return HACC_OK;
 }
 
@@ -217,6 +227,9 @@ hacc_status check_particles(hacc_ctx *ctx, int64_t n, const void *a, const void 
     if (n > 0 && b && !aligned16(b)) return set_error(ctx, HACC_EINVAL, "particle array not 16-byte aligned");
     return HACC_OK;
 }
+
+hacc_status launch_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, bool counted,
+                         cudaStream_t s);
 
 // The short-range force on sorted positions (w->Ps, cell starts and items in w->b).
 hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, Work *w, int mode,
@@ -243,8 +256,14 @@ hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts
         HACC_CUDA(candidate_count(g, w->b.cell_start, ctx->d_pairs, s), "candidate count");
         fl.within = ctx->d_pairs + 1;
     }
+    return launch_force(ctx, g, fc, fl, mode != kModePotential, s);
+}
+
+// One pair-kernel launch; timed with an event pair when timing is on.
+hacc_status launch_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, bool counted,
+                         cudaStream_t s) {
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (ctx->timing && mode != kModePotential) {
+    if (ctx->timing && counted) {
         if (ctx->ev_free.empty()) {
             cudaEvent_t a, b;
             HACC_CUDA(cudaEventCreate(&a), "cudaEventCreate");
@@ -256,7 +275,7 @@ hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts
         HACC_CUDA(cudaEventRecord(ev.first, s), "cudaEventRecord");
     }
     HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch");
-    if (mode != kModePotential) ctx->force_launches++;
+    if (counted) ctx->force_launches++;
     if (ev.first) {
         HACC_CUDA(cudaEventRecord(ev.second, s), "cudaEventRecord");
         ctx->ev_used.push_back(ev);
@@ -331,6 +350,13 @@ hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream) {
 }
 
 int32_t hacc_mesh_cells(double L, float r_cut) { return default_nc(L, r_cut); }
+
+int32_t hacc_ml_mesh_cells(double L, float r_cut, float skin) {
+    const int32_t nc = default_nc(L, r_cut);
+    if (nc < 0 || !(skin > 0) || !std::isfinite(skin)) return nc;
+    const int32_t nc2 = default_nc(L, (double)r_cut * (1.0 + (double)skin));
+    return (nc2 >= 3 && nc2 < nc) ? nc2 : nc;
+}
 
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant) {
     HACC_TRY(enter(ctx));
@@ -416,7 +442,9 @@ hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset) {
     out->force_ms = ctx->force_ms;
     out->candidate_pairs = pairs[0];
     out->within_pairs = pairs[1];
+    out->ml_rebins = ctx->ml_rebins;
     if (reset) {
+        ctx->ml_rebins = 0;
         ctx->launches = 0;
         ctx->force_launches = 0;
         ctx->force_ms = 0.0;
@@ -629,36 +657,17 @@ hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     return HACC_OK;
 }
 
-hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
-                             float *vel, double dt, int32_t d, int32_t lmax, int32_t *level_out,
-                             hacc_stream_t stream) {
-    HACC_TRY(enter(ctx));
-    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
-    if (lmax < 1 || lmax > kMaxLevels) return set_error(ctx, HACC_EINVAL, "lmax must be in [1, 16]");
-    if (!std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
-    Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
-    ForceConsts fc;
-    HACC_TRY(make_force_consts(ctx, split, g, &fc));
-    HACC_TRY(check_particles(ctx, n, pos_m, vel));
-    if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
-    if (n == 0) return HACC_OK;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    Work w;
-    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
-    float4 *pos_in = reinterpret_cast<float4 *>(pos_m);
-    float4 *V = reinterpret_cast<float4 *>(vel);
-    int32_t *level = w.ID;   // kick count per particle, input order
-    // kick counts from the cell densities at the start of the step
-    HACC_CUDA(bin_build(g, n, pos_in, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
-    HACC_CUDA(cudaMemsetAsync(w.present, 0, sizeof(int) * (kMaxLevels + 1), s), "memset");
-    HACC_CUDA(ml_levels(g, n, w.b, d, lmax, level, w.present, s), "kick counts");
-    if (level_out)
-        HACC_CUDA(cudaMemcpyAsync(level_out, level, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "levels out");
-    int present[kMaxLevels + 1];
-    HACC_CUDA(cudaMemcpyAsync(present, w.present, sizeof present, cudaMemcpyDeviceToHost, s), "levels present");
-    HACC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    // event times (2k+1)/(2l) dt of the counts present, as reduced fractions
+namespace {
+
+// One event of the multi-level step: its time and the kick of each count.
+struct MlEvent {
+    double t;
+    KickTable kt;
+};
+
+// Events (2k+1)/(2l) dt, k < l, over the kick counts l that occur, in time
+// order with duplicates merged (exact reduced fractions).
+std::vector<MlEvent> ml_schedule(const int *present, int lmax, double dt) {
     std::vector<std::pair<int64_t, int64_t>> ev;
     for (int l = 1; l <= lmax; ++l) {
         if (!present[l]) continue;
@@ -675,23 +684,109 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     std::sort(ev.begin(), ev.end(), [](const std::pair<int64_t, int64_t> &p, const std::pair<int64_t, int64_t> &q) {
         return p.first * q.second < q.first * p.second;
     });
-    double t_prev = 0.0;
+    std::vector<MlEvent> out;
     for (auto &e : ev) {
-        const double te = dt * (double)e.first / (double)e.second;
-        KickTable kt;
+        MlEvent m;
+        m.t = dt * (double)e.first / (double)e.second;
         for (int l = 0; l <= kMaxLevels; ++l) {
-            kt.h[l] = 0.0f;
+            m.kt.h[l] = 0.0f;
             if (l >= 1 && l <= lmax && present[l] && (2 * l * e.first) % e.second == 0 &&
                 ((2 * l * e.first) / e.second) % 2 == 1)
-                kt.h[l] = (float)(dt / l);
+                m.kt.h[l] = (float)(dt / l);
         }
-        // stream everyone to te, rebin, items for cells with a particle kicked now
-        HACC_CUDA(bin_build_ml(g, n, w.P, V, (float)(te - t_prev), level, kt, w.cell_active, w.b, ctx->d_flags, s),
-                  "binning");
-        t_prev = te;
-        HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, V, w.Vs, level, w.IDs, s), "gather");
+        out.push_back(m);
+    }
+    return out;
+}
+
+}  // namespace
+
+hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
+                             float *vel, double dt, int32_t d, int32_t lmax, float skin, int32_t *level_out,
+                             hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (lmax < 1 || lmax > kMaxLevels) return set_error(ctx, HACC_EINVAL, "lmax must be in [1, 16]");
+    if (!std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
+    if (!(skin >= 0) || !std::isfinite(skin)) return set_error(ctx, HACC_EINVAL, "skin must be finite and >= 0");
+    Geometry g;
+    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, pos_m, vel));
+    if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
+    if (n == 0) return HACC_OK;
+    // the step's mesh: cells at least r_cut (1 + skin) wide where the box allows
+    if (box->nc == 0) {
+        const int32_t nc = hacc_ml_mesh_cells(g.Ld, split->r_cut, skin);
+        g.nc = nc;
+        g.ncell = (int64_t)nc * nc * nc;
+        g.inv_w = (float)((double)nc / g.Ld);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w, true));
+    float4 *pos_in = reinterpret_cast<float4 *>(pos_m);
+    float4 *V = reinterpret_cast<float4 *>(vel);
+    unsigned *disp_bits = reinterpret_cast<unsigned *>(w.present + kMaxLevels + 1);
+
+    // The mesh is kept while the particles move: as long as none has drifted
+    // more than `half` along an axis from where it was binned, every pair
+    // within r_cut is still in neighbouring cells (the paper keeps its tree
+    // for the whole sub-cycle in the same way, Sec. 3.1).  Between events the
+    // sorted arrays are only streamed in place; the largest drift is read at
+    // every event and the particles are rebinned only when it passed `half`.
+    const double half = 0.5 * (g.Ld / g.nc - (double)split->r_cut);
+    float4 *Ps = w.Ps, *Vs = w.Vs, *Vt = w.V2, *Ref = w.R;
+    int32_t *lev_s = w.IDs, *lev_t = w.ID, *id_s = w.I1, *id_t = w.I2;   // kick counts start in lev_s, input order
+    // bin src (wrapped into w.P), then gather every array into its other buffer and swap the two
+    auto rebin = [&](const float4 *src, bool first) -> hacc_status {
+        if (!first) HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
+        HACC_CUDA(gather_ml(n, w.b.perm, w.P, Ps, Ref, first ? V : Vs, Vt, lev_s, lev_t, first ? nullptr : id_s, id_t,
+                            w.b.key, w.Ks, s),
+                  "gather");
+        std::swap(Vs, Vt);
+        std::swap(lev_s, lev_t);
+        std::swap(id_s, id_t);
+        HACC_CUDA(cudaMemsetAsync(disp_bits, 0, sizeof(unsigned), s), "memset");
+        return HACC_OK;
+    };
+    // kick counts from the cell densities at the start of the step
+    HACC_CUDA(bin_build(g, n, pos_in, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
+    HACC_CUDA(cudaMemsetAsync(w.present, 0, sizeof(int) * (kMaxLevels + 1), s), "memset");
+    HACC_CUDA(ml_levels(g, n, w.b, d, lmax, lev_s, w.present, s), "kick counts");
+    if (level_out)
+        HACC_CUDA(cudaMemcpyAsync(level_out, lev_s, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "levels out");
+    HACC_TRY(rebin(pos_in, true));
+    int present[kMaxLevels + 1];
+    HACC_CUDA(cudaMemcpyAsync(present, w.present, sizeof present, cudaMemcpyDeviceToHost, s), "levels present");
+    HACC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    const std::vector<MlEvent> ev = ml_schedule(present, lmax, dt);
+
+    double t_prev = 0.0;
+    for (const MlEvent &e : ev) {
+        HACC_CUDA(stream_sorted(n, Ps, Vs, (float)(e.t - t_prev), Ref, disp_bits, s), "stream");
+        t_prev = e.t;
+        unsigned bits = 0;
+        HACC_CUDA(cudaMemcpyAsync(&bits, disp_bits, sizeof bits, cudaMemcpyDeviceToHost, s), "largest drift");
+        HACC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        float drift;
+        std::memcpy(&drift, &bits, sizeof drift);
+        if (!std::isfinite(drift)) return set_error(ctx, HACC_EDOMAIN, "non-finite position in the multi-level step");
+        if ((double)drift > half * (1.0 - 1e-5)) {
+            HACC_TRY(rebin(Ps, false));
+            ctx->ml_rebins++;
+        }
+        // particles kicked now; a small launch splits its cells into smaller
+        // items (down to one lane per particle) so that enough warps share it
+        int64_t kicked = 0;
+        for (int l = 1; l <= lmax; ++l)
+            if (e.kt.h[l] != 0.0f) kicked += present[l];
+        const int64_t per_item = kicked / ((int64_t)ctx->num_sms * 64);
+        const int cap = (int)std::max<int64_t>(kItemMin, std::min<int64_t>(kItemMax, per_item / 32 * 32));
+        HACC_CUDA(items_active(g, n, w.Ks, lev_s, e.kt, w.cell_active, w.b, cap, s), "work items");
         ForceLaunch fl;
-        fl.pos = w.Ps;
+        fl.pos = Ps;
         fl.items = w.b.items;
         fl.n_items = w.b.n_items;
         fl.cell_start = w.b.cell_start;
@@ -699,7 +794,7 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         fl.mode = kModeKickLevels;
         fl.out = nullptr;
         fl.perm = nullptr;
-        fl.vel = w.Vs;
+        fl.vel = Vs;   // kicked in place, sorted order
         fl.pos_next = nullptr;
         fl.h_kick = 0.f;
         fl.h_drift = 0.f;
@@ -707,16 +802,16 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
         fl.mass_flag = w.b.mass_flag;
         fl.variant = ctx->variant;
-        fl.ids = w.b.perm;
-        fl.vel_pool = V;
-        fl.levels = w.IDs;
-        fl.kick = kt;
+        fl.ids = nullptr;
+        fl.vel_pool = nullptr;
+        fl.levels = lev_s;
+        fl.kick = e.kt;
         fl.flags = ctx->d_flags;
-        HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch (multi-level)");
-        ctx->force_launches++;
+        HACC_TRY(launch_force(ctx, g, fc, fl, true, s));
     }
-    // last stream, wrapped, into the caller's positions
-    HACC_CUDA(drift_wrap(n, w.P, V, (float)(dt - t_prev), pos_in, g.Lf, ctx->d_flags, s), "closing stream");
+    // last stream, then wrapped positions and velocities back to input order
+    HACC_CUDA(stream_sorted(n, Ps, Vs, (float)(dt - t_prev), nullptr, nullptr, s), "closing stream");
+    HACC_CUDA(scatter_rows(n, id_s, Ps, pos_in, Vs, V, g.Lf, ctx->d_flags, s), "scatter");
     return HACC_OK;
 }
 

@@ -83,17 +83,18 @@ __device__ __forceinline__ int item_shape(uint32_t n) {
     return 5;
 }
 
-__device__ __forceinline__ uint32_t items_of(uint32_t cnt) {
-    return cnt == 0 ? 0u : (cnt <= (uint32_t)kItemMax ? 1u : (cnt + kItemMax - 1) / kItemMax);
+// Work items of a cell of cnt particles, at most cap (kItemMin..kItemMax) per item.
+__device__ __forceinline__ uint32_t items_of(uint32_t cnt, uint32_t cap) {
+    return cnt == 0 ? 0u : (cnt <= cap ? 1u : (cnt + cap - 1) / cap);
 }
 
 __global__ void __launch_bounds__(kBlock) k_pack(int64_t ncell, const uint32_t *__restrict__ count,
                                                   const int *__restrict__ cell_active,
-                                                  unsigned long long *__restrict__ packed) {
+                                                  unsigned long long *__restrict__ packed, uint32_t cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     uint32_t k = count[c];
-    const uint32_t it = (cell_active && !cell_active[c]) ? 0u : items_of(k);
+    const uint32_t it = (cell_active && !cell_active[c]) ? 0u : items_of(k, cap);
     packed[c] = (unsigned long long)k | ((unsigned long long)it << 32);
 }
 
@@ -305,14 +306,14 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
                                                    int32_t *__restrict__ cell_start, int4 *__restrict__ items,
                                                    int32_t *__restrict__ n_items, int make_items,
                                                    const BoxDev *__restrict__ boxes, int nbox,
-                                                   const int *__restrict__ cell_active) {
+                                                   const int *__restrict__ cell_active, uint32_t cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) {
         cell_start[ncell] = (int32_t)n;
         if (make_items) {
             unsigned long long last = packed[ncell - 1];
             const bool on = !cell_active || cell_active[ncell - 1];
-            *n_items = (int32_t)((last >> 32) + (on ? items_of(count[ncell - 1]) : 0u));
+            *n_items = (int32_t)((last >> 32) + (on ? items_of(count[ncell - 1], cap) : 0u));
         }
     }
     if (c >= ncell) return;
@@ -333,11 +334,11 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
         }
         box = lo;
     }
-    uint32_t m = items_of(cnt);
+    uint32_t m = items_of(cnt, cap);
     for (uint32_t q = 0; q < m; ++q) {
-        uint32_t ni = cnt - q * kItemMax;
-        ni = ni > (uint32_t)kItemMax ? (uint32_t)kItemMax : ni;
-        items[it + q] = make_int4((int)c, (int)(s + q * kItemMax), (int)ni, (box << 8) | item_shape(ni));
+        uint32_t ni = cnt - q * cap;
+        ni = ni > cap ? cap : ni;
+        items[it + q] = make_int4((int)c, (int)(s + q * cap), (int)ni, (box << 8) | item_shape(ni));
     }
 }
 
@@ -389,6 +390,27 @@ __global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__r
     p_out[k] = p_in[i];
     if (v_out) v_out[k] = v_in[i];
     if (id_out) id_out[k] = id_in ? id_in[i] : i;
+}
+
+// Multi-level rebinning: gather positions (and a copy, the binned reference),
+// velocities, kick counts, input rows and cell ids into the new sorted order.
+__global__ void __launch_bounds__(kBlock) k_gather_ml(int64_t n, const int32_t *__restrict__ perm,
+                                                       const float4 *__restrict__ p_in, float4 *__restrict__ p_out,
+                                                       float4 *__restrict__ ref_out, const float4 *__restrict__ v_in,
+                                                       float4 *__restrict__ v_out, const int32_t *__restrict__ lev_in,
+                                                       int32_t *__restrict__ lev_out, const int32_t *__restrict__ id_in,
+                                                       int32_t *__restrict__ id_out, const int32_t *__restrict__ key,
+                                                       int32_t *__restrict__ key_out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t i = perm[k];
+    const float4 p = p_in[i];
+    p_out[k] = p;
+    ref_out[k] = p;
+    v_out[k] = v_in[i];
+    lev_out[k] = lev_in[i];
+    id_out[k] = id_in ? id_in[i] : i;
+    key_out[k] = key[i];
 }
 
 __global__ void __launch_bounds__(kBlock) k_scatter(int64_t n, const int32_t *__restrict__ id,
@@ -535,16 +557,47 @@ __global__ void __launch_bounds__(kBlock) k_ci_to_f64(int64_t n, const int32_t *
 __global__ void __launch_bounds__(kBlock) k_levels(int64_t n, int64_t ncell, const int32_t *__restrict__ key,
                                                     const uint32_t *__restrict__ count, int d, int lmax,
                                                     int32_t *__restrict__ level, int *__restrict__ present) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t l = lmax;
-    if (d > 0) {
-        const int64_t ratio = (int64_t)count[key[i]] * ncell / n;
-        l = ratio / d + 1;
-        if (l > lmax) l = lmax;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int l = 0;   // 0: no particle on this lane
+    if (i < n) {
+        int64_t q = lmax;
+        if (d > 0) {
+            const int64_t ratio = (int64_t)count[key[i]] * ncell / n;
+            q = ratio / d + 1;
+            if (q > lmax) q = lmax;
+        }
+        l = (int)q;
+        level[i] = l;
     }
-    level[i] = (int32_t)l;
-    present[l] = 1;
+    // particles per kick count, one atomic per distinct count in the warp
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    if (l > 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&present[l], __popc(peers));
+}
+
+// Stream sorted positions in place, without wrapping (inside one multi-level
+// step a particle stays near the cell it was binned in; the step's end wraps).
+// With p0, also the largest per-axis distance from the binned position (as
+// float bits) into *disp.
+__global__ void __launch_bounds__(kBlock) k_stream(int64_t n, float4 *__restrict__ pos,
+                                                    const float4 *__restrict__ vel, float drift,
+                                                    const float4 *__restrict__ p0, unsigned *disp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.0f;
+    if (i < n) {
+        float4 p = pos[i];
+        const float4 v = vel[i];
+        p.x = __fmaf_rn(drift, v.x, p.x);
+        p.y = __fmaf_rn(drift, v.y, p.y);
+        p.z = __fmaf_rn(drift, v.z, p.z);
+        pos[i] = p;
+        if (p0) {
+            const float4 q = p0[i];
+            m = fmaxf(fabsf(p.x - q.x), fmaxf(fabsf(p.y - q.y), fabsf(p.z - q.z)));
+        }
+    }
+    if (!p0) return;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(disp, __float_as_uint(m));
 }
 
 // Cells that hold a particle kicked at this event.
@@ -556,22 +609,6 @@ __global__ void __launch_bounds__(kBlock) k_mark_active(int64_t n, const int32_t
     if (kt.h[level[i]] != 0.0f) cell_active[key[i]] = 1;
 }
 
-__global__ void __launch_bounds__(kBlock) k_drift_wrap(int64_t n, const float4 *__restrict__ src,
-                                                        const float4 *__restrict__ vel, float drift,
-                                                        float4 *__restrict__ dst, float Lf, int *flags) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float4 p = src[i];
-    const float4 v = vel[i];
-    p.x = __fmaf_rn(drift, v.x, p.x);
-    p.y = __fmaf_rn(drift, v.y, p.y);
-    p.z = __fmaf_rn(drift, v.z, p.z);
-    bool ok = wrap1(p.x, Lf);
-    ok &= wrap1(p.y, Lf);
-    ok &= wrap1(p.z, Lf);
-    if (!ok) atomicOr(flags, kFlagDomain);
-    dst[i] = p;
-}
 
 inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
 
@@ -587,7 +624,7 @@ size_t scan_tmp_elems(int64_t len) {
     return total + 1;
 }
 
-int64_t max_items(int64_t n, int64_t ncell) { return ncell + n / kItemMax + 1; }
+int64_t max_items(int64_t n, int64_t ncell) { return ncell + n / kItemMin + 1; }
 
 void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
     b->key = c.take<int32_t>(n);
@@ -611,7 +648,7 @@ namespace {
 cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_items, const BoxDev *boxes, int nbox,
                      cudaStream_t s, const int *cell_active = nullptr) {
     cudaError_t e;
-    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, cell_active, b.packed);
+    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, cell_active, b.packed, (uint32_t)kItemMax);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(b.packed, ncell, b.scan_tmp, s)) != cudaSuccess) return e;
@@ -631,7 +668,7 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
         }
     }
     k_items<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items,
-                                                 make_items ? 1 : 0, boxes, nbox, cell_active);
+                                                 make_items ? 1 : 0, boxes, nbox, cell_active, (uint32_t)kItemMax);
     note_launch();
     return cudaGetLastError();
 }
@@ -659,32 +696,35 @@ cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, 
     return cudaGetLastError();
 }
 
-cudaError_t bin_build_ml(const Geometry &g, int64_t n, float4 *pos, const float4 *vel, float drift,
-                         const int32_t *level, const KickTable &kt, int *cell_active, const BinBuffers &b,
-                         int *d_flags, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(cell_active, 0, sizeof(int) * g.ncell, s)) != cudaSuccess) return e;
-    if (n > 0) {
-        k_key<<<blocks_for(n), kBlock, 0, s>>>(n, pos, vel, drift, pos, g.Lf, g.inv_w, g.Ld, g.nc, b.key, b.rank,
-                                               b.count, d_flags, b.mass_flag);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_mark_active<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, level, kt, cell_active);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return bin_sort(n, g.ncell, b, true, nullptr, 1, s, cell_active);
-}
-
-cudaError_t drift_wrap(int64_t n, const float4 *src, const float4 *vel, float drift, float4 *dst, float Lf,
-                       int *d_flags, cudaStream_t s) {
+cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift, const float4 *p0, unsigned *disp,
+                          cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_drift_wrap<<<blocks_for(n), kBlock, 0, s>>>(n, src, vel, drift, dst, Lf, d_flags);
+    k_stream<<<blocks_for(n), kBlock, 0, s>>>(n, pos, vel, drift, p0, disp);
     note_launch();
     return cudaGetLastError();
 }
+
+// Work items of the current binning, only for cells marked active.
+cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
+                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, cudaStream_t s) {
+    if (cap < kItemMin || cap > kItemMax) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(cell_active, 0, sizeof(int) * g.ncell, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_mark_active<<<blocks_for(n), kBlock, 0, s>>>(n, key, level, kt, cell_active);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_pack<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, b.count, cell_active, b.packed, (uint32_t)cap);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive(b.packed, g.ncell, b.scan_tmp, s)) != cudaSuccess) return e;
+    k_items<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items, 1,
+                                                   nullptr, 1, cell_active, (uint32_t)cap);
+    note_launch();
+    return cudaGetLastError();
+}
+
 
 cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int64_t ncell_total,
                             const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
@@ -747,6 +787,16 @@ cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, fl
                           float4 *v_out, const int32_t *id_in, int32_t *id_out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_gather<<<blocks_for(n), kBlock, 0, s>>>(n, perm, p_in, p_out, v_in, v_out, id_in, id_out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t gather_ml(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, float4 *ref_out,
+                      const float4 *v_in, float4 *v_out, const int32_t *lev_in, int32_t *lev_out, const int32_t *id_in,
+                      int32_t *id_out, const int32_t *key, int32_t *key_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_gather_ml<<<blocks_for(n), kBlock, 0, s>>>(n, perm, p_in, p_out, ref_out, v_in, v_out, lev_in, lev_out, id_in,
+                                                 id_out, key, key_out);
     note_launch();
     return cudaGetLastError();
 }

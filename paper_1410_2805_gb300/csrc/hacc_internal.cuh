@@ -21,7 +21,8 @@ enum DeviceFlag : int {
 // Chunking of a chaining-mesh cell into force work items: a cell of n
 // particles is one item when n <= 160, else ceil(n/160) items of up to 160
 // particles; each item is processed by one warp (see item_shape in bin.cu).
-constexpr int kItemMax = 160;
+constexpr int kItemMax = 160;   // particles per work item at most (5 per lane)
+constexpr int kItemMin = 32;    // smallest item cap (smaller launches split cells finer)
 
 struct Scratch {
     char *base = nullptr;
@@ -47,6 +48,7 @@ struct hacc_ctx {
     // statistics (hacc_stats_*)
     bool timing = false, counting = false;
     int64_t launches = 0, force_launches = 0;
+    int64_t ml_rebins = 0;
     int variant = 0;                          // pair-kernel variant (hacc_tune)
     double force_ms = 0.0;
     unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
@@ -200,16 +202,19 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
                             const BinBuffers &b, int *d_flags, cudaStream_t s);
 
 // Multi-level stepping: kick counts from the cell densities of the last
-// binning (keys/counts in b), and a binning pass that streams pos in place by
-// `drift` and builds work items only for cells holding a particle that the
-// kick table kicks now.
+// binning (keys/counts in b; present[l] += particles with l kicks); in-place stream of
+// sorted positions with the largest drift from the binned ones; the rebinning
+// gather; and work items of the current binning for the cells that hold a
+// particle kicked now (keys and kick counts in one common order).
 cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmax, int32_t *level,
                       int *present, cudaStream_t s);
-cudaError_t bin_build_ml(const Geometry &g, int64_t n, float4 *pos, const float4 *vel, float drift,
-                         const int32_t *level, const KickTable &kt, int *cell_active, const BinBuffers &b,
-                         int *d_flags, cudaStream_t s);
-cudaError_t drift_wrap(int64_t n, const float4 *src, const float4 *vel, float drift, float4 *dst, float Lf,
-                       int *d_flags, cudaStream_t s);
+cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift, const float4 *p0, unsigned *disp,
+                          cudaStream_t s);
+cudaError_t gather_ml(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, float4 *ref_out,
+                      const float4 *v_in, float4 *v_out, const int32_t *lev_in, int32_t *lev_out, const int32_t *id_in,
+                      int32_t *id_out, const int32_t *key, int32_t *key_out, cudaStream_t s);
+cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
+                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, cudaStream_t s);
 
 // Precision variant: positions as (cell id, FP32 in-cell offset, mass).
 // bin_build_ci optionally streams (FP64 on the global position) first.

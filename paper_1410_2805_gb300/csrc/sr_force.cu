@@ -75,40 +75,14 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
-// Accumulate the interaction of one staged j (already image-shifted) with
-// the K i-particles of this lane.
 // The pair-force constants, held in registers for the whole item.
 struct PairConsts {
     float eps, T, q0, q1, q2, q3, q4, q5;
 };
 
-// Accumulate a += f * r on the pairs inside the cutoff only (predicated FMAs,
-// the select of Sec. 3.1): pairs outside never touch the sums, whatever f is.
-__device__ __forceinline__ void acc_if_inside(float &ax, float &ay, float &az, float t, float T, float f, float dx,
-                                              float dy, float dz) {
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.lt.f32 p, %3, %4;\n\t"
-        "@p fma.rn.f32 %0, %5, %6, %0;\n\t"
-        "@p fma.rn.f32 %1, %5, %7, %1;\n\t"
-        "@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
-        : "+f"(ax), "+f"(ay), "+f"(az)
-        : "f"(t), "f"(T), "f"(f), "f"(dx), "f"(dy), "f"(dz));
-}
-
-// Same, and also skip t == 0 (with eps = 0, a pair at zero separation).
-__device__ __forceinline__ void acc_if_inside_nonzero(float &ax, float &ay, float &az, float t, float T, float f,
-                                                      float dx, float dy, float dz) {
-    asm("{\n\t.reg .pred p;\n\t"
-        "setp.lt.f32 p, %3, %4;\n\t"
-        "setp.gt.and.f32 p, %3, 0f00000000, p;\n\t"
-        "@p fma.rn.f32 %0, %5, %6, %0;\n\t"
-        "@p fma.rn.f32 %1, %5, %7, %1;\n\t"
-        "@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
-        : "+f"(ax), "+f"(ay), "+f"(az)
-        : "f"(t), "f"(T), "f"(f), "f"(dx), "f"(dy), "f"(dz));
-}
-
-// UM: all masses equal (the mass is applied once in the epilogue).
+// Accumulate the interaction of one staged j (already image-shifted) with
+// the K i-particles of this lane.  UM: all masses equal (the mass is applied
+// once in the epilogue).
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM>
 __device__ __forceinline__ void interact(const KParams &P, const PairConsts &C, float4 pj, int jidx, int iself, int lpg,
                                          const float (&xi)[K],
@@ -374,12 +348,12 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
             } else if (P.mode == kModeKickLevels) {
                 const float hk = P.kick.h[P.levels[i]];
                 if (hk != 0.0f) {
-                    const int row = P.ids[i];
                     float4 v = P.vel[i];
                     v.x = __fmaf_rn(hk, gx, v.x);
                     v.y = __fmaf_rn(hk, gy, v.y);
                     v.z = __fmaf_rn(hk, gz, v.z);
-                    P.vel_pool[row] = v;
+                    if (P.ids) P.vel_pool[P.ids[i]] = v;   // back to input order
+                    else P.vel[i] = v;                      // in place, sorted order
                 }
             } else if (P.mode == kModeKick) {
                 const int row = P.ids[i];

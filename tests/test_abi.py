@@ -58,3 +58,17 @@ def test_mesh_cells_rule():
     assert hacc.mesh_cells(512.0, rc) == 164
     assert hacc.mesh_cells(8.0, rc) == -1            # fewer than 3 cells
     assert hacc.mesh_cells(3.0 * rc, rc) == -1        # width would equal r_cut: one fewer
+
+
+def test_ml_mesh_cells_rule():
+    import paper_1410_2805_gb300 as hacc
+    rc = hacc.default_split().r_cut
+    # cells at least 1.05 r_cut wide: floor(128 / (1.05 rc)) = 39 < 41
+    assert hacc.mesh_cells(128.0, rc) == 41
+    assert hacc.ml_mesh_cells(128.0, rc, 0.05) == 39
+    assert hacc.ml_mesh_cells(128.0, rc, 0.0) == 41
+    # the slack of 20 / 6 already covers 5 %: unchanged
+    assert hacc.ml_mesh_cells(20.0, rc, 0.05) == hacc.mesh_cells(20.0, rc) == 6
+    # never below 3 cells: a 3-cell box keeps 3
+    assert hacc.ml_mesh_cells(10.0, rc, 0.5) == 3
+    assert hacc.ml_mesh_cells(8.0, rc, 0.05) == -1
