@@ -128,28 +128,73 @@ __device__ __forceinline__ void interact(const KParams &P, const PairConsts &C, 
     }
 }
 
+// Axis-aligned bounds of an item's i-particles (after the run's i shift).
+struct Bounds {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+// Entries of a staged tile: up to 32 G entries, plus room for the up to 31
+// that a compaction round carries past a full tile.
+constexpr int kTileCap = 32 * 8 + 32;
+
+// Run the warp's i-particles against the staged entries [0, nj) of buf:
+// group g takes entries g, g+G, g+2G, ... (consecutive float4 addresses
+// across groups: no bank conflicts).  ids (nullable): sorted index of each
+// entry, for the j != i tests of the counting and potential forms.
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U>
+__device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, const float4 *buf, const int *ids,
+                                         int nj, int iself, int lg, int grp, const float (&xs)[K],
+                                         const float (&ys)[K], const float (&zs)[K], float (&ax)[K], float (&ay)[K],
+                                         float (&az)[K], unsigned &cnt) {
+    const int G = 1 << lg;
+    const int lpg = 32 >> lg;
+    const int tg = (nj + G - 1) >> lg;   // entries per group (interleaved)
+    constexpr int kUnroll = U == 1 ? (K >= 3 ? 1 : 2) : (K >= 5 ? 1 : (K >= 3 ? 2 : 4));
+    if (U == 2) {
+        // pointer-stepped loop over the group's entries g, g+G, ...
+        const float4 *q = buf + grp;
+        int e = grp;
+#pragma unroll kUnroll
+        for (int t = 0; t < tg; ++t) {
+            const int jidx = (COUNT || POT) && e < nj ? ids[e] : -1;
+            interact<K, COUNT, POT, EPS0, UM>(P, C, *q, jidx, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
+            q += G;
+            e += G;
+        }
+    } else {
+        const float4 *bp = buf + grp;
+#pragma unroll kUnroll
+        for (int t = 0; t < tg; ++t) {
+            const int e = grp + (t << lg);
+            const int jidx = (COUNT || POT) && e < nj ? ids[e] : -1;
+            interact<K, COUNT, POT, EPS0, UM>(P, C, bp[t << lg], jidx, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
+        }
+    }
+}
+
 // Stream one run [ja, jb) of consecutive sorted particles through the warp's
 // shared tile.  (sx, sy, sz): image shift added to the staged j coordinates;
 // (tx, ty, tz): image shift added to this lane's i coordinates.  The warp is
-// split into G = 2^lg lane groups; group g takes the staged entries g, g+G,
-// g+2G, ... (consecutive float4 addresses across groups: no bank conflicts).
-// U selects the inner-loop form (the autotuner picks): 0 deep-unrolled and
-// 1 light-unrolled indexed loops, 2 pointer-stepped loop, 3 the lane-group
-// count as a compile-time constant (LGC >= 0; four times the code, which
-// measured 2x slower from instruction-cache misses, so not among the variants).
-// Every form visits the same entries in the same order: bitwise equal sums.
-template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI, int LGC = -1>
+// split into G = 2^lg lane groups that share the i-particles and split the j.
+// Staging keeps only the j that can be within the cutoff of some i of the
+// item: farther than r_cut (with a margin far above rounding) from the
+// item's bounding box, a j is outside the cutoff of every i and would add
+// exactly nothing, so dropping it leaves every pair sum unchanged; the kept j
+// are compacted in order (ballot + prefix count) into full tiles.  With
+// in-cell offsets (CI) every j is staged.  U selects the inner-loop form (the
+// autotuner picks): 0 deep-unrolled and 1 light-unrolled indexed loops, 2
+// pointer-stepped loop; every form visits the same entries in the same order.
+// (The lane-group count as a compile-time constant, four times the code,
+// measured 2x slower from instruction-cache misses.)
+template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
                                             float ty, float tz, int b1, int b2, int d0, int iself, int lg, int grp,
-                                            const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
-                                            float (&ax)[K], float (&ay)[K], float (&az)[K], unsigned &cnt,
-                                            float4 *buf, int lane) {
+                                            const Bounds &bb, const float (&xi)[K], const float (&yi)[K],
+                                            const float (&zi)[K], float (&ax)[K], float (&ay)[K], float (&az)[K],
+                                            unsigned &cnt, float4 *buf, int *ids, int lane) {
     const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
-    if (LGC >= 0) lg = LGC;
     const int G = 1 << lg;
-    const int lpg = 32 >> lg;
-    (void)G;
     float xs[K], ys[K], zs[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -158,61 +203,99 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
         zs[k] = ishift ? __fadd_rn(zi[k], tz) : zi[k];
     }
     const PairConsts C{P.eps, P.T, P.q0, P.q1, P.q2, P.q3, P.q4, P.q5};
-    // tiles of up to 32 G entries (each lane stages G of them)
+    const float4 dummy = make_float4(1e18f, 1e18f, 1e18f, 0.0f);   // far away, zero mass
     const int tile = 32 << lg;
-    for (int j0 = ja; j0 < jb; j0 += tile) {
-        const int nj = min(tile, jb - j0);
-        const int tg = (nj + G - 1) >> lg;   // entries per group (interleaved)
-        for (int e = lane; e < tile; e += 32) {
-            // entries past the run are far away with zero mass: outside the cutoff
-            float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-            if (e < nj) {
-                v = P.pos[j0 + e];
-                if (CI) {
+    if (CI) {
+        for (int j0 = ja; j0 < jb; j0 += tile) {
+            const int nj = min(tile, jb - j0);
+            for (int e = lane; e < tile; e += 32) {
+                float4 v = dummy;
+                if (e < nj) {
                     // in-cell offsets: move j into the frame of i's cell (cell steps
                     // of w = w_hi + w_lo, applied in two adds; the x step depends on
                     // which of the run's cells j sits in)
+                    v = P.pos[j0 + e];
                     const int j = j0 + e;
                     const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
                     v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
                     v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
                     v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
-                } else if (jshift) {
+                }
+                buf[e] = v;
+                if (COUNT || POT) ids[e] = j0 + e;
+            }
+            __syncwarp();
+            run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
+            __syncwarp();
+        }
+        return;
+    }
+    // the item's bounds in this run's frame (monotone rounding keeps them bounds)
+    const float lx = ishift ? __fadd_rn(bb.lx, tx) : bb.lx, hx = ishift ? __fadd_rn(bb.hx, tx) : bb.hx;
+    const float ly = ishift ? __fadd_rn(bb.ly, ty) : bb.ly, hy = ishift ? __fadd_rn(bb.hy, ty) : bb.hy;
+    const float lz = ishift ? __fadd_rn(bb.lz, tz) : bb.lz, hz = ishift ? __fadd_rn(bb.hz, tz) : bb.hz;
+    const float keep_r2 = P.T * 1.001f + 1e-3f;
+    const unsigned below = (1u << lane) - 1u;
+    int fill = 0;   // staged entries, warp-uniform
+    int j0 = ja;
+#pragma unroll 1
+    while (true) {
+        // stage 32 candidates at a time until a tile is full or the run ends
+#pragma unroll 1
+        while (fill < tile && j0 < jb) {
+            const int j = j0 + lane;
+            bool keep = false;
+            float4 v = dummy;
+            if (j < jb) {
+                v = P.pos[j];
+                if (jshift) {
                     v.x = __fadd_rn(v.x, sx);
                     v.y = __fadd_rn(v.y, sy);
                     v.z = __fadd_rn(v.z, sz);
                 }
+                const float ex = fmaxf(fmaxf(lx - v.x, v.x - hx), 0.0f);
+                const float ey = fmaxf(fmaxf(ly - v.y, v.y - hy), 0.0f);
+                const float ez = fmaxf(fmaxf(lz - v.z, v.z - hz), 0.0f);
+                keep = __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, ez * ez)) < keep_r2;
             }
-            buf[e] = v;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int at = fill + __popc(m & below);
+                buf[at] = v;
+                if (COUNT || POT) ids[at] = j;
+            }
+            fill += __popc(m);
+            j0 += 32;
+        }
+        const int nj = min(fill, tile);
+        if (nj == 0) break;
+        // a short last tile is padded to whole lane groups with far, massless entries
+        const int padded = (nj + G - 1) & ~(G - 1);
+        if (nj < tile && lane < padded - nj) buf[nj + lane] = dummy;
+        __syncwarp();
+        run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
+        __syncwarp();
+        // carry the entries past the tile to the front
+        const int rest = fill - nj;
+        float4 cv = dummy;
+        int ci = 0;
+        if (lane < rest) {
+            cv = buf[nj + lane];
+            if (COUNT || POT) ci = ids[nj + lane];
         }
         __syncwarp();
-        constexpr int kUnroll = U == 1 ? (K >= 3 ? 1 : 2) : (K >= 5 ? 1 : (K >= 3 ? 2 : 4));
-        if (U == 2) {
-            // pointer-stepped loop over the group's entries g, g+G, ...
-            const float4 *q = buf + grp;
-            int e = grp;
-#pragma unroll kUnroll
-            for (int t = 0; t < tg; ++t) {
-                interact<K, COUNT, POT, EPS0, UM>(P, C, *q, e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax, ay, az,
-                                                  cnt);
-                q += G;
-                e += G;
-            }
-        } else {
-            const float4 *bp = buf + grp;
-#pragma unroll kUnroll
-            for (int t = 0; t < tg; ++t) {
-                const int e = grp + (t << lg);
-                interact<K, COUNT, POT, EPS0, UM>(P, C, bp[t << lg], e < nj ? j0 + e : -1, iself, lpg, xs, ys, zs, ax,
-                                                  ay, az, cnt);
-            }
+        if (lane < rest) {
+            buf[lane] = cv;
+            if (COUNT || POT) ids[lane] = ci;
         }
-        __syncwarp();
+        fill = rest;
+        if (j0 >= jb && fill == 0) break;
     }
+    __syncwarp();
 }
 
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
-__device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane, float m_uniform) {
+__device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids, int lane, float m_uniform) {
     // geometry: the single box of the call, or this item's box of a batch
     int nc = P.nc;
     float L = P.L;
@@ -245,6 +328,27 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
     }
     unsigned cnt = 0;
     const int iself = i0 + slot;          // sorted index of this lane's k = 0 particle
+    // bounding box of the item's particles (for the j culling of the runs)
+    Bounds bb{1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (slot + lpg * k < ni) {
+            bb.lx = fminf(bb.lx, xi[k]);
+            bb.hx = fmaxf(bb.hx, xi[k]);
+            bb.ly = fminf(bb.ly, yi[k]);
+            bb.hy = fmaxf(bb.hy, yi[k]);
+            bb.lz = fminf(bb.lz, zi[k]);
+            bb.hz = fmaxf(bb.hz, zi[k]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bb.lx = fminf(bb.lx, __shfl_xor_sync(0xffffffffu, bb.lx, o));
+        bb.hx = fmaxf(bb.hx, __shfl_xor_sync(0xffffffffu, bb.hx, o));
+        bb.ly = fminf(bb.ly, __shfl_xor_sync(0xffffffffu, bb.ly, o));
+        bb.hy = fmaxf(bb.hy, __shfl_xor_sync(0xffffffffu, bb.hy, o));
+        bb.lz = fminf(bb.lz, __shfl_xor_sync(0xffffffffu, bb.lz, o));
+        bb.hz = fmaxf(bb.hz, __shfl_xor_sync(0xffffffffu, bb.hz, o));
+    }
 
     for (int dz = -1; dz <= 1; ++dz) {
         int rz = cz + dz;
@@ -288,33 +392,8 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
                 }
                 b2 = (cx == 0 || cx == nc - 1) ? jb : row[cx + 1];
                 if (CI) six = 0.0f;
-                if (U == 3) {
-                    switch (lg) {
-                        case 0:
-                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 0>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
-                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
-                                                                           cnt, buf, lane);
-                            break;
-                        case 1:
-                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 1>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
-                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
-                                                                           cnt, buf, lane);
-                            break;
-                        case 2:
-                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 2>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
-                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
-                                                                           cnt, buf, lane);
-                            break;
-                        default:
-                            process_run<K, COUNT, POT, EPS0, UM, U, CI, 3>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2,
-                                                                           d0, iself, lg, grp, xi, yi, zi, ax, ay, az,
-                                                                           cnt, buf, lane);
-                            break;
-                    }
-                } else {
-                    process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0,
-                                                                iself, lg, grp, xi, yi, zi, ax, ay, az, cnt, buf, lane);
-                }
+                process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
+                                                            lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, buf, ids, lane);
             }
         }
     }
@@ -397,7 +476,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int lane,
 }
 
 template <bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI = false>
-__device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lane, float m_uniform) {
+__device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *ids, int lane, float m_uniform) {
     const int n_items = *P.n_items;
     while (true) {
         int it = 0;
@@ -406,11 +485,11 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lan
         if (it >= n_items) break;
         int4 item = P.items[it];
         switch (item.w & 15) {
-            case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
-            case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
-            case 3: process_item<3, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
-            case 4: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
-            default: process_item<5, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, lane, m_uniform); break;
+            case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
+            case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
+            case 3: process_item<3, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
+            case 4: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
+            default: process_item<5, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
         }
     }
 }
@@ -419,26 +498,28 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int lan
 // 5 -> 96 registers per thread); U: unroll policy.  The autotuner picks.
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
 __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
-    __shared__ float4 tiles[kWarps][32 * 8];
+    __shared__ float4 tiles[kWarps][kTileCap];
+    __shared__ int tile_ids[COUNT || POT ? kWarps : 1][kTileCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
+    int *ids = tile_ids[COUNT || POT ? w : 0];
     // equal masses (flag left 0 by the binning pass): apply the mass once per i
     if (!POT && P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
-        work_loop<COUNT, POT, EPS0, true, U>(P, buf, lane, P.pos[0].w);
+        work_loop<COUNT, POT, EPS0, true, U>(P, buf, ids, lane, P.pos[0].w);
     else
-        work_loop<COUNT, POT, EPS0, false, U>(P, buf, lane, 0.0f);
+        work_loop<COUNT, POT, EPS0, false, U>(P, buf, ids, lane, 0.0f);
 }
 
 // Positions as (cell, in-cell offset): the precision variant.
 template <bool EPS0>
 __global__ void __launch_bounds__(kThreads, 5) k_sr_force_ci(KParams P) {
-    __shared__ float4 tiles[kWarps][32 * 8];
+    __shared__ float4 tiles[kWarps][kTileCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
     if (P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
-        work_loop<false, false, EPS0, true, 0, true>(P, buf, lane, P.pos[0].w);
+        work_loop<false, false, EPS0, true, 0, true>(P, buf, nullptr, lane, P.pos[0].w);
     else
-        work_loop<false, false, EPS0, false, 0, true>(P, buf, lane, 0.0f);
+        work_loop<false, false, EPS0, false, 0, true>(P, buf, nullptr, lane, 0.0f);
 }
 
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
