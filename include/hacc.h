@@ -363,6 +363,8 @@ typedef struct {
     double force_ms;          /* summed CUDA-event durations of those launches (timing on) */
     uint64_t candidate_pairs; /* 27-cell candidate pairs of those launches (counting on) */
     uint64_t within_pairs;    /* ordered pairs (i, j != i) inside the cutoff (counting on) */
+    uint64_t evaluated_pairs; /* ordered pairs the pair kernel evaluated: the candidates left after
+                                 dropping j farther than r_cut from the item's bounds (counting on) */
     int64_t ml_rebins;        /* rebinnings inside multi-level steps after their first binning */
 } hacc_stats;
 

@@ -44,7 +44,8 @@ class _Split(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("force_launches", ctypes.c_int64),
                 ("force_ms", ctypes.c_double), ("candidate_pairs", ctypes.c_uint64),
-                ("within_pairs", ctypes.c_uint64), ("ml_rebins", ctypes.c_int64)]
+                ("within_pairs", ctypes.c_uint64), ("evaluated_pairs", ctypes.c_uint64),
+                ("ml_rebins", ctypes.c_int64)]
 
 
 class _BatchBox(ctypes.Structure):
@@ -331,7 +332,8 @@ class Context:
         st = _Stats()
         self._check(lib().hacc_stats_read(self._h, ctypes.byref(st), int(reset)), "hacc_stats_read")
         return dict(kernel_launches=st.kernel_launches, force_launches=st.force_launches, force_ms=st.force_ms,
-                    candidate_pairs=st.candidate_pairs, within_pairs=st.within_pairs, ml_rebins=st.ml_rebins)
+                    candidate_pairs=st.candidate_pairs, within_pairs=st.within_pairs, evaluated_pairs=st.evaluated_pairs,
+                    ml_rebins=st.ml_rebins)
 
     def scratch_bytes(self) -> int:
         return int(lib().hacc_ctx_scratch_bytes(self._h))

@@ -256,6 +256,7 @@ hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts
         HACC_CUDA(candidate_count(g, w->b.cell_start, ctx->d_pairs, s), "candidate count");
         fl.within = ctx->d_pairs + 1;
     }
+    if (ctx->counting && fl.within) fl.evaluated = ctx->d_pairs + 2;
     return launch_force(ctx, g, fc, fl, mode != kModePotential, s);
 }
 
@@ -302,8 +303,8 @@ hacc_status hacc_ctx_create(hacc_ctx **out, int device, size_t hbm_budget_bytes)
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_flags, 4 * sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->d_flags, 0, 4 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_pairs, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_pairs, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pairs, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return HACC_ENOMEM;
@@ -435,13 +436,14 @@ hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset) {
         ctx->ev_free.push_back(e);
     }
     ctx->ev_used.clear();
-    unsigned long long pairs[2] = {0, 0};
+    unsigned long long pairs[3] = {0, 0, 0};
     HACC_CUDA(cudaMemcpy(pairs, ctx->d_pairs, sizeof pairs, cudaMemcpyDeviceToHost), "reading pair counts");
     out->kernel_launches = ctx->launches;
     out->force_launches = ctx->force_launches;
     out->force_ms = ctx->force_ms;
     out->candidate_pairs = pairs[0];
     out->within_pairs = pairs[1];
+    out->evaluated_pairs = pairs[2];
     out->ml_rebins = ctx->ml_rebins;
     if (reset) {
         ctx->ml_rebins = 0;
@@ -800,6 +802,7 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         fl.h_drift = 0.f;
         fl.phi_out = nullptr;
         fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
+        fl.evaluated = ctx->counting ? ctx->d_pairs + 2 : nullptr;
         fl.mass_flag = w.b.mass_flag;
         fl.variant = ctx->variant;
         fl.ids = nullptr;

@@ -131,6 +131,7 @@ hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const
     fl.h_drift = 0.f;
     fl.phi_out = nullptr;
     fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
+    fl.evaluated = ctx->counting ? ctx->d_pairs + 2 : nullptr;
     fl.mass_flag = w.b.mass_flag;
     fl.variant = ctx->variant;
     fl.boxes = tab;

@@ -267,6 +267,7 @@ struct ForceLaunch {
     // kModePotential: phi_out[i] = G m_i/2 sum_j m_j phi(s_ij) (sorted order)
     float *phi_out;
     unsigned long long *within; // non-null: count pairs inside the cutoff
+    unsigned long long *evaluated = nullptr;   // with within: count the pairs evaluated (after culling)
     const int *mass_flag;       // from the binning pass (null: masses differ)
     // kModeBatch: geometry and kick/stream factors per box, write-back to the pool
     const BoxDev *boxes = nullptr;

@@ -58,6 +58,7 @@ struct KParams {
     float h_kick, h_drift;
     float *phi_out;
     unsigned long long *within;
+    unsigned long long *evaluated;
     const int *mass_flag;
     float w, w_lo, w_ratio;   // cell width w = w + w_lo (FP32 pair), w_ratio = w_lo / w
     const int32_t *levels;
@@ -191,7 +192,7 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
                                             float ty, float tz, int b1, int b2, int d0, int iself, int lg, int grp,
                                             const Bounds &bb, const float (&xi)[K], const float (&yi)[K],
                                             const float (&zi)[K], float (&ax)[K], float (&ay)[K], float (&az)[K],
-                                            unsigned &cnt, float4 *buf, int *ids, int lane) {
+                                            unsigned &cnt, unsigned &jsum, float4 *buf, int *ids, int lane) {
     const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
     const int G = 1 << lg;
@@ -227,6 +228,7 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
             __syncwarp();
             run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
             __syncwarp();
+            if (COUNT) jsum += nj;
         }
         return;
     }
@@ -275,6 +277,7 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
         __syncwarp();
         run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
         __syncwarp();
+        if (COUNT) jsum += nj;
         // carry the entries past the tile to the front
         const int rest = fill - nj;
         float4 cv = dummy;
@@ -326,7 +329,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
         xi[k] = p.x; yi[k] = p.y; zi[k] = p.z; mi[k] = p.w;
         ax[k] = 0.0f; ay[k] = 0.0f; az[k] = 0.0f;
     }
-    unsigned cnt = 0;
+    unsigned cnt = 0, jsum = 0;           // pairs inside the cutoff; j evaluated (counting form)
     const int iself = i0 + slot;          // sorted index of this lane's k = 0 particle
     // bounding box of the item's particles (for the j culling of the runs)
     Bounds bb{1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
@@ -393,7 +396,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
                 b2 = (cx == 0 || cx == nc - 1) ? jb : row[cx + 1];
                 if (CI) six = 0.0f;
                 process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
-                                                            lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, buf, ids, lane);
+                                                            lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane);
             }
         }
     }
@@ -472,6 +475,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c64 += __shfl_down_sync(0xffffffffu, c64, o);
         if (lane == 0) atomicAdd(P.within, c64);
+        if (lane == 0 && P.evaluated) atomicAdd(P.evaluated, (unsigned long long)jsum * (unsigned long long)ni);
     }
 }
 
@@ -577,6 +581,7 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.h_drift = fl.h_drift;
     P.phi_out = fl.phi_out;
     P.within = fl.within;
+    P.evaluated = fl.evaluated;
     P.mass_flag = fl.mass_flag;
     P.boxes = fl.boxes;
     P.ids = fl.ids;

@@ -256,3 +256,24 @@ def test_bin_crowded_cells_bit_exact(torch, hacc, ctx, split_params):
     _check_bin(torch, hacc, ctx, pos, 24.0, np.float32(split_params["r_cut"]))
     _, cell_o, _ = oracle.wrap_cell(pos, 24.0, hacc.mesh_cells(24.0, np.float32(split_params["r_cut"])))
     assert np.bincount(cell_o).max() > 4096
+
+
+def test_bounding_box_cull_counts(torch, hacc, ctx, split_params):
+    # the pair kernel evaluates the 27-cell candidates minus the j it drops
+    # as farther than r_cut from the item's bounds: never fewer than the
+    # pairs inside the cutoff, never more than the candidates, and on a
+    # uniform box a clear share of the candidates is dropped
+    L = 40.0
+    pos = synth.uniform(40000, L, seed=91)
+    p = _dev(torch, pos)
+    ctx.stats_read(reset=True)
+    ctx.stats_enable(counting=True)
+    ctx.sr_force(hacc.Box(L=L), split_params, p)
+    st = ctx.stats_read(reset=True)
+    ctx.stats_enable()
+    cand, within, ev = st["candidate_pairs"], st["within_pairs"], st["evaluated_pairs"]
+    nc = hacc.mesh_cells(L, split_params["r_cut"])
+    _, cell_o, _ = oracle.wrap_cell(pos, L, nc)
+    count_o, _, _ = oracle.bin_cells(cell_o, nc)
+    assert cand == oracle.candidates(count_o, nc)
+    assert within < ev < 0.9 * cand
