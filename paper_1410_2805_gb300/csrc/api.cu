@@ -303,8 +303,8 @@ hacc_status hacc_ctx_create(hacc_ctx **out, int device, size_t hbm_budget_bytes)
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_flags, 4 * sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->d_flags, 0, 4 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_pairs, 3 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(ctx->d_pairs, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_pairs, 5 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pairs, 0, 5 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return HACC_ENOMEM;
@@ -323,6 +323,9 @@ void hacc_ctx_destroy(hacc_ctx *ctx) {
     if (ctx->io_base) cudaFree(ctx->io_base);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+    if (ctx->ml_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->ml_exec));
+    if (ctx->cap_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->cap_stream));
+    if (ctx->cap_stream2) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->cap_stream2));
     for (auto &e : ctx->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (auto &e : ctx->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     if (tl_launches == &ctx->launches) tl_launches = nullptr;
@@ -436,15 +439,16 @@ hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset) {
         ctx->ev_free.push_back(e);
     }
     ctx->ev_used.clear();
-    unsigned long long pairs[3] = {0, 0, 0};
+    // candidates, inside the cutoff, evaluated; multi-level graph rebinnings and their kernel launches
+    unsigned long long pairs[5] = {0, 0, 0, 0, 0};
     HACC_CUDA(cudaMemcpy(pairs, ctx->d_pairs, sizeof pairs, cudaMemcpyDeviceToHost), "reading pair counts");
-    out->kernel_launches = ctx->launches;
+    out->kernel_launches = ctx->launches + (int64_t)pairs[4];
     out->force_launches = ctx->force_launches;
     out->force_ms = ctx->force_ms;
     out->candidate_pairs = pairs[0];
     out->within_pairs = pairs[1];
     out->evaluated_pairs = pairs[2];
-    out->ml_rebins = ctx->ml_rebins;
+    out->ml_rebins = ctx->ml_rebins + (int64_t)pairs[3];
     if (reset) {
         ctx->ml_rebins = 0;
         ctx->launches = 0;
@@ -701,6 +705,136 @@ std::vector<MlEvent> ml_schedule(const int *present, int lmax, double dt) {
     return out;
 }
 
+uint64_t mixk(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+uint32_t fbits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return u;
+}
+
+// Buffers of the multi-level event loop, fixed for one call.
+struct MlLoop {
+    int64_t n;
+    float4 *Ps, *Vs, *Vt, *Ref, *pos_in, *V;
+    int32_t *lev_s, *lev_t, *id_s, *id_t;
+    unsigned *disp_bits;
+    float half_lim;
+};
+
+ForceLaunch ml_force(hacc_ctx *ctx, Work &w, const MlLoop &m, const KickTable &kt) {
+    ForceLaunch fl;
+    fl.pos = m.Ps;
+    fl.items = w.b.items;
+    fl.n_items = w.b.n_items;
+    fl.cell_start = w.b.cell_start;
+    fl.work_counter = w.counter;
+    fl.mode = kModeKickLevels;
+    fl.out = nullptr;
+    fl.perm = nullptr;
+    fl.vel = m.Vs;   // kicked in place, sorted order
+    fl.pos_next = nullptr;
+    fl.h_kick = 0.f;
+    fl.h_drift = 0.f;
+    fl.phi_out = nullptr;
+    fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
+    fl.evaluated = ctx->counting ? ctx->d_pairs + 2 : nullptr;
+    fl.mass_flag = w.b.mass_flag;
+    fl.variant = ctx->variant;
+    fl.ids = nullptr;
+    fl.vel_pool = nullptr;
+    fl.levels = m.lev_s;
+    fl.kick = kt;
+    fl.flags = ctx->d_flags;
+    return fl;
+}
+
+// Capture the event loop (streams, drift checks, rebinnings as conditional
+// graph nodes, work items, pair-kernel launches, closing stream and scatter)
+// as one CUDA graph.  Recorded on the context's own capture streams; nothing
+// runs here.
+cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, Work &w, const MlLoop &m,
+                       const std::vector<MlEvent> &ev, const std::vector<int> &caps, double dt, cudaGraphExec_t *out,
+                       int64_t *launches, int64_t *forces) {
+    cudaError_t e;
+    if (!ctx->cap_stream) {
+        cudaStream_t a = nullptr, b = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking)) != cudaSuccess) {
+            cudaStreamDestroy(a);
+            return e;
+        }
+        ctx->cap_stream = a;
+        ctx->cap_stream2 = b;
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(ctx->cap_stream), cs2 = static_cast<cudaStream_t>(ctx->cap_stream2);
+    const int64_t l0 = ctx->launches, f0 = ctx->force_launches;
+    int64_t body = 0;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    double t_prev = 0.0;
+    for (size_t k = 0; k < ev.size() && e == cudaSuccess; ++k) {
+        if ((e = stream_sorted(m.n, m.Ps, m.Vs, (float)(ev[k].t - t_prev), m.Ref, m.disp_bits, cs)) != cudaSuccess) break;
+        t_prev = ev[k].t;
+        cudaStreamCaptureStatus st;
+        cudaGraph_t graph = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        if ((e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &nd)) != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+        if ((e = ml_decide(m.disp_bits, m.half_lim, h, ctx->d_pairs + 3, ctx->d_flags, cs)) != cudaSuccess) break;
+        if ((e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &nd)) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        if ((e = cudaGraphAddNode(&cn, graph, deps, nullptr, nd, &cp)) != cudaSuccess) break;
+        if ((e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            break;
+        // the rebinning body: bin the streamed positions, gather everything
+        // into the second buffers, move them back
+        cudaGraph_t bg = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(cs2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            break;
+        const int64_t b0 = ctx->launches;
+        cudaError_t eb = bin_build(g, m.n, m.Ps, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, cs2);
+        if (eb == cudaSuccess)
+            eb = gather_ml(m.n, w.b.perm, w.P, m.Ps, m.Ref, m.Vs, m.Vt, m.lev_s, m.lev_t, m.id_s, m.id_t, w.b.key,
+                           w.Ks, cs2);
+        body = ctx->launches - b0 + 1;
+        if (eb == cudaSuccess)
+            eb = ml_commit(m.n, m.Vt, m.Vs, m.lev_t, m.lev_s, m.id_t, m.id_s, m.disp_bits, (unsigned)body,
+                           ctx->d_pairs + 4, cs2);
+        e = cudaStreamEndCapture(cs2, &bg);
+        if (eb != cudaSuccess) e = eb;
+        if (e != cudaSuccess) break;
+        if ((e = items_active(g, m.n, w.Ks, m.lev_s, ev[k].kt, w.cell_active, w.b, caps[k], cs)) != cudaSuccess) break;
+        if ((e = sr_force_launch(g, fc, ml_force(ctx, w, m, ev[k].kt), ctx->num_sms, cs)) != cudaSuccess) break;
+        ctx->force_launches++;
+    }
+    if (e == cudaSuccess) e = stream_sorted(m.n, m.Ps, m.Vs, (float)(dt - t_prev), nullptr, nullptr, cs);
+    if (e == cudaSuccess) e = scatter_rows(m.n, m.id_s, m.Ps, m.pos_in, m.Vs, m.V, g.Lf, ctx->d_flags, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    // kernels of the rebinning bodies are counted on the device when they run
+    *launches = ctx->launches - l0 - (int64_t)ev.size() * body;
+    *forces = ctx->force_launches - f0;
+    ctx->launches = l0;
+    ctx->force_launches = f0;
+    cudaGetLastError();
+    return e;
+}
+
 }  // namespace
 
 hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
@@ -764,9 +898,72 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     HACC_CUDA(cudaMemcpyAsync(present, w.present, sizeof present, cudaMemcpyDeviceToHost, s), "levels present");
     HACC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     const std::vector<MlEvent> ev = ml_schedule(present, lmax, dt);
+    const float half_lim = (float)(half * (1.0 - 1e-5));
+    // particles kicked at each event; a small launch splits its cells into
+    // smaller items (down to one lane per particle) so that enough warps share it
+    std::vector<int> caps(ev.size());
+    for (size_t k = 0; k < ev.size(); ++k) {
+        int64_t kicked = 0;
+        for (int l = 1; l <= lmax; ++l)
+            if (ev[k].kt.h[l] != 0.0f) kicked += present[l];
+        const int64_t per_item = kicked / ((int64_t)ctx->num_sms * 64);
+        caps[k] = (int)std::max<int64_t>(kItemMin, std::min<int64_t>(kItemMax, per_item / 32 * 32));
+    }
 
+    // Without timing or counting the event loop runs as one cached CUDA graph
+    // whose rebinnings are conditional nodes set by the drift check on the
+    // device: no host round trip per event.
+    if (!ctx->timing && !ctx->counting && !ctx->ml_graph_off) {
+        const MlLoop m{n, Ps, Vs, Vt, Ref, pos_in, V, lev_s, lev_t, id_s, id_t, disp_bits, half_lim};
+        uint64_t key = 0x6d6c67ull;
+        key = mixk(key, (uint64_t)n);
+        key = mixk(key, (uint64_t)g.nc);
+        key = mixk(key, fbits(g.Lf));
+        key = mixk(key, fbits(half_lim));
+        for (size_t k = 0; k < ev.size(); ++k) {
+            uint64_t tb;
+            std::memcpy(&tb, &ev[k].t, 8);
+            key = mixk(key, tb);
+            for (int l = 0; l <= kMaxLevels; ++l) key = mixk(key, fbits(ev[k].kt.h[l]));
+            key = mixk(key, (uint64_t)caps[k]);
+        }
+        uint64_t db;
+        std::memcpy(&db, &dt, 8);
+        key = mixk(key, db);
+        uint32_t fcb[sizeof(ForceConsts) / 4];
+        std::memcpy(fcb, &fc, sizeof fcb);
+        for (uint32_t v : fcb) key = mixk(key, v);
+        for (const void *p : {(const void *)pos_in, (const void *)V, (const void *)ctx->scratch.base, (const void *)Ps,
+                              (const void *)Vs, (const void *)Vt, (const void *)lev_s, (const void *)id_s})
+            key = mixk(key, (uint64_t)(uintptr_t)p);
+        key = mixk(key, (uint64_t)ctx->variant);
+        if (!ctx->ml_exec || ctx->ml_key != key) {
+            if (ctx->ml_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->ml_exec));
+            ctx->ml_exec = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            int64_t gl = 0, gf = 0;
+            if (ml_capture(ctx, g, fc, w, m, ev, caps, dt, &exec, &gl, &gf) == cudaSuccess) {
+                ctx->ml_exec = exec;
+                ctx->ml_key = key;
+                ctx->ml_launches = gl;
+                ctx->ml_forces = gf;
+            } else {
+                if (exec) cudaGraphExecDestroy(exec);
+                ctx->ml_graph_off = true;   // run the loop from the host from now on
+            }
+        }
+        if (ctx->ml_exec) {
+            HACC_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(ctx->ml_exec), s), "cudaGraphLaunch");
+            ctx->launches += ctx->ml_launches;
+            ctx->force_launches += ctx->ml_forces;
+            return HACC_OK;
+        }
+    }
+
+    // the same loop from the host: one synchronisation per event reads the drift
     double t_prev = 0.0;
-    for (const MlEvent &e : ev) {
+    for (size_t k = 0; k < ev.size(); ++k) {
+        const MlEvent &e = ev[k];
         HACC_CUDA(stream_sorted(n, Ps, Vs, (float)(e.t - t_prev), Ref, disp_bits, s), "stream");
         t_prev = e.t;
         unsigned bits = 0;
@@ -775,42 +972,13 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         float drift;
         std::memcpy(&drift, &bits, sizeof drift);
         if (!std::isfinite(drift)) return set_error(ctx, HACC_EDOMAIN, "non-finite position in the multi-level step");
-        if ((double)drift > half * (1.0 - 1e-5)) {
+        if (drift > half_lim) {
             HACC_TRY(rebin(Ps, false));
             ctx->ml_rebins++;
         }
-        // particles kicked now; a small launch splits its cells into smaller
-        // items (down to one lane per particle) so that enough warps share it
-        int64_t kicked = 0;
-        for (int l = 1; l <= lmax; ++l)
-            if (e.kt.h[l] != 0.0f) kicked += present[l];
-        const int64_t per_item = kicked / ((int64_t)ctx->num_sms * 64);
-        const int cap = (int)std::max<int64_t>(kItemMin, std::min<int64_t>(kItemMax, per_item / 32 * 32));
-        HACC_CUDA(items_active(g, n, w.Ks, lev_s, e.kt, w.cell_active, w.b, cap, s), "work items");
-        ForceLaunch fl;
-        fl.pos = Ps;
-        fl.items = w.b.items;
-        fl.n_items = w.b.n_items;
-        fl.cell_start = w.b.cell_start;
-        fl.work_counter = w.counter;
-        fl.mode = kModeKickLevels;
-        fl.out = nullptr;
-        fl.perm = nullptr;
-        fl.vel = Vs;   // kicked in place, sorted order
-        fl.pos_next = nullptr;
-        fl.h_kick = 0.f;
-        fl.h_drift = 0.f;
-        fl.phi_out = nullptr;
-        fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
-        fl.evaluated = ctx->counting ? ctx->d_pairs + 2 : nullptr;
-        fl.mass_flag = w.b.mass_flag;
-        fl.variant = ctx->variant;
-        fl.ids = nullptr;
-        fl.vel_pool = nullptr;
-        fl.levels = lev_s;
-        fl.kick = e.kt;
-        fl.flags = ctx->d_flags;
-        HACC_TRY(launch_force(ctx, g, fc, fl, true, s));
+        HACC_CUDA(items_active(g, n, w.Ks, lev_s, e.kt, w.cell_active, w.b, caps[k], s), "work items");
+        const MlLoop m{n, Ps, Vs, Vt, Ref, pos_in, V, lev_s, lev_t, id_s, id_t, disp_bits, half_lim};
+        HACC_TRY(launch_force(ctx, g, fc, ml_force(ctx, w, m, e.kt), true, s));
     }
     // last stream, then wrapped positions and velocities back to input order
     HACC_CUDA(stream_sorted(n, Ps, Vs, (float)(dt - t_prev), nullptr, nullptr, s), "closing stream");

@@ -600,6 +600,35 @@ __global__ void __launch_bounds__(kBlock) k_stream(int64_t n, float4 *__restrict
     if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(disp, __float_as_uint(m));
 }
 
+__global__ void k_ml_decide(const unsigned *disp_bits, float half_lim, cudaGraphConditionalHandle handle,
+                            unsigned long long *rebins, int *flags) {
+    const float d = __uint_as_float(*disp_bits);
+    bool rebin = d > half_lim;
+    if (!isfinite(d)) {
+        atomicOr(flags, kFlagDomain);
+        rebin = false;
+    }
+    cudaGraphSetConditional(handle, rebin ? 1u : 0u);
+    if (rebin) *rebins += 1ull;
+}
+
+__global__ void __launch_bounds__(kBlock) k_ml_commit(int64_t n, const float4 *__restrict__ v_from,
+                                                       float4 *__restrict__ v_to, const int32_t *__restrict__ lev_from,
+                                                       int32_t *__restrict__ lev_to,
+                                                       const int32_t *__restrict__ id_from,
+                                                       int32_t *__restrict__ id_to, unsigned *disp_bits,
+                                                       unsigned body_launches, unsigned long long *launches) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        *disp_bits = 0u;
+        *launches += body_launches;
+    }
+    if (i >= n) return;
+    v_to[i] = v_from[i];
+    lev_to[i] = lev_from[i];
+    id_to[i] = id_from[i];
+}
+
 // Cells that hold a particle kicked at this event.
 __global__ void __launch_bounds__(kBlock) k_mark_active(int64_t n, const int32_t *__restrict__ key,
                                                          const int32_t *__restrict__ level, KickTable kt,
@@ -692,6 +721,22 @@ cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, 
                       int *present, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_levels<<<blocks_for(n), kBlock, 0, s>>>(n, g.ncell, b.key, b.count, d, lmax, level, present);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t ml_decide(const unsigned *disp_bits, float half_lim, cudaGraphConditionalHandle handle,
+                      unsigned long long *rebins, int *d_flags, cudaStream_t s) {
+    k_ml_decide<<<1, 1, 0, s>>>(disp_bits, half_lim, handle, rebins, d_flags);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t ml_commit(int64_t n, const float4 *v_from, float4 *v_to, const int32_t *lev_from, int32_t *lev_to,
+                      const int32_t *id_from, int32_t *id_to, unsigned *disp_bits, unsigned body_launches,
+                      unsigned long long *launches, cudaStream_t s) {
+    k_ml_commit<<<blocks_for(n > 0 ? n : 1), kBlock, 0, s>>>(n, v_from, v_to, lev_from, lev_to, id_from, id_to,
+                                                             disp_bits, body_launches, launches);
     note_launch();
     return cudaGetLastError();
 }

@@ -60,6 +60,13 @@ struct hacc_ctx {
     void *graph_exec = nullptr;
     uint64_t graph_key = 0;
     int64_t graph_launches = 0, graph_forces = 0;
+    // multi-level steps (api.cu): cached CUDA graph of the event loop, with a
+    // conditional rebinning node per event; captured on a stream of its own
+    void *ml_exec = nullptr;
+    uint64_t ml_key = 0;
+    int64_t ml_launches = 0, ml_forces = 0;
+    void *cap_stream = nullptr, *cap_stream2 = nullptr;
+    bool ml_graph_off = false;   // set when the device refused the graph once
 };
 
 namespace hacc {
@@ -213,6 +220,16 @@ cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift
 cudaError_t gather_ml(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, float4 *ref_out,
                       const float4 *v_in, float4 *v_out, const int32_t *lev_in, int32_t *lev_out, const int32_t *id_in,
                       int32_t *id_out, const int32_t *key, int32_t *key_out, cudaStream_t s);
+// Graph form of the drift check: set the conditional node `handle` to
+// whether the largest drift passed `half_lim` (and count the rebinning in
+// *rebins); a non-finite drift raises the domain flag instead.  ml_commit
+// (last node of the rebinning body) moves the gathered arrays back into
+// place, clears the drift word and adds the body's kernel count to *launches.
+cudaError_t ml_decide(const unsigned *disp_bits, float half_lim, cudaGraphConditionalHandle handle,
+                      unsigned long long *rebins, int *d_flags, cudaStream_t s);
+cudaError_t ml_commit(int64_t n, const float4 *v_from, float4 *v_to, const int32_t *lev_from, int32_t *lev_to,
+                      const int32_t *id_from, int32_t *id_to, unsigned *disp_bits, unsigned body_launches,
+                      unsigned long long *launches, cudaStream_t s);
 cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
                          const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, cudaStream_t s);
 

@@ -116,3 +116,28 @@ def test_multilevel_rejects_a_bad_skin(env, split_params):
         with pytest.raises(hacc.HaccError) as e:
             ctx.subcycle_ml(hacc.Box(L=16.0), split_params, p, v, 0.01, 1, 2, skin=bad)
         assert e.value.status == hacc.HACC_EINVAL
+
+
+@pytest.mark.parametrize("case", ["kept", "rebinned"])
+def test_multilevel_graph_equals_host_loop(env, split_params, case):
+    # without timing or counting the event loop runs as a CUDA graph whose
+    # rebinnings are conditional nodes; with counting on it runs from the host
+    # (one drift read per event): the same kernels in the same order
+    torch, hacc, ctx = env
+    L, n, sig, bsig, dt = {"kept": (22.0, 7000, 0.1, 1.5, 0.06), "rebinned": (20.0, 6000, 0.0, 0.7, 0.1)}[case]
+    pos = synth.blob_mixture(n, L, seed=84, n_blobs=8, sigma=bsig)
+    vel = synth.gaussian_velocities(n, seed=84, sigma=sig) if sig > 0 else np.zeros((n, 4), np.float32)
+    sp = dict(split_params, eps=float(np.float32(0.01)))
+    runs = []
+    for counting in (True, False, False):   # the second graph call replays the cached graph
+        p, v = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
+        ctx.stats_enable(counting=counting)
+        ctx.stats_read(reset=True)
+        ctx.subcycle_ml(hacc.Box(L=L), sp, p, v, dt, 1, 3)
+        st = ctx.stats_read(reset=True)
+        runs.append((p, v, st["ml_rebins"]))
+    ctx.stats_enable()
+    for p, v, rb in runs[1:]:
+        assert torch.equal(p, runs[0][0]) and torch.equal(v, runs[0][1])
+        assert rb == runs[0][2]
+    assert (runs[0][2] == 0) == (case == "kept")
