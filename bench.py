@@ -367,6 +367,38 @@ def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, worklo
     return out
 
 
+def run_fine_mesh(torch, hacc, ctx, split, pos, L, reps=3):
+    """One force evaluation of the bench box with cells >= r_cut (27-cell
+    search) and cells >= r_cut/2 (125-cell search): device time per call and
+    the pair counts of each."""
+    box = hacc.Box(L=L)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for R in (1, 2):
+        ctx.set_stencil(R)
+        try:
+            ctx.sr_force(box, split, pos)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.sr_force(box, split, pos)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.stats_read(reset=True)
+            ctx.stats_enable(counting=True)
+            ctx.sr_force(box, split, pos)
+            st = ctx.stats_read(reset=True)
+            ctx.stats_enable()
+        finally:
+            ctx.set_stencil(1)
+        out["cells_%d" % (27 if R == 1 else 125)] = {
+            "ms_per_force_call": e0.elapsed_time(e1) / reps, "candidate_pairs": st["candidate_pairs"],
+            "evaluated_pairs": st["evaluated_pairs"], "within_pairs": st["within_pairs"]}
+    out["speedup_125_over_27"] = out["cells_27"]["ms_per_force_call"] / out["cells_125"]["ms_per_force_call"]
+    return out
+
+
 def run_served(torch, hacc, ctx, split, rate, window, cap_s, seed=5, max_active=64 << 20, pool_gb=150.0):
     """Poisson arrivals (rate/s over `window` s) of runs with N in {32^3, 64^3,
     128^3, 256^3} (blob mixture, blobs of 256) and 5-50 SR sub-cycles of step
@@ -598,6 +630,7 @@ def run_ours(args):
         # blob box where the mesh is rebuilt at almost every event
         line["multilevel"] = run_multilevel(torch, hacc, ctx, split, workload="zel128", d=1, lmax=4, dt=0.02)
         line["multilevel_violent"] = run_multilevel(torch, hacc, ctx, split, workload="blob128", d=2, lmax=4, dt=0.04)
+        line["fine_mesh"] = run_fine_mesh(torch, hacc, ctx, split, pos, L)
     if not args.no_served:
         served = run_served(torch, hacc, ctx, split, rate=50.0, window=args.served_window, cap_s=args.served_cap)
         served["vs_plain_pairs_per_s"] = served["pair_interactions_per_s"] / (within / secs)

@@ -353,6 +353,18 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
                       const float *pos_m, int32_t reps, double *times_ms, int32_t *chosen,
                       hacc_stream_t stream);
 
+/* Finer chaining mesh for the single-box force paths (hacc_sr_force,
+ * hacc_subcycle, hacc_step, hacc_diagnostics, hacc_tune and their host forms):
+ * cells_per_rcut = 1 (default) bins into cells at least r_cut wide and searches
+ * the 27 cells around each particle's own (Sec. 3.3); 2 bins into cells at
+ * least r_cut/2 wide (box->nc = 0: hacc_mesh_cells(L, r_cut/2); nc >= 5) and
+ * searches the 125 cells within two cells, which covers the same sphere with a
+ * smaller search volume (a variant of the library; the paper's own P3M search
+ * is the 27-cell one).  The forces are those of the same pairs.  Batched,
+ * served, multi-level, cell/offset and allocation-free paths always use 27
+ * cells.  HACC_EINVAL for other values. */
+hacc_status hacc_set_stencil(hacc_ctx *ctx, int32_t cells_per_rcut);
+
 /* Select the pair-kernel variant by hand (0 <= variant < HACC_FORCE_VARIANTS). */
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant);
 

@@ -166,6 +166,7 @@ def lib():
             "hacc_tune": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, i32,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
             "hacc_set_variant": (st, [p, i32]),
+            "hacc_set_stencil": (st, [p, i32]),
             "hacc_batch_subcycle": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, i32, i32,
                                          p]),
             "hacc_batch_tick": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, p]),
@@ -324,6 +325,10 @@ class Context:
 
     def set_variant(self, variant: int):
         self._check(lib().hacc_set_variant(self._h, int(variant)), "hacc_set_variant")
+
+    def set_stencil(self, cells_per_rcut: int):
+        """1: cells >= r_cut, 27-cell search (default); 2: cells >= r_cut/2, 125-cell search."""
+        self._check(lib().hacc_set_stencil(self._h, int(cells_per_rcut)), "hacc_set_stencil")
 
     def stats_enable(self, timing: bool = False, counting: bool = False):
         self._check(lib().hacc_stats_enable(self._h, int(timing), int(counting)), "hacc_stats_enable")

@@ -88,6 +88,16 @@ hacc_status make_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geome
     return HACC_OK;
 }
 
+// Geometry of the single-box force paths: cells at least r_cut / R wide,
+// searched over the (2R+1)^3 cells around each (R = the context's stencil).
+hacc_status make_sr_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geometry *g) {
+    const int R = ctx->stencil;
+    HACC_STATUS_RETURN(make_geometry(ctx, box, R == 2 ? 0.5f * r_cut : r_cut, g));
+    if (g->nc < 2 * R + 1) return set_error(ctx, HACC_EDOMAIN, "a 125-cell stencil needs at least 5 cells per side");
+    g->R = R;
+    return HACC_OK;
+}
+
 static double binom(int n, int k) {
     double r = 1.0;
     for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
@@ -362,6 +372,13 @@ int32_t hacc_ml_mesh_cells(double L, float r_cut, float skin) {
     return (nc2 >= 3 && nc2 < nc) ? nc2 : nc;
 }
 
+hacc_status hacc_set_stencil(hacc_ctx *ctx, int32_t cells_per_rcut) {
+    HACC_TRY(enter(ctx));
+    if (cells_per_rcut != 1 && cells_per_rcut != 2) return set_error(ctx, HACC_EINVAL, "stencil must be 1 or 2");
+    ctx->stencil = cells_per_rcut;
+    return HACC_OK;
+}
+
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant) {
     HACC_TRY(enter(ctx));
     if (variant < 0 || variant >= kForceVariants) return set_error(ctx, HACC_EINVAL, "variant out of range");
@@ -375,7 +392,7 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     if (reps < 1) return set_error(ctx, HACC_EINVAL, "reps must be >= 1");
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    HACC_TRY(make_sr_geometry(ctx, box, split->r_cut, &g));
     ForceConsts fc;
     HACC_TRY(make_force_consts(ctx, split, g, &fc));
     HACC_TRY(check_particles(ctx, n, pos_m, nullptr));
@@ -489,7 +506,7 @@ hacc_status hacc_sr_force(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
     HACC_TRY(enter(ctx));
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    HACC_TRY(make_sr_geometry(ctx, box, split->r_cut, &g));
     ForceConsts fc;
     HACC_TRY(make_force_consts(ctx, split, g, &fc));
     HACC_TRY(check_particles(ctx, n, pos_m, acc));
@@ -520,7 +537,7 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
     if (n_sub < 1) return set_error(ctx, HACC_EINVAL, "n_sub must be >= 1");
     if (!std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    HACC_TRY(make_sr_geometry(ctx, box, split->r_cut, &g));
     ForceConsts fc;
     HACC_TRY(make_force_consts(ctx, split, g, &fc));
     HACC_TRY(check_particles(ctx, n, pos_m, vel));
@@ -991,7 +1008,7 @@ hacc_status hacc_diagnostics(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     HACC_TRY(enter(ctx));
     if (!split || !out) return set_error(ctx, HACC_EINVAL, "split or out is NULL");
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    HACC_TRY(make_sr_geometry(ctx, box, split->r_cut, &g));
     ForceConsts fc;
     HACC_TRY(make_force_consts(ctx, split, g, &fc));
     HACC_TRY(check_particles(ctx, n, pos_m, vel));

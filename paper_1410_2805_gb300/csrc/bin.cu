@@ -435,8 +435,9 @@ __global__ void __launch_bounds__(kBlock) k_scatter(int64_t n, const int32_t *__
     }
 }
 
-// Candidate pairs of the 27-cell chaining mesh: sum_c n_c * sum_{nbr} n_nbr.
-__global__ void __launch_bounds__(kBlock) k_candidates(int nc, const int32_t *__restrict__ cell_start,
+// Candidate pairs of the chaining mesh: sum_c n_c * sum_{nbr} n_nbr over the
+// (2R+1)^3 neighbour cells (R = 1: the 27 cells).
+__global__ void __launch_bounds__(kBlock) k_candidates(int nc, int R, const int32_t *__restrict__ cell_start,
                                                         unsigned long long *out) {
     int64_t ncell = (int64_t)nc * nc * nc;
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,9 +447,9 @@ __global__ void __launch_bounds__(kBlock) k_candidates(int nc, const int32_t *__
         if (ni) {
             int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
             unsigned long long nb = 0;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
+            for (int dz = -R; dz <= R; ++dz)
+                for (int dy = -R; dy <= R; ++dy)
+                    for (int dx = -R; dx <= R; ++dx) {
                         int jx = (cx + dx + nc) % nc, jy = (cy + dy + nc) % nc, jz = (cz + dz + nc) % nc;
                         int64_t j = ((int64_t)jz * nc + jy) * nc + jx;
                         nb += (unsigned long long)(cell_start[j + 1] - cell_start[j]);
@@ -855,7 +856,7 @@ cudaError_t scatter_rows(int64_t n, const int32_t *id, const float4 *p_in, float
 }
 
 cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsigned long long *out, cudaStream_t s) {
-    k_candidates<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.nc, cell_start, out);
+    k_candidates<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.nc, g.R, cell_start, out);
     note_launch();
     return cudaGetLastError();
 }

@@ -50,6 +50,7 @@ struct hacc_ctx {
     int64_t launches = 0, force_launches = 0;
     int64_t ml_rebins = 0;
     int variant = 0;                          // pair-kernel variant (hacc_tune)
+    int stencil = 1;                          // single-box force paths: 1 (27 cells) or 2 (125 cells of half width)
     double force_ms = 0.0;
     unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -116,6 +117,7 @@ struct Geometry {
     int nc;          // chaining-mesh cells per side
     int64_t ncell;   // nc^3
     float inv_w;     // fl(nc / L), first guess of the cell index
+    int R = 1;       // neighbour cells per side searched: 1 (27 cells >= r_cut), 2 (125 cells >= r_cut/2)
 };
 
 hacc_status make_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geometry *g);

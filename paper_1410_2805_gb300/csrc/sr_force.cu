@@ -46,6 +46,7 @@ struct KParams {
     const int32_t *__restrict__ cell_start;
     int *work_counter;
     int nc;
+    int R;            // neighbour cells per side of a cell's own (1: 27 cells, 2: 125 cells)
     float L;
     float T, eps, G;
     float q0, q1, q2, q3, q4, q5;
@@ -353,47 +354,51 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
         bb.hz = fmaxf(bb.hz, __shfl_xor_sync(0xffffffffu, bb.hz, o));
     }
 
-    for (int dz = -1; dz <= 1; ++dz) {
+    // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine)
+    const int R = P.boxes ? 1 : P.R;
+    for (int dz = -R; dz <= R; ++dz) {
         int rz = cz + dz;
         float sjz = 0.0f, siz = 0.0f;
         if (rz < 0) { rz += nc; sjz = -L; }
         else if (rz >= nc) { rz -= nc; siz = -L; }
         if (CI) { sjz = (float)dz * P.w; siz = 0.0f; }
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             int ry = cy + dy;
             float sjy = 0.0f, siy = 0.0f;
             if (ry < 0) { ry += nc; sjy = -L; }
             else if (ry >= nc) { ry -= nc; siy = -L; }
             if (CI) { sjy = (float)dy * P.w; siy = 0.0f; }
             const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
-            // cells (cx-1, cx, cx+1) of this row: one run, or two when it wraps in x
-            const int nruns = (cx == 0 || cx == nc - 1) ? 2 : 1;
+            // cells lo..hi of this row: one run, or two when it wraps in x
+            const int lo = cx - R, hi = cx + R;
+            const bool wraps = lo < 0 || hi >= nc;
+            const int nruns = wraps ? 2 : 1;
 #pragma unroll 1
             for (int r = 0; r < nruns; ++r) {
                 int ja, jb;
                 float sjx = 0.0f, six = 0.0f;
-                // with in-cell offsets: x cell step of the run's entries is
-                // d0 + (j >= b1) + (j >= b2)
+                // with in-cell offsets (R = 1 only): x cell step of the run's
+                // entries is d0 + (j >= b1) + (j >= b2)
                 int b1, b2, d0;
-                if (cx == 0) {
-                    ja = r ? row[nc - 1] : row[0];
-                    jb = r ? row[nc] : row[2];
+                if (lo < 0) {           // [0, hi], then [nc + lo, nc) with j shifted by -L
+                    ja = r ? row[nc + lo] : row[0];
+                    jb = r ? row[nc] : row[hi + 1];
                     sjx = r ? -L : 0.0f;
                     b1 = r ? jb : row[1];
                     d0 = r ? -1 : 0;
-                } else if (cx == nc - 1) {
-                    ja = r ? row[0] : row[nc - 2];
-                    jb = r ? row[1] : row[nc];
+                } else if (hi >= nc) {  // [lo, nc), then [0, hi - nc] with i shifted by -L
+                    ja = r ? row[0] : row[lo];
+                    jb = r ? row[hi - nc + 1] : row[nc];
                     six = r ? -L : 0.0f;
                     b1 = r ? jb : row[nc - 1];
                     d0 = r ? 1 : -1;
                 } else {
-                    ja = row[cx - 1];
-                    jb = row[cx + 2];
+                    ja = row[lo];
+                    jb = row[hi + 1];
                     b1 = row[cx];
                     d0 = -1;
                 }
-                b2 = (cx == 0 || cx == nc - 1) ? jb : row[cx + 1];
+                b2 = wraps ? jb : row[cx + 1];
                 if (CI) six = 0.0f;
                 process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
                                                             lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane);
@@ -564,6 +569,7 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.cell_start = fl.cell_start;
     P.work_counter = fl.work_counter;
     P.nc = g.nc;
+    P.R = g.R;
     P.L = g.Lf;
     P.T = fc.T;
     P.eps = fc.eps;

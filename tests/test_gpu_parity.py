@@ -277,3 +277,70 @@ def test_bounding_box_cull_counts(torch, hacc, ctx, split_params):
     count_o, _, _ = oracle.bin_cells(cell_o, nc)
     assert cand == oracle.candidates(count_o, nc)
     assert within < ev < 0.9 * cand
+
+
+def _candidates_numpy(pos, L, nc, R):
+    # sum over cells of n_c times the particles of the (2R+1)^3 cells around it
+    _, cell_o, _ = oracle.wrap_cell(pos, L, nc)
+    cnt = np.bincount(cell_o, minlength=nc ** 3).reshape(nc, nc, nc).astype(np.int64)
+    nb = np.zeros_like(cnt)
+    for a in range(-R, R + 1):
+        for b in range(-R, R + 1):
+            for c in range(-R, R + 1):
+                nb += np.roll(np.roll(np.roll(cnt, a, 0), b, 1), c, 2)
+    return int((cnt * nb).sum())
+
+
+@pytest.mark.parametrize("case", ["blob", "zeldovich"])
+def test_fine_mesh_stencil_against_oracle(torch, hacc, ctx, split_params, case):
+    # cells >= r_cut/2 searched over 125 cells: the same pairs as the 27-cell
+    # search (the same image shifts, so the same FP32 separations)
+    if case == "blob":
+        L, pos = 24.0, synth.blob_mixture(6000, 24.0, seed=93, n_blobs=4, sigma=0.6)
+    else:
+        L, pos = 32.0, synth.zeldovich(32, seed=94, L=32.0)
+    sp = split_params
+    a_ref, _ = oracle.force_mesh(pos, L, sp)
+    p = _dev(torch, pos)
+    box = hacc.Box(L=L)
+    cand1, within1 = ctx.pair_counts(box, sp, p)
+    a1 = ctx.sr_force(box, sp, p).cpu().numpy()
+    ctx.set_stencil(2)
+    try:
+        cand2, within2 = ctx.pair_counts(box, sp, p)
+        a2 = ctx.sr_force(box, sp, p).cpu().numpy()
+    finally:
+        ctx.set_stencil(1)
+    assert _force_err(a2, a_ref) <= FORCE_TOL
+    assert within2 == within1
+    nc2 = hacc.mesh_cells(L, np.float32(sp["r_cut"]) / 2)
+    assert cand2 == _candidates_numpy(pos, L, nc2, 2)
+    assert cand1 == _candidates_numpy(pos, L, hacc.mesh_cells(L, sp["r_cut"]), 1)
+    assert cand2 < 0.75 * cand1
+    # the two are FP32 sums of the same pairs in different orders
+    assert _force_err(a2, a1[:, :3].astype(np.float64)) <= FORCE_TOL
+
+
+def test_fine_mesh_subcycle_and_limits(torch, hacc, ctx, split_params):
+    L = 24.0
+    pos = synth.blob_mixture(8000, L, seed=95)
+    vel = synth.gaussian_velocities(8000, seed=95)
+    sp = dict(split_params, eps=float(np.float32(0.01)))
+    p1, v1 = _dev(torch, pos), _dev(torch, vel)
+    p2, v2 = p1.clone(), v1.clone()
+    ctx.subcycle(hacc.Box(L=L), sp, p1, v1, 0.05, 3)
+    ctx.set_stencil(2)
+    try:
+        ctx.subcycle(hacc.Box(L=L), sp, p2, v2, 0.05, 3)
+        # fewer than 5 cells of width r_cut/2 per side
+        with pytest.raises(hacc.HaccError) as e:
+            ctx.sr_force(hacc.Box(L=7.0), sp, _dev(torch, synth.uniform(100, 7.0, seed=1)))
+        assert e.value.status == hacc.HACC_EDOMAIN
+    finally:
+        ctx.set_stencil(1)
+    d = (p1 - p2).cpu().numpy()[:, :3]
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < 1e-5 * L
+    with pytest.raises(hacc.HaccError) as e:
+        ctx.set_stencil(3)
+    assert e.value.status == hacc.HACC_EINVAL
