@@ -183,7 +183,8 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
 // item's bounding box, a j is outside the cutoff of every i and would add
 // exactly nothing, so dropping it leaves every pair sum unchanged; the kept j
 // are compacted in order (ballot + prefix count) into full tiles.  With
-// in-cell offsets (CI) every j is staged.  U selects the inner-loop form (the
+// in-cell offsets (CI) the test runs in the frame of i's cell, where both the
+// bounds and the staged j live.  U selects the inner-loop form (the
 // autotuner picks): 0 deep-unrolled and 1 light-unrolled indexed loops, 2
 // pointer-stepped loop; every form visits the same entries in the same order.
 // (The lane-group count as a compile-time constant, four times the code,
@@ -207,32 +208,6 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
     const PairConsts C{P.eps, P.T, P.q0, P.q1, P.q2, P.q3, P.q4, P.q5};
     const float4 dummy = make_float4(1e18f, 1e18f, 1e18f, 0.0f);   // far away, zero mass
     const int tile = 32 << lg;
-    if (CI) {
-        for (int j0 = ja; j0 < jb; j0 += tile) {
-            const int nj = min(tile, jb - j0);
-            for (int e = lane; e < tile; e += 32) {
-                float4 v = dummy;
-                if (e < nj) {
-                    // in-cell offsets: move j into the frame of i's cell (cell steps
-                    // of w = w_hi + w_lo, applied in two adds; the x step depends on
-                    // which of the run's cells j sits in)
-                    v = P.pos[j0 + e];
-                    const int j = j0 + e;
-                    const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
-                    v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
-                    v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
-                    v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
-                }
-                buf[e] = v;
-                if (COUNT || POT) ids[e] = j0 + e;
-            }
-            __syncwarp();
-            run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
-            __syncwarp();
-            if (COUNT) jsum += nj;
-        }
-        return;
-    }
     // the item's bounds in this run's frame (monotone rounding keeps them bounds)
     const float lx = ishift ? __fadd_rn(bb.lx, tx) : bb.lx, hx = ishift ? __fadd_rn(bb.hx, tx) : bb.hx;
     const float ly = ishift ? __fadd_rn(bb.ly, ty) : bb.ly, hy = ishift ? __fadd_rn(bb.hy, ty) : bb.hy;
@@ -251,7 +226,15 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
             float4 v = dummy;
             if (j < jb) {
                 v = P.pos[j];
-                if (jshift) {
+                if (CI) {
+                    // in-cell offsets: move j into the frame of i's cell (cell steps
+                    // of w = w_hi + w_lo, applied in two adds; the x step depends on
+                    // which of the run's cells j sits in)
+                    const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
+                    v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
+                    v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
+                    v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
+                } else if (jshift) {
                     v.x = __fadd_rn(v.x, sx);
                     v.y = __fadd_rn(v.y, sy);
                     v.z = __fadd_rn(v.z, sz);
