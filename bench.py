@@ -399,6 +399,34 @@ def run_fine_mesh(torch, hacc, ctx, split, pos, L, reps=3):
     return out
 
 
+def run_binning(torch, hacc, ctx, split, pos, L, reps=5):
+    """hacc_bin on the bench box (wrap, exact cell key, count, scan, stable
+    order): device time per call and HBM throughput on the algorithmic bytes
+    (read the positions, write them wrapped, write cell ids, the permutation
+    and the cell starts)."""
+    box = hacc.Box(L=L)
+    work = pos.clone()
+    r_cut = split.r_cut
+    ctx.bin(box, r_cut, work)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.bin(box, r_cut, work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    n = int(pos.shape[0])
+    nc = hacc.mesh_cells(L, r_cut)
+    alg = n * (16 + 16 + 4 + 4) + (nc ** 3 + 1) * 4
+    gbs = alg / (ms / 1e3) / 1e9
+    peak = measured_peaks().get("hbm_gbs")
+    return {"ms_per_call": ms, "algorithmic_bytes": alg, "bytes_per_particle": 40, "achieved_gbs": gbs,
+            "peak_gbs": peak, "frac": (gbs / peak) if peak else None, "bound": "hbm",
+            "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+
 def run_served(torch, hacc, ctx, split, rate, window, cap_s, seed=5, max_active=64 << 20, pool_gb=150.0):
     """Poisson arrivals (rate/s over `window` s) of runs with N in {32^3, 64^3,
     128^3, 256^3} (blob mixture, blobs of 256) and 5-50 SR sub-cycles of step
@@ -610,6 +638,7 @@ def run_ours(args):
                 "evaluated_frac": (evaluated_tflops / peak) if evaluated_tflops else None,
                 "force_ms_per_launch": st["force_ms"] / max(1, st["force_launches"]),
                 "force_launches": st["force_launches"], "force_share_of_step": st["force_ms"] / ms if ms else None}
+    binning = run_binning(torch, hacc, ctx, split, snap_p, L)
     line = {"metric": METRIC, "value": value, "unit": "pair interactions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -625,7 +654,7 @@ def run_ours(args):
             "evaluated_pairs_per_step": evaluated / args.steps,
             "replay_bitwise_equal": replay_ok,
             "gpu_launches": st["kernel_launches"],
-            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "binning_roofline": binning, "e2e": e2e, "clocks": clk,
             "autotune": {"variant": tuning["chosen"], "force_ms_by_variant": tuning["times_ms"],
                          "variants": "(blocks/SM, inner loop) = (5,indexed), (4,indexed), (5,pointer-stepped), (4,pointer-stepped)"}}
     if not args.no_batch:
