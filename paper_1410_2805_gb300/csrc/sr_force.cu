@@ -182,7 +182,8 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
 // item: farther than r_cut (with a margin far above rounding) from the
 // item's bounding box, a j is outside the cutoff of every i and would add
 // exactly nothing, so dropping it leaves every pair sum unchanged; the kept j
-// are compacted in order (ballot + prefix count) into full tiles.  With
+// are compacted in order (ballot + prefix count) into full tiles, which carry
+// over from one run to the next (fill, warp-uniform) until `last`.  With
 // in-cell offsets (CI) the test runs in the frame of i's cell, where both the
 // bounds and the staged j live.  U selects the inner-loop form (the
 // autotuner picks): 0 deep-unrolled and 1 light-unrolled indexed loops, 2
@@ -194,7 +195,8 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
                                             float ty, float tz, int b1, int b2, int d0, int iself, int lg, int grp,
                                             const Bounds &bb, const float (&xi)[K], const float (&yi)[K],
                                             const float (&zi)[K], float (&ax)[K], float (&ay)[K], float (&az)[K],
-                                            unsigned &cnt, unsigned &jsum, float4 *buf, int *ids, int lane) {
+                                            unsigned &cnt, unsigned &jsum, float4 *buf, int *ids, int lane,
+                                            int &fill, bool last) {
     const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
     const int G = 1 << lg;
@@ -214,7 +216,6 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
     const float lz = ishift ? __fadd_rn(bb.lz, tz) : bb.lz, hz = ishift ? __fadd_rn(bb.hz, tz) : bb.hz;
     const float keep_r2 = P.T * 1.001f + 1e-3f;
     const unsigned below = (1u << lane) - 1u;
-    int fill = 0;   // staged entries, warp-uniform
     int j0 = ja;
 #pragma unroll 1
     while (true) {
@@ -253,6 +254,8 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
             fill += __popc(m);
             j0 += 32;
         }
+        // a partial tile waits for the next run unless this is the last one
+        if (fill < tile && !last) break;
         const int nj = min(fill, tile);
         if (nj == 0) break;
         // a short last tile is padded to whole lane groups with far, massless entries
@@ -339,6 +342,10 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
 
     // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine)
     const int R = P.boxes ? 1 : P.R;
+    // Staged tiles run on across the runs unless a run shifts the i side
+    // (cells within R of the high faces): then every run ends its own tile.
+    const bool carry = CI || (cx + R < nc && cy + R < nc && cz + R < nc);
+    int fill = 0;
     for (int dz = -R; dz <= R; ++dz) {
         int rz = cz + dz;
         float sjz = 0.0f, siz = 0.0f;
@@ -383,8 +390,10 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
                 }
                 b2 = wraps ? jb : row[cx + 1];
                 if (CI) six = 0.0f;
+                const bool last = !carry || (dz == R && dy == R && r == nruns - 1);
                 process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
-                                                            lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane);
+                                                            lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane,
+                                                            fill, last);
             }
         }
     }
