@@ -174,30 +174,44 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
     }
 }
 
-// Stream one run [ja, jb) of consecutive sorted particles through the warp's
-// shared tile.  (sx, sy, sz): image shift added to the staged j coordinates;
-// (tx, ty, tz): image shift added to this lane's i coordinates.  The warp is
-// split into G = 2^lg lane groups that share the i-particles and split the j.
-// Staging keeps only the j that can be within the cutoff of some i of the
-// item: farther than r_cut (with a margin far above rounding) from the
-// item's bounding box, a j is outside the cutoff of every i and would add
-// exactly nothing, so dropping it leaves every pair sum unchanged; the kept j
-// are compacted in order (ballot + prefix count) into full tiles, which carry
-// over from one run to the next (fill, warp-uniform) until `last`.  With
-// in-cell offsets (CI) the test runs in the frame of i's cell, where both the
-// bounds and the staged j live.  U selects the inner-loop form (the
-// autotuner picks): 0 deep-unrolled and 1 light-unrolled indexed loops, 2
-// pointer-stepped loop; every form visits the same entries in the same order.
-// (The lane-group count as a compile-time constant, four times the code,
-// measured 2x slower from instruction-cache misses.)
+// The neighbour cells of an item as x-runs of consecutive sorted particles:
+// row (dz, dy) of the (2R+1)^2 rows gives run 2*row (cells cx-R..cx+R, or the
+// part of them in [0, nc) when the row wraps in x) and run 2*row+1 (the
+// wrapped part, else empty).  One table per warp in shared memory:
+//   A = (exclusive end of the run in the item's concatenated stream,
+//        offset j - t of its entries, shift bits, unused)
+//   shift bits: 1/2/4 add -L to the staged j's x/y/z, 8/16/32 add -L to
+//   the i side (runs of cells within R of a high face); with in-cell
+//   offsets (CI) bits 0-3 and 4-7 hold dy + 2 and dz + 2 instead, and
+//   B = (b1, b2, d0): the x cell step of entry j is d0 + (j >= b1) + (j >= b2).
+constexpr int kMaxRuns = 64;   // 2 (2R+1)^2 <= 50 for R <= 2
+
+struct RunTable {
+    int4 *A;
+    int4 *B;
+};
+
+// Stream the runs [r0, r1) of the table (all with the same i shift tx, ty,
+// tz) through the warp's shared tile.  The warp is split into G = 2^lg lane
+// groups that share the i-particles and split the j.  Staging keeps only the
+// j that can be within the cutoff of some i of the item: farther than r_cut
+// (with a margin far above rounding) from the item's bounding box, a j is
+// outside the cutoff of every i and would add exactly nothing, so dropping it
+// leaves every pair sum unchanged; the kept j are compacted in stream order
+// (ballot + prefix count) into full tiles, which carry over to the next call
+// (fill, warp-uniform) until `last`.  With in-cell offsets (CI) the test runs
+// in the frame of i's cell, where both the bounds and the staged j live.
+// U selects the inner-loop form (the autotuner picks): 0 deep-unrolled and 1
+// light-unrolled indexed loops, 2 pointer-stepped loop; every form visits the
+// same entries in the same order.  (The lane-group count as a compile-time
+// constant, four times the code, measured 2x slower from instruction-cache
+// misses.)
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
-__device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, float sx, float sy, float sz, float tx,
-                                            float ty, float tz, int b1, int b2, int d0, int iself, int lg, int grp,
-                                            const Bounds &bb, const float (&xi)[K], const float (&yi)[K],
-                                            const float (&zi)[K], float (&ax)[K], float (&ay)[K], float (&az)[K],
-                                            unsigned &cnt, unsigned &jsum, float4 *buf, int *ids, int lane,
-                                            int &fill, bool last) {
-    const bool jshift = (sx != 0.0f) || (sy != 0.0f) || (sz != 0.0f);
+__device__ __forceinline__ void process_runs(const KParams &P, const RunTable &rt, int r0, int r1, float L, float tx,
+                                             float ty, float tz, int iself, int lg, int grp, const Bounds &bb,
+                                             const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
+                                             float (&ax)[K], float (&ay)[K], float (&az)[K], unsigned &cnt,
+                                             unsigned &jsum, float4 *buf, int *ids, int lane, int &fill, bool last) {
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
     const int G = 1 << lg;
     float xs[K], ys[K], zs[K];
@@ -210,35 +224,43 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
     const PairConsts C{P.eps, P.T, P.q0, P.q1, P.q2, P.q3, P.q4, P.q5};
     const float4 dummy = make_float4(1e18f, 1e18f, 1e18f, 0.0f);   // far away, zero mass
     const int tile = 32 << lg;
-    // the item's bounds in this run's frame (monotone rounding keeps them bounds)
+    // the item's bounds in this frame (monotone rounding keeps them bounds)
     const float lx = ishift ? __fadd_rn(bb.lx, tx) : bb.lx, hx = ishift ? __fadd_rn(bb.hx, tx) : bb.hx;
     const float ly = ishift ? __fadd_rn(bb.ly, ty) : bb.ly, hy = ishift ? __fadd_rn(bb.hy, ty) : bb.hy;
     const float lz = ishift ? __fadd_rn(bb.lz, tz) : bb.lz, hz = ishift ? __fadd_rn(bb.hz, tz) : bb.hz;
     const float keep_r2 = P.T * 1.001f + 1e-3f;
     const unsigned below = (1u << lane) - 1u;
-    int j0 = ja;
+    const int t_end = rt.A[r1 - 1].x;
+    int t0 = r0 > 0 ? rt.A[r0 - 1].x : 0;
+    int cur = r0;   // this lane's run
 #pragma unroll 1
     while (true) {
-        // stage 32 candidates at a time until a tile is full or the run ends
+        // stage 32 candidates at a time until a tile is full or the runs end
 #pragma unroll 1
-        while (fill < tile && j0 < jb) {
-            const int j = j0 + lane;
+        while (fill < tile && t0 < t_end) {
+            const int t = t0 + lane;
             bool keep = false;
             float4 v = dummy;
-            if (j < jb) {
+            int j = -1;
+            if (t < t_end) {
+                while (t >= rt.A[cur].x) ++cur;
+                const int4 a = rt.A[cur];
+                j = t + a.y;
                 v = P.pos[j];
                 if (CI) {
                     // in-cell offsets: move j into the frame of i's cell (cell steps
                     // of w = w_hi + w_lo, applied in two adds; the x step depends on
                     // which of the run's cells j sits in)
-                    const float dlt = (float)(d0 + (j >= b1) + (j >= b2));
+                    const int4 b = rt.B[cur];
+                    const float dlt = (float)(b.z + (j >= b.x) + (j >= b.y));
+                    const float sy = (float)((a.z & 15) - 2) * P.w, sz = (float)(((a.z >> 4) & 15) - 2) * P.w;
                     v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
                     v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
                     v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
-                } else if (jshift) {
-                    v.x = __fadd_rn(v.x, sx);
-                    v.y = __fadd_rn(v.y, sy);
-                    v.z = __fadd_rn(v.z, sz);
+                } else if (a.z & 7) {
+                    if (a.z & 1) v.x = __fadd_rn(v.x, -L);
+                    if (a.z & 2) v.y = __fadd_rn(v.y, -L);
+                    if (a.z & 4) v.z = __fadd_rn(v.z, -L);
                 }
                 const float ex = fmaxf(fmaxf(lx - v.x, v.x - hx), 0.0f);
                 const float ey = fmaxf(fmaxf(ly - v.y, v.y - hy), 0.0f);
@@ -252,9 +274,9 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
                 if (COUNT || POT) ids[at] = j;
             }
             fill += __popc(m);
-            j0 += 32;
+            t0 += 32;
         }
-        // a partial tile waits for the next run unless this is the last one
+        // a partial tile waits for the next call unless this is the last one
         if (fill < tile && !last) break;
         const int nj = min(fill, tile);
         if (nj == 0) break;
@@ -279,13 +301,14 @@ __device__ __forceinline__ void process_run(const KParams &P, int ja, int jb, fl
             if (COUNT || POT) ids[lane] = ci;
         }
         fill = rest;
-        if (j0 >= jb && fill == 0) break;
+        if (t0 >= t_end && fill == 0) break;
     }
     __syncwarp();
 }
 
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
-__device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids, int lane, float m_uniform) {
+__device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids, const RunTable &rt, int lane,
+                             float m_uniform) {
     // geometry: the single box of the call, or this item's box of a batch
     int nc = P.nc;
     float L = P.L;
@@ -340,61 +363,78 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
         bb.hz = fmaxf(bb.hz, __shfl_xor_sync(0xffffffffu, bb.hz, o));
     }
 
-    // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine)
+    // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine),
+    // described by the lanes in the warp's run table
     const int R = P.boxes ? 1 : P.R;
-    // Staged tiles run on across the runs unless a run shifts the i side
-    // (cells within R of the high faces): then every run ends its own tile.
-    const bool carry = CI || (cx + R < nc && cy + R < nc && cz + R < nc);
-    int fill = 0;
-    for (int dz = -R; dz <= R; ++dz) {
-        int rz = cz + dz;
-        float sjz = 0.0f, siz = 0.0f;
-        if (rz < 0) { rz += nc; sjz = -L; }
-        else if (rz >= nc) { rz -= nc; siz = -L; }
-        if (CI) { sjz = (float)dz * P.w; siz = 0.0f; }
-        for (int dy = -R; dy <= R; ++dy) {
-            int ry = cy + dy;
-            float sjy = 0.0f, siy = 0.0f;
-            if (ry < 0) { ry += nc; sjy = -L; }
-            else if (ry >= nc) { ry -= nc; siy = -L; }
-            if (CI) { sjy = (float)dy * P.w; siy = 0.0f; }
+    const int span = 2 * R + 1;
+    const int nrun = 2 * span * span;
+    int run_end = 0;   // running total of the run lengths written so far
+    for (int q0 = 0; q0 < nrun; q0 += 32) {
+        const int q = q0 + lane;
+        int ja = 0, jb = 0, bits = 0, b1 = 0, b2 = 0, d0 = 0;
+        if (q < nrun) {
+            const int rowi = q >> 1, r = q & 1;
+            const int dz = rowi / span - R, dy = rowi % span - R;
+            int rz = cz + dz, ry = cy + dy;
+            if (rz < 0) { rz += nc; bits |= 4; }
+            else if (rz >= nc) { rz -= nc; bits |= 32; }
+            if (ry < 0) { ry += nc; bits |= 2; }
+            else if (ry >= nc) { ry -= nc; bits |= 16; }
+            if (CI) bits = (dy + 2) | ((dz + 2) << 4);
             const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
             // cells lo..hi of this row: one run, or two when it wraps in x
             const int lo = cx - R, hi = cx + R;
             const bool wraps = lo < 0 || hi >= nc;
-            const int nruns = wraps ? 2 : 1;
-#pragma unroll 1
-            for (int r = 0; r < nruns; ++r) {
-                int ja, jb;
-                float sjx = 0.0f, six = 0.0f;
-                // with in-cell offsets (R = 1 only): x cell step of the run's
-                // entries is d0 + (j >= b1) + (j >= b2)
-                int b1, b2, d0;
-                if (lo < 0) {           // [0, hi], then [nc + lo, nc) with j shifted by -L
-                    ja = r ? row[nc + lo] : row[0];
-                    jb = r ? row[nc] : row[hi + 1];
-                    sjx = r ? -L : 0.0f;
-                    b1 = r ? jb : row[1];
-                    d0 = r ? -1 : 0;
-                } else if (hi >= nc) {  // [lo, nc), then [0, hi - nc] with i shifted by -L
-                    ja = r ? row[0] : row[lo];
-                    jb = r ? row[hi - nc + 1] : row[nc];
-                    six = r ? -L : 0.0f;
-                    b1 = r ? jb : row[nc - 1];
-                    d0 = r ? 1 : -1;
-                } else {
-                    ja = row[lo];
-                    jb = row[hi + 1];
-                    b1 = row[cx];
-                    d0 = -1;
-                }
-                b2 = wraps ? jb : row[cx + 1];
-                if (CI) six = 0.0f;
-                const bool last = !carry || (dz == R && dy == R && r == nruns - 1);
-                process_run<K, COUNT, POT, EPS0, UM, U, CI>(P, ja, jb, sjx, sjy, sjz, six, siy, siz, b1, b2, d0, iself,
-                                                            lg, grp, bb, xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane,
-                                                            fill, last);
+            if (lo < 0) {           // [0, hi], then [nc + lo, nc) with j shifted by -L
+                ja = r ? row[nc + lo] : row[0];
+                jb = r ? row[nc] : row[hi + 1];
+                if (r && !CI) bits |= 1;
+                b1 = r ? jb : row[1];
+                d0 = r ? -1 : 0;
+            } else if (hi >= nc) {  // [lo, nc), then [0, hi - nc] with i shifted by -L
+                ja = r ? row[0] : row[lo];
+                jb = r ? row[hi - nc + 1] : row[nc];
+                if (r && !CI) bits |= 8;
+                b1 = r ? jb : row[nc - 1];
+                d0 = r ? 1 : -1;
+            } else if (r == 0) {
+                ja = row[lo];
+                jb = row[hi + 1];
+                b1 = row[cx];
+                d0 = -1;
             }
+            b2 = wraps ? jb : (r == 0 ? row[cx + 1] : 0);
+        }
+        // exclusive ends of the runs in the concatenated stream
+        int e = jb - ja;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, e, o);
+            if (lane >= o) e += y;
+        }
+        e += run_end;
+        if (q < nrun) {
+            rt.A[q] = make_int4(e, ja - (e - (jb - ja)), bits, 0);
+            if (CI) rt.B[q] = make_int4(b1, b2, d0, 0);
+        }
+        run_end = __shfl_sync(0xffffffffu, e, 31);
+    }
+    __syncwarp();
+    // Tiles run on across all runs unless a run shifts the i side (cells
+    // within R of the high faces): then every run ends its own tile.
+    const bool carry = CI || (cx + R < nc && cy + R < nc && cz + R < nc);
+    int fill = 0;
+    if (carry) {
+        process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, 0, nrun, L, 0.0f, 0.0f, 0.0f, iself, lg, grp, bb, xi, yi,
+                                                     zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
+    } else {
+#pragma unroll 1
+        for (int q = 0; q < nrun; ++q) {
+            const int4 a = rt.A[q];
+            const int start = q > 0 ? rt.A[q - 1].x : 0;
+            if (a.x == start) continue;   // empty run
+            const float tx = (a.z & 8) ? -L : 0.0f, ty = (a.z & 16) ? -L : 0.0f, tz = (a.z & 32) ? -L : 0.0f;
+            process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, q, q + 1, L, tx, ty, tz, iself, lg, grp, bb, xi, yi,
+                                                         zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
         }
     }
 
@@ -477,7 +517,8 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
 }
 
 template <bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI = false>
-__device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *ids, int lane, float m_uniform) {
+__device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *ids, const RunTable &rt, int lane,
+                                          float m_uniform) {
     const int n_items = *P.n_items;
     while (true) {
         int it = 0;
@@ -486,11 +527,11 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *id
         if (it >= n_items) break;
         int4 item = P.items[it];
         switch (item.w & 15) {
-            case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
-            case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
-            case 3: process_item<3, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
-            case 4: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
-            default: process_item<5, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, lane, m_uniform); break;
+            case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
+            case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
+            case 3: process_item<3, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
+            case 4: process_item<4, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
+            default: process_item<5, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
         }
     }
 }
@@ -501,26 +542,31 @@ template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
 __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
     __shared__ float4 tiles[kWarps][kTileCap];
     __shared__ int tile_ids[COUNT || POT ? kWarps : 1][kTileCap];
+    __shared__ int4 runs[kWarps][kMaxRuns];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
     int *ids = tile_ids[COUNT || POT ? w : 0];
+    const RunTable rt{runs[w], nullptr};
     // equal masses (flag left 0 by the binning pass): apply the mass once per i
     if (!POT && P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
-        work_loop<COUNT, POT, EPS0, true, U>(P, buf, ids, lane, P.pos[0].w);
+        work_loop<COUNT, POT, EPS0, true, U>(P, buf, ids, rt, lane, P.pos[0].w);
     else
-        work_loop<COUNT, POT, EPS0, false, U>(P, buf, ids, lane, 0.0f);
+        work_loop<COUNT, POT, EPS0, false, U>(P, buf, ids, rt, lane, 0.0f);
 }
 
 // Positions as (cell, in-cell offset): the precision variant.
 template <bool EPS0>
 __global__ void __launch_bounds__(kThreads, 5) k_sr_force_ci(KParams P) {
     __shared__ float4 tiles[kWarps][kTileCap];
+    __shared__ int4 runs[kWarps][kMaxRuns];
+    __shared__ int4 steps[kWarps][kMaxRuns];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
+    const RunTable rt{runs[w], steps[w]};
     if (P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
-        work_loop<false, false, EPS0, true, 0, true>(P, buf, nullptr, lane, P.pos[0].w);
+        work_loop<false, false, EPS0, true, 0, true>(P, buf, nullptr, rt, lane, P.pos[0].w);
     else
-        work_loop<false, false, EPS0, false, 0, true>(P, buf, nullptr, lane, 0.0f);
+        work_loop<false, false, EPS0, false, 0, true>(P, buf, nullptr, rt, lane, 0.0f);
 }
 
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
