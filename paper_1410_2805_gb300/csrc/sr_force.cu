@@ -208,18 +208,21 @@ struct RunTable {
 // misses.)
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &rt, int r0, int r1, float L, float tx,
-                                             float ty, float tz, int iself, int lg, int grp, const Bounds &bb,
-                                             const float (&xi)[K], const float (&yi)[K], const float (&zi)[K],
+                                             float ty, float tz, int iself, int i_end, int lg, int grp,
+                                             const Bounds &bb, float (&xs)[K], float (&ys)[K], float (&zs)[K],
                                              float (&ax)[K], float (&ay)[K], float (&az)[K], unsigned &cnt,
                                              unsigned &jsum, float4 *buf, int *ids, int lane, int &fill, bool last) {
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
     const int G = 1 << lg;
-    float xs[K], ys[K], zs[K];
+    // the i shift is applied in place and undone by reloading the coordinates
+    // after the runs (no second copy of them in registers)
+    if (ishift) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        xs[k] = ishift ? __fadd_rn(xi[k], tx) : xi[k];
-        ys[k] = ishift ? __fadd_rn(yi[k], ty) : yi[k];
-        zs[k] = ishift ? __fadd_rn(zi[k], tz) : zi[k];
+        for (int k = 0; k < K; ++k) {
+            xs[k] = __fadd_rn(xs[k], tx);
+            ys[k] = __fadd_rn(ys[k], ty);
+            zs[k] = __fadd_rn(zs[k], tz);
+        }
     }
     const PairConsts C{P.eps, P.T, P.q0, P.q1, P.q2, P.q3, P.q4, P.q5};
     const float4 dummy = make_float4(1e18f, 1e18f, 1e18f, 0.0f);   // far away, zero mass
@@ -304,6 +307,16 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
         if (t0 >= t_end && fill == 0) break;
     }
     __syncwarp();
+    if (ishift) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = iself + (32 >> lg) * k;
+            const float4 p = i < i_end ? P.pos[i] : make_float4(-1e30f, -1e30f, -1e30f, 0.0f);
+            xs[k] = p.x;
+            ys[k] = p.y;
+            zs[k] = p.z;
+        }
+    }
 }
 
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
@@ -423,19 +436,16 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
     // within R of the high faces): then every run ends its own tile.
     const bool carry = CI || (cx + R < nc && cy + R < nc && cz + R < nc);
     int fill = 0;
-    if (carry) {
-        process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, 0, nrun, L, 0.0f, 0.0f, 0.0f, iself, lg, grp, bb, xi, yi,
-                                                     zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
-    } else {
 #pragma unroll 1
-        for (int q = 0; q < nrun; ++q) {
-            const int4 a = rt.A[q];
-            const int start = q > 0 ? rt.A[q - 1].x : 0;
-            if (a.x == start) continue;   // empty run
-            const float tx = (a.z & 8) ? -L : 0.0f, ty = (a.z & 16) ? -L : 0.0f, tz = (a.z & 32) ? -L : 0.0f;
-            process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, q, q + 1, L, tx, ty, tz, iself, lg, grp, bb, xi, yi,
-                                                         zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
-        }
+    for (int q = 0; q < nrun;) {
+        // all runs at once, or one run with its own i shift
+        const int q1 = carry ? nrun : q + 1;
+        const int bits = carry ? 0 : rt.A[q].z;
+        const float tx = (bits & 8) ? -L : 0.0f, ty = (bits & 16) ? -L : 0.0f, tz = (bits & 32) ? -L : 0.0f;
+        if (rt.A[q1 - 1].x > (q > 0 ? rt.A[q - 1].x : 0))   // not empty
+            process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, q, q1, L, tx, ty, tz, iself, i0 + ni, lg, grp, bb,
+                                                         xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
+        q = q1;
     }
 
     // sum the groups' partial forces (the groups saw disjoint j)
