@@ -336,6 +336,9 @@ void hacc_ctx_destroy(hacc_ctx *ctx) {
     if (ctx->ml_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->ml_exec));
     if (ctx->cap_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->cap_stream));
     if (ctx->cap_stream2) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->cap_stream2));
+    if (ctx->io_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->io_stream));
+    for (void *e : ctx->io_ev)
+        if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
     for (auto &e : ctx->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (auto &e : ctx->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     if (tl_launches == &ctx->launches) tl_launches = nullptr;
@@ -1040,9 +1043,12 @@ hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm,
                     nullptr, 0.0f, s);
 }
 
-hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm, int64_t n,
-                      float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream) {
-    HACC_TRY(enter(ctx));
+// The full step (Eq. tstep); vel_ready (nullable) is waited for before the
+// first use of vel, pos_final (nullable) is recorded once pos holds its final
+// values (before the closing PM half kick, which only reads pos).
+static hacc_status step_impl(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
+                             int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream,
+                             cudaEvent_t vel_ready, cudaEvent_t pos_final) {
     if (n_c < 1) return set_error(ctx, HACC_EINVAL, "n_c must be >= 1");
     HACC_TRY(check_particles(ctx, n, pos_m, vel));
     if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
@@ -1051,10 +1057,18 @@ hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     float4 *v = reinterpret_cast<float4 *>(vel);
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     // M_lr(dt/2): kick by the long-range force
-    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s));
+    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s, vel_ready));
+    if (vel_ready && n == 0) HACC_CUDA(cudaStreamWaitEvent(s, vel_ready, 0), "cudaStreamWaitEvent");
     HACC_TRY(hacc_subcycle(ctx, box, split, n, pos_m, vel, dt, n_c, stream));
+    if (pos_final) HACC_CUDA(cudaEventRecord(pos_final, s), "cudaEventRecord");
     HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s));
     return HACC_OK;
+}
+
+hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm, int64_t n,
+                      float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    return step_impl(ctx, box, split, pm, n, pos_m, vel, dt, n_c, stream, nullptr, nullptr);
 }
 
 hacc_status hacc_sr_force_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
@@ -1101,11 +1115,33 @@ hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split 
     char *base = static_cast<char *>(ctx->io_base);
     float *dp = reinterpret_cast<float *>(base);
     float *dv = reinterpret_cast<float *>(base + ((bytes + 255) & ~size_t(255)));
+    // a second stream overlaps the velocity upload with the first PM field
+    // solve and the position download with the closing PM half kick
+    if (!ctx->io_stream) {
+        cudaStream_t a = nullptr;
+        HACC_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking), "cudaStreamCreate");
+        ctx->io_stream = a;
+        for (auto &ev : ctx->io_ev) {
+            cudaEvent_t e = nullptr;
+            HACC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+            ev = e;
+        }
+    }
+    cudaStream_t aux = static_cast<cudaStream_t>(ctx->io_stream);
+    cudaEvent_t ev_start = static_cast<cudaEvent_t>(ctx->io_ev[0]);
+    cudaEvent_t ev_vel = static_cast<cudaEvent_t>(ctx->io_ev[1]);
+    cudaEvent_t ev_pos = static_cast<cudaEvent_t>(ctx->io_ev[2]);
+    HACC_CUDA(cudaEventRecord(ev_start, s), "cudaEventRecord");
+    HACC_CUDA(cudaStreamWaitEvent(aux, ev_start, 0), "cudaStreamWaitEvent");
     HACC_CUDA(cudaMemcpyAsync(dp, pos_m, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
-    HACC_CUDA(cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
-    HACC_TRY(hacc_step(ctx, box, split, pm, n, dp, dv, dt, n_c, stream));
-    HACC_CUDA(cudaMemcpyAsync(pos_m, dp, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    HACC_CUDA(cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, aux), "H2D copy");
+    HACC_CUDA(cudaEventRecord(ev_vel, aux), "cudaEventRecord");
+    HACC_TRY(step_impl(ctx, box, split, pm, n, dp, dv, dt, n_c, stream, ev_vel, ev_pos));
+    HACC_CUDA(cudaStreamWaitEvent(aux, ev_pos, 0), "cudaStreamWaitEvent");
+    HACC_CUDA(cudaMemcpyAsync(pos_m, dp, bytes, cudaMemcpyDeviceToHost, aux), "D2H copy");
+    HACC_CUDA(cudaEventRecord(ev_start, aux), "cudaEventRecord");
     HACC_CUDA(cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
+    HACC_CUDA(cudaStreamWaitEvent(s, ev_start, 0), "cudaStreamWaitEvent");
     return hacc_ctx_sync(ctx, stream);
 }
 

@@ -67,6 +67,10 @@ struct hacc_ctx {
     uint64_t ml_key = 0;
     int64_t ml_launches = 0, ml_forces = 0;
     void *cap_stream = nullptr, *cap_stream2 = nullptr;
+    // host-buffer full steps (api.cu): a second stream and events that let the
+    // velocity upload and the position download overlap the PM stages
+    void *io_stream = nullptr;
+    void *io_ev[3] = {nullptr, nullptr, nullptr};
     bool ml_graph_off = false;   // set when the device refused the graph once
 };
 
@@ -316,8 +320,10 @@ cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const f
 // ---- PM (pm.cu) ------------------------------------------------------------
 // Long-range acceleration G * a_PM at pos; stored to acc (if non-null) and/or
 // added as a kick vel += kick * a (if vel_kick is non-null).
+// before_kick (nullable): an event the stream waits for between the field
+// solve and the interpolation, which is the first use of vel_kick.
 hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, double G, int64_t n, const float4 *pos,
-                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s);
+                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s, cudaEvent_t before_kick = nullptr);
 void pm_destroy(hacc_ctx *ctx);
 
 }  // namespace hacc

@@ -237,7 +237,7 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBl
 }  // namespace
 
 hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, double G, int64_t n, const float4 *pos,
-                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s) {
+                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s, cudaEvent_t before_kick) {
     if (!box || !pm) return set_error(ctx, HACC_EINVAL, "box or pm is NULL");
     const double L = box->L;
     if (!(L > 0) || !std::isfinite(L)) return set_error(ctx, HACC_EINVAL, "box side L must be finite and > 0");
@@ -270,6 +270,8 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
     for (int c = 0; c < 3; ++c)
         if (cufftExecC2R(st->c2r, st->ak + c * nm, st->field + c * ng3) != CUFFT_SUCCESS)
             return set_error(ctx, HACC_ECUDA, "cufftExecC2R failed");
+    if (before_kick && (e = cudaStreamWaitEvent(s, before_kick, 0)) != cudaSuccess)
+        return check_cuda(ctx, e, "cudaStreamWaitEvent");
     k_interp<<<blocks_for(n), kBlock, 0, s>>>(n, pos, inv_d, ng, st->field, acc, vel_kick, kick);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(ctx, e, "PM kernels");
