@@ -8,15 +8,18 @@
 // cutoff test into the force evaluation the same way, with fsel).
 //
 // GPU mapping.  Work item = up to 160 particles of one cell (one warp; K of
-// them per lane, K = 1..5, in 1-8 lane groups, by cell occupancy).  Because cells are numbered
-// x-fastest, the three cells (ix-1, ix, ix+1) of each of the 9 (dy, dz) rows
-// are one contiguous run of the cell-sorted particle array, so an item
-// streams 9 runs (a second run when the row wraps in x).  Each run is staged
-// 32 particles at a time into a per-warp shared-memory tile with coalesced
-// 16-byte loads; every lane then reads each j with one broadcast 16-byte
+// them per lane, K = 1..5, in 1-8 lane groups, by cell occupancy).  Because
+// cells are numbered x-fastest, the three cells (ix-1, ix, ix+1) of each of
+// the 9 (dy, dz) rows are one contiguous run of the cell-sorted particle
+// array (a second run when the row wraps in x).  The lanes first write the
+// item's runs into a per-warp table; the runs are then staged as one stream,
+// 32 candidates per round with coalesced 16-byte loads, into a per-warp
+// shared-memory tile, keeping only the candidates within reach of the item's
+// bounding box.  Every lane reads each staged j with one broadcast 16-byte
 // shared load and evaluates it against its K particles, accumulating in FP32
 // registers.  Work items are taken from an atomic counter so that clustered
-// cells do not leave SMs idle.
+// cells do not leave SMs idle.  With the finer mesh (stencil radius R = 2)
+// the rows are 25 and the runs 5 cells long.
 //
 // Periodic images without rounding error: for a neighbour row that wraps on
 // the low side (cell -1 -> nc-1), the staged j coordinates get -L (they lie in
@@ -24,10 +27,11 @@
 // (cell nc -> 0), the i coordinates get -L instead (same argument).  Either
 // way r_ij = x_j' - x_i' carries only the rounding of one subtraction.
 //
-// Per candidate pair (FP32): 3 FADD (r), 3 FFMA (t = s + eps), 1 MUFU rsqrt,
-// 2 FMUL (t^-3/2), 5 FFMA (P5 in t), 1 FADD, 1 FMUL (mass), compare + select
-// (cutoff), 3 FFMA (accumulate); P5 is re-expanded in t = s + eps on the
-// host, and the cutoff test is t < fl(r_cut^2 + eps).
+// Per evaluated pair (FP32): 3 FADD (r), 3 FFMA (t = s + eps), 1 MUFU rsqrt,
+// 1 FMUL + 1 FFMA (t^-3/2 - P5), 5 FFMA (P5 in t), 1 FMUL (mass; dropped when
+// all masses are equal), 1 compare, 3 predicated FFMA (accumulate inside the
+// cutoff); P5 is re-expanded in t = s + eps on the host, and the cutoff test
+// is t < fl(r_cut^2 + eps).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
