@@ -173,11 +173,16 @@ hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
  * times (2k+1)/(2l) dt, k < l; all particles stream together between the union
  * of those times over the counts that occur, so each streams by dt in total.
  * The mesh is kept while the particles move (as the paper keeps its tree):
- * at each event the largest per-axis drift from the binned positions is read
- * (one host synchronisation per event), and only when it passes half the
- * cell's excess width over r_cut are the particles rebinned.  At an event only
- * the cells holding a kicked particle get work items.  skin must be finite
- * and >= 0.  level_out (nullable, device, n) receives the kick counts. */
+ * at each event the largest per-axis drift from the binned positions is
+ * checked, and only when it passes half the cell's excess width over r_cut
+ * are the particles rebinned.  At an event only the cells holding a kicked
+ * particle get work items.  One host synchronisation per step reads which
+ * kick counts occur; the events then run as one CUDA graph cached by the
+ * context (the rebinnings are conditional nodes decided on the device), or,
+ * with statistics timing or counting on, from the host with one
+ * synchronisation per event (the same kernels in the same order).  skin must
+ * be finite and >= 0.  level_out (nullable, device, n) receives the kick
+ * counts. */
 hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
                              float *vel, double dt, int32_t d, int32_t lmax, float skin, int32_t *level_out,
                              hacc_stream_t stream);
