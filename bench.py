@@ -664,8 +664,10 @@ def run_ours(args):
         # Zel'dovich box at a step where most particles drift a small part of
         # a cell (the regime the paper's fixed tree assumes), and the violent
         # blob box where the mesh is rebuilt at almost every event
-        line["multilevel"] = run_multilevel(torch, hacc, ctx, split, workload="zel128", d=1, lmax=4, dt=0.02)
-        line["multilevel_violent"] = run_multilevel(torch, hacc, ctx, split, workload="blob128", d=2, lmax=4, dt=0.04)
+        line["multilevel"] = run_multilevel(torch, hacc, ctx, split, workload="zel128", d=1, lmax=4, dt=0.02,
+                                            skin=0.1)
+        line["multilevel_violent"] = run_multilevel(torch, hacc, ctx, split, workload="blob128", d=2, lmax=4, dt=0.04,
+                                                    skin=0.1)
         line["fine_mesh"] = run_fine_mesh(torch, hacc, ctx, split, pos, L)
     if not args.no_served:
         served = run_served(torch, hacc, ctx, split, rate=50.0, window=args.served_window, cap_s=args.served_cap)
