@@ -54,6 +54,7 @@ class _BatchBox(ctypes.Structure):
 
 
 TICK_FIRST, TICK_LAST = 1, 2
+FORCE_VARIANTS = 4   # HACC_FORCE_VARIANTS
 
 
 @dataclass
@@ -261,7 +262,7 @@ class Context:
         """Time every pair-kernel variant on this machine and keep the fastest."""
         _dev_rows(pos, "pos")
         sp = _split_of(split)
-        nv = 4
+        nv = FORCE_VARIANTS
         times = (ctypes.c_double * nv)()
         chosen = ctypes.c_int32(-1)
         self._check(lib().hacc_tune(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0], _ptr(pos),

@@ -323,6 +323,117 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
     }
 }
 
+// Write the run table of cell (cx, cy, cz) (of the box whose cells start at
+// cbase) for stencil radius R, one run per lane; returns the number of runs.
+template <bool CI>
+__device__ __forceinline__ int build_runs(const KParams &P, const RunTable &rt, int cbase, int nc, int cx, int cy,
+                                          int cz, int R, int lane) {
+    const int span = 2 * R + 1;
+    const int nrun = 2 * span * span;
+    int run_end = 0;   // running total of the run lengths written so far
+    for (int q0 = 0; q0 < nrun; q0 += 32) {
+        const int q = q0 + lane;
+        int ja = 0, jb = 0, bits = 0, b1 = 0, b2 = 0, d0 = 0;
+        if (q < nrun) {
+            const int rowi = q >> 1, r = q & 1;
+            const int dz = rowi / span - R, dy = rowi % span - R;
+            int rz = cz + dz, ry = cy + dy;
+            if (rz < 0) { rz += nc; bits |= 4; }
+            else if (rz >= nc) { rz -= nc; bits |= 32; }
+            if (ry < 0) { ry += nc; bits |= 2; }
+            else if (ry >= nc) { ry -= nc; bits |= 16; }
+            if (CI) bits = (dy + 2) | ((dz + 2) << 4);
+            const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
+            // cells lo..hi of this row: one run, or two when it wraps in x
+            const int lo = cx - R, hi = cx + R;
+            const bool wraps = lo < 0 || hi >= nc;
+            if (lo < 0) {           // [0, hi], then [nc + lo, nc) with j shifted by -L
+                ja = r ? row[nc + lo] : row[0];
+                jb = r ? row[nc] : row[hi + 1];
+                if (r && !CI) bits |= 1;
+                b1 = r ? jb : row[1];
+                d0 = r ? -1 : 0;
+            } else if (hi >= nc) {  // [lo, nc), then [0, hi - nc] with i shifted by -L
+                ja = r ? row[0] : row[lo];
+                jb = r ? row[hi - nc + 1] : row[nc];
+                if (r && !CI) bits |= 8;
+                b1 = r ? jb : row[nc - 1];
+                d0 = r ? 1 : -1;
+            } else if (r == 0) {
+                ja = row[lo];
+                jb = row[hi + 1];
+                b1 = row[cx];
+                d0 = -1;
+            }
+            b2 = wraps ? jb : (r == 0 ? row[cx + 1] : 0);
+        }
+        // exclusive ends of the runs in the concatenated stream
+        int e = jb - ja;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, e, o);
+            if (lane >= o) e += y;
+        }
+        e += run_end;
+        if (q < nrun) {
+            rt.A[q] = make_int4(e, ja - (e - (jb - ja)), bits, 0);
+            if (CI) rt.B[q] = make_int4(b1, b2, d0, 0);
+        }
+        run_end = __shfl_sync(0xffffffffu, e, 31);
+    }
+    __syncwarp();
+    return nrun;
+}
+
+// Apply the force on sorted particle i (position x, y, z, mass m) as the
+// launch's mode says: store it, kick, or kick and stream.
+__device__ __forceinline__ void write_result(const KParams &P, int i, float gx, float gy, float gz, float x, float y,
+                                             float z, float m, float h_kick, float h_drift, float L) {
+    if (P.mode == kModeForce) {
+        int o = P.perm ? P.perm[i] : i;
+        P.out[o] = make_float4(gx, gy, gz, 0.0f);
+    } else if (P.mode == kModeKickLevels) {
+        const float hk = P.kick.h[P.levels[i]];
+        if (hk != 0.0f) {
+            float4 v = P.vel[i];
+            v.x = __fmaf_rn(hk, gx, v.x);
+            v.y = __fmaf_rn(hk, gy, v.y);
+            v.z = __fmaf_rn(hk, gz, v.z);
+            if (P.ids) P.vel_pool[P.ids[i]] = v;   // back to input order
+            else P.vel[i] = v;                      // in place, sorted order
+        }
+    } else if (P.mode == kModeKick) {
+        const int row = P.ids[i];
+        float4 v = P.vel[i];
+        v.x = __fmaf_rn(h_kick, gx, v.x);
+        v.y = __fmaf_rn(h_kick, gy, v.y);
+        v.z = __fmaf_rn(h_kick, gz, v.z);
+        P.vel_pool[row] = v;
+    } else {
+        float4 v = P.vel[i];
+        v.x = __fmaf_rn(h_kick, gx, v.x);
+        v.y = __fmaf_rn(h_kick, gy, v.y);
+        v.z = __fmaf_rn(h_kick, gz, v.z);
+        float4 p;
+        p.x = __fmaf_rn(h_drift, v.x, x);
+        p.y = __fmaf_rn(h_drift, v.y, y);
+        p.z = __fmaf_rn(h_drift, v.z, z);
+        p.w = m;
+        if (P.mode == kModeBatch) {
+            // back to the box's pool row, wrapped into [0, L)
+            bool ok = wrap1(p.x, L);
+            ok &= wrap1(p.y, L);
+            ok &= wrap1(p.z, L);
+            if (!ok) atomicOr(P.flags, kFlagDomain);
+            const int row = P.ids[i];
+            P.vel_pool[row] = v;
+            P.pos_pool[row] = p;
+        } else {
+            P.vel[i] = v;
+            P.pos_next[i] = p;
+        }
+    }
+}
+
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids, const RunTable &rt, int lane,
                              float m_uniform) {
@@ -380,62 +491,9 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
         bb.hz = fmaxf(bb.hz, __shfl_xor_sync(0xffffffffu, bb.hz, o));
     }
 
-    // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine),
-    // described by the lanes in the warp's run table
+    // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine)
     const int R = P.boxes ? 1 : P.R;
-    const int span = 2 * R + 1;
-    const int nrun = 2 * span * span;
-    int run_end = 0;   // running total of the run lengths written so far
-    for (int q0 = 0; q0 < nrun; q0 += 32) {
-        const int q = q0 + lane;
-        int ja = 0, jb = 0, bits = 0, b1 = 0, b2 = 0, d0 = 0;
-        if (q < nrun) {
-            const int rowi = q >> 1, r = q & 1;
-            const int dz = rowi / span - R, dy = rowi % span - R;
-            int rz = cz + dz, ry = cy + dy;
-            if (rz < 0) { rz += nc; bits |= 4; }
-            else if (rz >= nc) { rz -= nc; bits |= 32; }
-            if (ry < 0) { ry += nc; bits |= 2; }
-            else if (ry >= nc) { ry -= nc; bits |= 16; }
-            if (CI) bits = (dy + 2) | ((dz + 2) << 4);
-            const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
-            // cells lo..hi of this row: one run, or two when it wraps in x
-            const int lo = cx - R, hi = cx + R;
-            const bool wraps = lo < 0 || hi >= nc;
-            if (lo < 0) {           // [0, hi], then [nc + lo, nc) with j shifted by -L
-                ja = r ? row[nc + lo] : row[0];
-                jb = r ? row[nc] : row[hi + 1];
-                if (r && !CI) bits |= 1;
-                b1 = r ? jb : row[1];
-                d0 = r ? -1 : 0;
-            } else if (hi >= nc) {  // [lo, nc), then [0, hi - nc] with i shifted by -L
-                ja = r ? row[0] : row[lo];
-                jb = r ? row[hi - nc + 1] : row[nc];
-                if (r && !CI) bits |= 8;
-                b1 = r ? jb : row[nc - 1];
-                d0 = r ? 1 : -1;
-            } else if (r == 0) {
-                ja = row[lo];
-                jb = row[hi + 1];
-                b1 = row[cx];
-                d0 = -1;
-            }
-            b2 = wraps ? jb : (r == 0 ? row[cx + 1] : 0);
-        }
-        // exclusive ends of the runs in the concatenated stream
-        int e = jb - ja;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, e, o);
-            if (lane >= o) e += y;
-        }
-        e += run_end;
-        if (q < nrun) {
-            rt.A[q] = make_int4(e, ja - (e - (jb - ja)), bits, 0);
-            if (CI) rt.B[q] = make_int4(b1, b2, d0, 0);
-        }
-        run_end = __shfl_sync(0xffffffffu, e, 31);
-    }
-    __syncwarp();
+    const int nrun = build_runs<CI>(P, rt, cbase, nc, cx, cy, cz, R, lane);
     // Tiles run on across all runs unless a run shifts the i side (cells
     // within R of the high faces): then every run ends its own tile.
     const bool carry = CI || (cx + R < nc && cy + R < nc && cz + R < nc);
@@ -474,51 +532,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
                 continue;
             }
             const float gm = UM ? P.G * m_uniform : P.G;
-            float gx = gm * ax[k], gy = gm * ay[k], gz = gm * az[k];
-            if (P.mode == kModeForce) {
-                int o = P.perm ? P.perm[i] : i;
-                P.out[o] = make_float4(gx, gy, gz, 0.0f);
-            } else if (P.mode == kModeKickLevels) {
-                const float hk = P.kick.h[P.levels[i]];
-                if (hk != 0.0f) {
-                    float4 v = P.vel[i];
-                    v.x = __fmaf_rn(hk, gx, v.x);
-                    v.y = __fmaf_rn(hk, gy, v.y);
-                    v.z = __fmaf_rn(hk, gz, v.z);
-                    if (P.ids) P.vel_pool[P.ids[i]] = v;   // back to input order
-                    else P.vel[i] = v;                      // in place, sorted order
-                }
-            } else if (P.mode == kModeKick) {
-                const int row = P.ids[i];
-                float4 v = P.vel[i];
-                v.x = __fmaf_rn(h_kick, gx, v.x);
-                v.y = __fmaf_rn(h_kick, gy, v.y);
-                v.z = __fmaf_rn(h_kick, gz, v.z);
-                P.vel_pool[row] = v;
-            } else {
-                float4 v = P.vel[i];
-                v.x = __fmaf_rn(h_kick, gx, v.x);
-                v.y = __fmaf_rn(h_kick, gy, v.y);
-                v.z = __fmaf_rn(h_kick, gz, v.z);
-                float4 p;
-                p.x = __fmaf_rn(h_drift, v.x, xi[k]);
-                p.y = __fmaf_rn(h_drift, v.y, yi[k]);
-                p.z = __fmaf_rn(h_drift, v.z, zi[k]);
-                p.w = mi[k];
-                if (P.mode == kModeBatch) {
-                    // back to the box's pool row, wrapped into [0, L)
-                    bool ok = wrap1(p.x, L);
-                    ok &= wrap1(p.y, L);
-                    ok &= wrap1(p.z, L);
-                    if (!ok) atomicOr(P.flags, kFlagDomain);
-                    const int row = P.ids[i];
-                    P.vel_pool[row] = v;
-                    P.pos_pool[row] = p;
-                } else {
-                    P.vel[i] = v;
-                    P.pos_next[i] = p;
-                }
-            }
+            write_result(P, i, gm * ax[k], gm * ay[k], gm * az[k], xi[k], yi[k], zi[k], mi[k], h_kick, h_drift, L);
         }
     }
     if (COUNT) {

@@ -239,9 +239,10 @@ def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_para
     p = _dev(torch, pos)
     box = hacc.Box(L=28.0)
     res = ctx.tune(box, split_params, p, reps=1)
-    assert 0 <= res["chosen"] < 4 and all(t > 0 for t in res["times_ms"])
+    assert 0 <= res["chosen"] < hacc.FORCE_VARIANTS and all(t > 0 for t in res["times_ms"])
+    assert len(res["times_ms"]) == hacc.FORCE_VARIANTS
     ref = None
-    for v in range(4):
+    for v in range(hacc.FORCE_VARIANTS):
         ctx.set_variant(v)
         a = ctx.sr_force(box, split_params, p).clone()
         if ref is None:
