@@ -345,3 +345,24 @@ def test_fine_mesh_subcycle_and_limits(torch, hacc, ctx, split_params):
     with pytest.raises(hacc.HaccError) as e:
         ctx.set_stencil(3)
     assert e.value.status == hacc.HACC_EINVAL
+
+
+def test_fine_mesh_smallest_box_against_brute_force(torch, hacc, ctx, split_params):
+    # L = 9 holds 5 cells of width >= r_cut/2 (the 125-cell stencil then spans
+    # the whole box once) but fewer than 3 cells of width >= r_cut: only the
+    # finer mesh can take it; brute force over all pairs is the reference
+    L = 9.0
+    sp = split_params
+    assert hacc.mesh_cells(L, np.float32(sp["r_cut"]) / 2) == 5 and hacc.mesh_cells(L, sp["r_cut"]) == -1
+    pos = synth.blob_mixture(700, L, seed=96, n_blobs=3, sigma=0.5)
+    a_ref, _ = oracle.force_brute(pos, L, sp)
+    p = _dev(torch, pos)
+    ctx.set_stencil(2)
+    try:
+        a = ctx.sr_force(hacc.Box(L=L), sp, p).cpu().numpy()
+    finally:
+        ctx.set_stencil(1)
+    assert _force_err(a, a_ref) <= FORCE_TOL
+    with pytest.raises(hacc.HaccError) as e:
+        ctx.sr_force(hacc.Box(L=L), sp, p)
+    assert e.value.status == hacc.HACC_EDOMAIN
