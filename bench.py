@@ -301,13 +301,34 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
         cnt = ctx.stats_read(reset=True)
         ctx.stats_enable(counting=False)
         same = bool(torch.equal(P, fin_p) and torch.equal(V, fin_v))
+        # the same steps once more without the graph, pair-kernel launches timed
+        P.copy_(snap_p)
+        V.copy_(snap_v)
+        ctx.stats_enable(timing=True)
+        for _ in range(steps):
+            ctx.batch_subcycle(split, boxes, P, V, n_sub, use_graph=False, stream=stream)
+        stream.synchronize()
+        tst = ctx.stats_read(reset=True)
+        ctx.stats_enable()
     ctx.sync(stream)          # raises if a coordinate left [-L, 2L)
     n = off
+    peaks = measured_peaks()
+    num_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = fp32_peak_tflops(num_sms, float(peaks.get("sm_max_mhz") or 2070.0))
+    force_s = tst["force_ms"] / 1e3
+    ach = cnt["candidate_pairs"] * FLOPS_PER_PAIR / force_s / 1e12 if force_s > 0 else None
     return {"workload": "200 blob-mixture boxes, N log-uniform 16^3..128^3 (total %d), 10 SR sub-cycles per "
                         "step, one batched launch per sub-cycle, CUDA graph" % n,
             "pair_interactions_per_s": cnt["within_pairs"] / (ms / 1e3),
             "particle_steps_per_s": n * n_sub * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
-            "gpu_launches": st["kernel_launches"], "replay_bitwise_equal": same}
+            "gpu_launches": st["kernel_launches"], "replay_bitwise_equal": same,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (ach / peak) if ach else None,
+                         "candidate_pairs_per_step": cnt["candidate_pairs"] / steps,
+                         "evaluated_pairs_per_step": cnt["evaluated_pairs"] / steps,
+                         "force_ms_per_step": tst["force_ms"] / steps,
+                         "basis": "29 flop per 27-cell candidate pair over the pair-kernel time (events, "
+                                  "a replay without the graph)"}}
 
 
 def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, workload="blob128", dt=0.04, skin=0.05):

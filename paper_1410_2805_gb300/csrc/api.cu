@@ -296,6 +296,14 @@ hacc_status launch_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc
 
 }  // namespace
 
+// One counted pair-kernel launch, timed when statistics timing is on (for
+// the batched path; not while the stream is being captured).
+hacc_status hacc::timed_force_launch(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl,
+                                     cudaStream_t s) {
+    return launch_force(ctx, g, fc, fl, true, s);
+}
+
+
 extern "C" {
 
 hacc_status hacc_ctx_create(hacc_ctx **out, int device, size_t hbm_budget_bytes) {

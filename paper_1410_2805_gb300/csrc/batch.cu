@@ -145,6 +145,12 @@ hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const
     g.nc = 3;
     g.ncell = 27;
     g.inv_w = 3.f;
+    if (ctx->counting)
+        HACC_CUDA_RETURN(candidate_count_batch(pl.ncell_total, tab, pl.nbox, w.b.cell_start, ctx->d_pairs, s),
+                         "batched candidate count");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HACC_CUDA_RETURN(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+    if (cap == cudaStreamCaptureStatusNone) return timed_force_launch(ctx, g, fc, fl, s);
     HACC_CUDA_RETURN(sr_force_launch(g, fc, fl, ctx->num_sms, s), "batched pair force");
     ctx->force_launches++;
     return HACC_OK;

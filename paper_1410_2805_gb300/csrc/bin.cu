@@ -435,6 +435,39 @@ __global__ void __launch_bounds__(kBlock) k_scatter(int64_t n, const int32_t *__
     }
 }
 
+__global__ void __launch_bounds__(kBlock) k_candidates_batch(int64_t ncell_total, const BoxDev *__restrict__ boxes,
+                                                              int nbox, const int32_t *__restrict__ cell_start,
+                                                              unsigned long long *out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (c < ncell_total) {
+        const int ni = cell_start[c + 1] - cell_start[c];
+        if (ni) {
+            int lo = 0, hi = nbox - 1;   // last box whose first cell is <= c
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (boxes[mid].cell_base <= c) lo = mid;
+                else hi = mid - 1;
+            }
+            const int nc = boxes[lo].nc, base = boxes[lo].cell_base;
+            const int64_t l = c - base;
+            const int cx = (int)(l % nc), cy = (int)((l / nc) % nc), cz = (int)(l / ((int64_t)nc * nc));
+            unsigned long long nb = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int jx = (cx + dx + nc) % nc, jy = (cy + dy + nc) % nc, jz = (cz + dz + nc) % nc;
+                        const int64_t j = base + ((int64_t)jz * nc + jy) * nc + jx;
+                        nb += (unsigned long long)(cell_start[j + 1] - cell_start[j]);
+                    }
+            v = (unsigned long long)ni * nb;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 // Candidate pairs of the chaining mesh: sum_c n_c * sum_{nbr} n_nbr over the
 // (2R+1)^3 neighbour cells (R = 1: the 27 cells).
 __global__ void __launch_bounds__(kBlock) k_candidates(int nc, int R, const int32_t *__restrict__ cell_start,
@@ -851,6 +884,13 @@ cudaError_t scatter_rows(int64_t n, const int32_t *id, const float4 *p_in, float
                          float4 *v_out, float Lf, int *d_flags, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_scatter<<<blocks_for(n), kBlock, 0, s>>>(n, id, p_in, p_out, v_in, v_out, Lf, d_flags);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t candidate_count_batch(int64_t ncell_total, const BoxDev *boxes, int nbox, const int32_t *cell_start,
+                                  unsigned long long *out, cudaStream_t s) {
+    k_candidates_batch<<<blocks_for(ncell_total), kBlock, 0, s>>>(ncell_total, boxes, nbox, cell_start, out);
     note_launch();
     return cudaGetLastError();
 }

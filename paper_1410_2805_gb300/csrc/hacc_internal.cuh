@@ -260,6 +260,10 @@ cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, fl
 cudaError_t scatter_rows(int64_t n, const int32_t *id, const float4 *p_in, float4 *p_out,
                          const float4 *v_in, float4 *v_out, float Lf, int *d_flags, cudaStream_t s);
 
+// Candidate pairs of a batch: each global cell against the 27 cells around
+// it inside its own box (boxes sorted by cell_base).
+cudaError_t candidate_count_batch(int64_t ncell_total, const BoxDev *boxes, int nbox, const int32_t *cell_start,
+                                  unsigned long long *out, cudaStream_t s);
 cudaError_t candidate_count(const Geometry &g, const int32_t *cell_start, unsigned long long *out,
                             cudaStream_t s);
 
@@ -312,6 +316,8 @@ constexpr int kForceVariants = 4;
 
 cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
                             cudaStream_t s);
+hacc_status timed_force_launch(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl,
+                               cudaStream_t s);
 
 // FP64 sums: out[0..2] = sum m v, out[3] = sum m v^2 / 2, out[4] = sum phi.
 cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const float *phi, double *out,
