@@ -113,3 +113,26 @@ def test_ticks_equal_subcycle(env, split_params):
                                       for (o, n, L) in boxes], P2, V2)
     ctx.sync()
     assert torch.equal(P1, P2) and torch.equal(V1, V2)
+
+
+def test_batch_candidate_count_exact(env, split_params):
+    # at rest the batched sub-cycle bins the given positions; its 27-cell
+    # candidate count is then the sum of every box's own count
+    torch, hacc, ctx = env
+    pos, _, boxes = _pool(SPECS)
+    P = torch.from_numpy(pos).cuda()
+    V = torch.zeros_like(P)
+    bb = [hacc.BatchBox(L=L, offset=o, n=n, dt=0.1) for (o, n, L) in boxes]
+    ctx.stats_read(reset=True)
+    ctx.stats_enable(counting=True)
+    ctx.batch_subcycle(split_params, bb, P, V, n_sub=1)
+    st = ctx.stats_read(reset=True)
+    ctx.stats_enable()
+    want = 0
+    for (o, n, L) in boxes:
+        nc = hacc.mesh_cells(L, split_params["r_cut"])
+        _, cell_o, _ = oracle.wrap_cell(pos[o:o + n], L, nc)
+        count_o, _, _ = oracle.bin_cells(cell_o, nc)
+        want += oracle.candidates(count_o, nc)
+    assert st["candidate_pairs"] == want
+    assert st["within_pairs"] <= st["evaluated_pairs"] <= st["candidate_pairs"]
