@@ -365,7 +365,8 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
  * least r_cut/2 wide (box->nc = 0: hacc_mesh_cells(L, r_cut/2); nc >= 5) and
  * searches the 125 cells within two cells, which covers the same sphere with a
  * smaller search volume (a variant of the library; the paper's own P3M search
- * is the 27-cell one).  The forces are those of the same pairs.  Batched,
+ * is the 27-cell one).  The forces are those of the same pairs.  It also
+ * takes boxes from 5 r_cut / 2 up (the 27-cell mesh needs 3 r_cut).  Batched,
  * served, multi-level, cell/offset and allocation-free paths always use 27
  * cells.  HACC_EINVAL for other values. */
 hacc_status hacc_set_stencil(hacc_ctx *ctx, int32_t cells_per_rcut);
