@@ -703,12 +703,23 @@ def run_ours(args):
         sp = osplit.default_split()
         sp["r_cut"] = float(np.float32(sp["r_cut"]))
         sp["eps"] = float(np.float32(sp["eps"]))
-        cb = cpu_oracle_rate(snap_p.cpu().numpy(), L, sp, target_s=args.cpu_seconds)
+        host = snap_p.cpu().numpy()
+        cb = cpu_oracle_rate(host, L, sp, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": cb["value"], "unit": "pair interactions/s", "cores": cb["threads"],
                                 "kind": "oracle",
                                 "sample": "FP64 short-range force of %d random particles of the warmed-up box "
                                           "(all %d particles as sources, %.1f s)" % (cb["sample_particles"], n,
                                                                                       cb["seconds"])}
+        # the same on one core (a shorter sample)
+        import oracle
+        all_threads = oracle.threads()
+        oracle.set_threads(1)
+        try:
+            c1 = cpu_oracle_rate(host, L, sp, target_s=max(2.0, args.cpu_seconds / 2))
+        finally:
+            oracle.set_threads(all_threads)
+        line["cpu_baseline"]["single_core"] = {"value": c1["value"], "sample_particles": c1["sample_particles"],
+                                               "seconds": c1["seconds"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
