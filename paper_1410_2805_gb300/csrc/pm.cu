@@ -38,7 +38,7 @@ struct PmState {
     unsigned long long *mass = nullptr;  // ng^3 fixed-point mass per grid point
     cufftComplex *rk = nullptr;  // ng*ng*(ng/2+1)
     cufftComplex *ak = nullptr;  // 3 x ng*ng*(ng/2+1)
-    float *field = nullptr;      // 3 x ng^3
+    float4 *field = nullptr;     // ng^3 (a_x, a_y, a_z, 0): one 16-byte load per CIC corner
     float *tab = nullptr;        // per-axis tables: t[ng], sl[ng], K2[ng]
     size_t bytes = 0;
 };
@@ -143,8 +143,16 @@ __global__ void __launch_bounds__(kBlock) k_kspace(int ng, float D, float sigma,
     }
 }
 
+// Component c of the force field from a real ng^3 array into the interleaved grid.
+__global__ void __launch_bounds__(kBlock) k_pack_component(int64_t ng3, const float *__restrict__ src,
+                                                            float4 *__restrict__ field, int c) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng3) return;
+    reinterpret_cast<float *>(field + g)[c] = src[g];
+}
+
 __global__ void __launch_bounds__(kBlock) k_interp(int64_t n, const float4 *__restrict__ pos, float inv_d, int ng,
-                                                    const float *__restrict__ field, float4 *acc, float4 *vel,
+                                                    const float4 *__restrict__ field, float4 *acc, float4 *vel,
                                                     float kick) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(int64_t n, const float4 *__re
     cic_setup(p.x, inv_d, ng, a0, a1, fa);
     cic_setup(p.y, inv_d, ng, b0, b1, fb);
     cic_setup(p.z, inv_d, ng, c0, c1, fc);
-    const int64_t ng2 = (int64_t)ng * ng, ng3 = ng2 * ng;
+    const int64_t ng2 = (int64_t)ng * ng;
     const int ia[2] = {a0, a1}, ib[2] = {b0, b1}, ic[2] = {c0, c1};
     const float wa[2] = {1.f - fa, fa}, wb[2] = {1.f - fb, fb}, wc[2] = {1.f - fc, fc};
     float s[3] = {0.f, 0.f, 0.f};
@@ -166,8 +174,10 @@ __global__ void __launch_bounds__(kBlock) k_interp(int64_t n, const float4 *__re
             for (int z = 0; z < 2; ++z) {
                 int64_t g = ia[x] * ng2 + (int64_t)ib[y] * ng + ic[z];
                 float w = wa[x] * wb[y] * wc[z];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) s[c] = __fmaf_rn(w, field[c * ng3 + g], s[c]);
+                const float4 fg = field[g];
+                s[0] = __fmaf_rn(w, fg.x, s[0]);
+                s[1] = __fmaf_rn(w, fg.y, s[1]);
+                s[2] = __fmaf_rn(w, fg.z, s[2]);
             }
     if (acc) acc[i] = make_float4(s[0], s[1], s[2], 0.f);
     if (vel) {
@@ -204,12 +214,12 @@ hacc_status get_state(hacc_ctx *ctx, int ng, double L, cudaStream_t s, PmState *
         cudaStreamSynchronize(s);
         free_state(st);
         const size_t ng3 = (size_t)ng * ng * ng, nm = (size_t)ng * ng * (ng / 2 + 1);
-        size_t bytes = ng3 * 4 * 4 + ng3 * 8 + nm * 8 * 4 + 3 * ng * 4;
+        size_t bytes = ng3 * 4 + ng3 * 8 + nm * 8 * 4 + ng3 * 16 + 3 * ng * 4;
         if (ctx->budget && ctx->scratch.cap + bytes > ctx->budget)
             return set_error(ctx, HACC_ENOMEM, "PM grid exceeds the context budget");
         if (cudaMalloc(&st->rho, ng3 * 4) != cudaSuccess || cudaMalloc(&st->mass, ng3 * 8) != cudaSuccess ||
             cudaMalloc(&st->rk, nm * 8) != cudaSuccess ||
-            cudaMalloc(&st->ak, 3 * nm * 8) != cudaSuccess || cudaMalloc(&st->field, 3 * ng3 * 4) != cudaSuccess ||
+            cudaMalloc(&st->ak, 3 * nm * 8) != cudaSuccess || cudaMalloc(&st->field, ng3 * 16) != cudaSuccess ||
             cudaMalloc(&st->tab, 3 * ng * 4) != cudaSuccess) {
             cudaGetLastError();
             free_state(st);
@@ -267,9 +277,14 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
     const float pref = (float)(4.0 * 3.14159265358979323846 * G / (double)ng3);
     k_kspace<<<blocks_for(nm), kBlock, 0, s>>>(ng, (float)D, pm->sigma, pm->ns, pref, st->tab, st->rk, st->ak);
     note_launch();
-    for (int c = 0; c < 3; ++c)
-        if (cufftExecC2R(st->c2r, st->ak + c * nm, st->field + c * ng3) != CUFFT_SUCCESS)
+    // each component back to real space (into the density array, free after
+    // the forward transform), then interleaved into the field grid
+    for (int c = 0; c < 3; ++c) {
+        if (cufftExecC2R(st->c2r, st->ak + c * nm, st->rho) != CUFFT_SUCCESS)
             return set_error(ctx, HACC_ECUDA, "cufftExecC2R failed");
+        k_pack_component<<<blocks_for((int64_t)ng3), kBlock, 0, s>>>((int64_t)ng3, st->rho, st->field, c);
+        note_launch();
+    }
     if (before_kick && (e = cudaStreamWaitEvent(s, before_kick, 0)) != cudaSuccess)
         return check_cuda(ctx, e, "cudaStreamWaitEvent");
     k_interp<<<blocks_for(n), kBlock, 0, s>>>(n, pos, inv_d, ng, st->field, acc, vel_kick, kick);
