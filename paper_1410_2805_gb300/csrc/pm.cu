@@ -143,12 +143,14 @@ __global__ void __launch_bounds__(kBlock) k_kspace(int ng, float D, float sigma,
     }
 }
 
-// Component c of the force field from a real ng^3 array into the interleaved grid.
-__global__ void __launch_bounds__(kBlock) k_pack_component(int64_t ng3, const float *__restrict__ src,
-                                                            float4 *__restrict__ field, int c) {
+// The three force components from real ng^3 arrays into the interleaved grid.
+__global__ void __launch_bounds__(kBlock) k_pack_components(int64_t ng3, const float *__restrict__ fx,
+                                                             const float *__restrict__ fy,
+                                                             const float *__restrict__ fz,
+                                                             float4 *__restrict__ field) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng3) return;
-    reinterpret_cast<float *>(field + g)[c] = src[g];
+    field[g] = make_float4(fx[g], fy[g], fz[g], 0.0f);
 }
 
 __global__ void __launch_bounds__(kBlock) k_interp(int64_t n, const float4 *__restrict__ pos, float inv_d, int ng,
@@ -277,14 +279,15 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
     const float pref = (float)(4.0 * 3.14159265358979323846 * G / (double)ng3);
     k_kspace<<<blocks_for(nm), kBlock, 0, s>>>(ng, (float)D, pm->sigma, pm->ns, pref, st->tab, st->rk, st->ak);
     note_launch();
-    // each component back to real space (into the density array, free after
-    // the forward transform), then interleaved into the field grid
-    for (int c = 0; c < 3; ++c) {
-        if (cufftExecC2R(st->c2r, st->ak + c * nm, st->rho) != CUFFT_SUCCESS)
+    // the components back to real space into arrays free at this point (the
+    // density, and the fixed-point mass grid as two real arrays), then
+    // interleaved into the field grid in one pass
+    float *comp[3] = {st->rho, reinterpret_cast<float *>(st->mass), reinterpret_cast<float *>(st->mass) + ng3};
+    for (int c = 0; c < 3; ++c)
+        if (cufftExecC2R(st->c2r, st->ak + c * nm, comp[c]) != CUFFT_SUCCESS)
             return set_error(ctx, HACC_ECUDA, "cufftExecC2R failed");
-        k_pack_component<<<blocks_for((int64_t)ng3), kBlock, 0, s>>>((int64_t)ng3, st->rho, st->field, c);
-        note_launch();
-    }
+    k_pack_components<<<blocks_for((int64_t)ng3), kBlock, 0, s>>>((int64_t)ng3, comp[0], comp[1], comp[2], st->field);
+    note_launch();
     if (before_kick && (e = cudaStreamWaitEvent(s, before_kick, 0)) != cudaSuccess)
         return check_cuda(ctx, e, "cudaStreamWaitEvent");
     k_interp<<<blocks_for(n), kBlock, 0, s>>>(n, pos, inv_d, ng, st->field, acc, vel_kick, kick);
