@@ -222,10 +222,16 @@ __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t 
         if (lane < (int)cnt) perm[s + r] = v;
         return;
     }
+    // larger cells: the ids go to shared memory once, then every lane ranks
+    // its ids against them (broadcast reads)
+    __shared__ int32_t ids[kBlock / 32][kBigCell];
+    int32_t *w = ids[threadIdx.x >> 5];
+    for (uint32_t e = lane; e < cnt; e += 32) w[e] = seg[e];
+    __syncwarp();
     for (uint32_t e = lane; e < cnt; e += 32) {
-        int32_t v = seg[e];
+        const int32_t v = w[e];
         uint32_t r = 0;
-        for (uint32_t q = 0; q < cnt; ++q) r += (seg[q] < v);
+        for (uint32_t q = 0; q < cnt; ++q) r += (w[q] < v);
         perm[s + r] = v;
     }
 }
