@@ -160,7 +160,7 @@ def measured_peaks():
 
 def measured_traffic(n_particles: int):
     """DRAM bytes of one pair-kernel launch from the committed ncu capture,
-    scaled by particles (traffic is ~34 B per particle per launch), or None
+    scaled by particles (traffic is ~63 B per particle per launch), or None
     when the kernel source changed since the capture."""
     import hashlib
     try:
@@ -331,10 +331,13 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
                                   "a replay without the graph)"}}
 
 
-def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, workload="blob128", dt=0.04, skin=0.05):
-    """One 128^3 box: lmax uniform SKS sub-cycles per step against the
-    multi-level step with kick counts l = floor(floor(rho/rho0)/d) + 1 <= lmax
-    (Eq. (kicks)); device time per step, and the pair-kernel share of it."""
+def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, workload="blob128", dt=0.04, skin=0.05,
+                   lmin=1, n_plain=None):
+    """One 128^3 box: n_plain (default lmax) uniform SKS sub-cycles per step
+    against the multi-level step with kick counts l = floor(floor(rho/rho0)/d) + 1
+    clamped to [lmin, lmax] (Eq. (kicks)); device time per step, and the
+    pair-kernel share of it."""
+    n_plain = lmax if n_plain is None else n_plain
     import numpy as np
 
     import synth
@@ -355,9 +358,9 @@ def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, worklo
 
         def one():
             if mode == "plain":
-                ctx.subcycle(box, split, P, V, dt, lmax)
+                ctx.subcycle(box, split, P, V, dt, n_plain)
             else:
-                ctx.subcycle_ml(box, split, P, V, dt, d, lmax, skin=skin, levels=lev)
+                ctx.subcycle_ml(box, split, P, V, dt, d, lmax, skin=skin, levels=lev, lmin=lmin)
         one()
         torch.cuda.synchronize()
         ctx.stats_read(reset=True)
@@ -383,8 +386,8 @@ def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, worklo
             out["force_evaluations_per_particle"] = float((np.arange(1, lmax + 1) * h).sum() / h.sum())
     ctx.sync()
     out["speedup"] = out["ms_per_step_plain"] / out["ms_per_step_multilevel"]
-    out["workload"] = "%s, step %g, d = %d, l_max = %d, skin %g r_cut (%d^3 cells)" % (
-        desc, dt, d, lmax, skin, hacc.ml_mesh_cells(L, split.r_cut, skin))
+    out["workload"] = "%s, step %g, %d uniform sub-cycles vs d = %d, l in [%d, %d], skin %g r_cut (%d^3 cells)" % (
+        desc, dt, n_plain, d, lmin, lmax, skin, hacc.ml_mesh_cells(L, split.r_cut, skin))
     return out
 
 
@@ -689,6 +692,10 @@ def run_ours(args):
                                             skin=0.1)
         line["multilevel_violent"] = run_multilevel(torch, hacc, ctx, split, workload="blob128", d=2, lmax=4, dt=0.04,
                                                     skin=0.1)
+        # the paper's test of Sec. 3.1: 5 sub-cycles for every particle against
+        # at least 2 kicks and up to two more levels, d = 20
+        line["multilevel_paper"] = run_multilevel(torch, hacc, ctx, split, workload="zel128", d=20, lmin=2, lmax=4,
+                                                  n_plain=5, dt=0.02, skin=0.1)
         line["fine_mesh"] = run_fine_mesh(torch, hacc, ctx, split, pos, L)
     if not args.no_served:
         served = run_served(torch, hacc, ctx, split, rate=50.0, window=args.served_window, cap_s=args.served_cap)

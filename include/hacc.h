@@ -169,7 +169,8 @@ hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
  * least r_cut (1 + skin) wide.  The density of each particle's cell at the
  * start of the step, rho / rho0 = count nc_ml^3 / n, sets its kick count
  * l = floor(floor(rho/rho0) / d) + 1 (integers; d <= 0 gives every particle
- * lmax), capped at lmax (1..16).  A particle with l kicks is kicked by dt/l at
+ * lmax), clamped to [lmin, lmax] (1 <= lmin <= lmax <= 16; the paper's test
+ * gives every particle at least two kicks).  A particle with l kicks is kicked by dt/l at
  * times (2k+1)/(2l) dt, k < l; all particles stream together between the union
  * of those times over the counts that occur, so each streams by dt in total.
  * The mesh is kept while the particles move (as the paper keeps its tree):
@@ -184,8 +185,8 @@ hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
  * be finite and >= 0.  level_out (nullable, device, n) receives the kick
  * counts. */
 hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
-                             float *vel, double dt, int32_t d, int32_t lmax, float skin, int32_t *level_out,
-                             hacc_stream_t stream);
+                             float *vel, double dt, int32_t d, int32_t lmin, int32_t lmax, float skin,
+                             int32_t *level_out, hacc_stream_t stream);
 
 /* Cells per side of the multi-level step's chaining mesh for box->nc = 0:
  * hacc_mesh_cells(L, r_cut (1 + skin)) when that gives at least 3 cells and

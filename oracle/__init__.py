@@ -64,7 +64,7 @@ def lib():
             L.hacc_oracle_diagnostics.restype = None
             L.hacc_oracle_diagnostics.argtypes = [i64, p, p, p, d, d, d, p, d, p]
             L.hacc_oracle_ml_levels.restype = None
-            L.hacc_oracle_ml_levels.argtypes = [i64, p, d, i32, i32, i32, p]
+            L.hacc_oracle_ml_levels.argtypes = [i64, p, d, i32, i32, i32, i32, p]
             L.hacc_oracle_subcycle_ml.restype = None
             L.hacc_oracle_subcycle_ml.argtypes = [i64, p, p, p, d, d, d, p, d, d, i32, p]
             L.hacc_oracle_threads.restype = i32
@@ -204,11 +204,12 @@ def step(pos, vel, L, split_params, dt, n_c, ng=None, sigma=0.8, ns=3):
     return x, v
 
 
-def ml_levels(pos32, L, nc, d, lmax):
-    """Kick counts of Eq. (kicks) from the chaining-mesh densities of the FP32 start positions."""
+def ml_levels(pos32, L, nc, d, lmax, lmin=1):
+    """Kick counts of Eq. (kicks) from the chaining-mesh densities of the FP32 start positions,
+    clamped to [lmin, lmax]."""
     p = np.ascontiguousarray(pos32, dtype=np.float32)
     lev = np.empty(p.shape[0], dtype=np.int32)
-    lib().hacc_oracle_ml_levels(p.shape[0], _ptr(p), float(L), int(nc), int(d), int(lmax), _ptr(lev))
+    lib().hacc_oracle_ml_levels(p.shape[0], _ptr(p), float(L), int(nc), int(d), int(lmin), int(lmax), _ptr(lev))
     return lev
 
 

@@ -402,9 +402,12 @@ void hacc_oracle_diagnostics(int64_t n, const double *x, const double *v, const 
  * Levels: with the chaining mesh of hacc_oracle_wrap_cell on the FP32 start
  * positions, a cell holding count particles has density rho / rho0 =
  * count nc^3 / n; its particles get l = floor(floor(rho/rho0) / d) + 1 kicks
- * (integer arithmetic), capped at lmax.  d <= 0 gives every particle lmax.
+ * (integer arithmetic), capped at lmax and raised to at least lmin (the paper
+ * runs its test with every particle taking at least two sub-cycles and up to two
+ * more levels in the densest regions).  d <= 0 gives every particle lmax.
  * pos32: n x 4 floats (wrapped copy is made internally); level: n ints out. */
-void hacc_oracle_ml_levels(int64_t n, const float *pos32, double L, int nc, int d, int lmax, int32_t *level) {
+void hacc_oracle_ml_levels(int64_t n, const float *pos32, double L, int nc, int d, int lmin, int lmax,
+                           int32_t *level) {
     int64_t ncell = (int64_t)nc * nc * nc;
     float *p = (float *)malloc(sizeof(float) * 4 * (size_t)(n ? n : 1));
     memcpy(p, pos32, sizeof(float) * 4 * (size_t)n);
@@ -419,6 +422,7 @@ void hacc_oracle_ml_levels(int64_t n, const float *pos32, double L, int nc, int 
             l = ratio / d + 1;
             if (l > lmax) l = lmax;
         }
+        if (l < lmin) l = lmin;
         level[i] = (int32_t)l;
     }
     free(count);

@@ -158,7 +158,7 @@ def lib():
                                     p, d, i32, p]),
             "hacc_stats_enable": (st, [p, ctypes.c_int, ctypes.c_int]),
             "hacc_subcycle_ml": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, d, i32, i32,
-                                      ctypes.c_float, p, p]),
+                                      i32, ctypes.c_float, p, p]),
             "hacc_ml_mesh_cells": (i32, [d, ctypes.c_float, ctypes.c_float]),
             "hacc_ci_from_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p, p]),
             "hacc_ci_to_f64": (st, [p, ctypes.POINTER(_Box), ctypes.c_float, i64, p, p, p, p]),
@@ -387,15 +387,15 @@ class Context:
                     "hacc_subcycle")
 
     def subcycle_ml(self, box: Box, split, pos, vel, dt: float, d: int, lmax: int, skin: float = 0.05,
-                    levels=None, stream=None):
-        """One multi-level short-range step (kick counts from cell densities, Eq. (kicks)) on a
-        chaining mesh of ml_mesh_cells(L, r_cut, skin) cells per side."""
+                    levels=None, stream=None, lmin: int = 1):
+        """One multi-level short-range step (kick counts from cell densities, Eq. (kicks), clamped
+        to [lmin, lmax]) on a chaining mesh of ml_mesh_cells(L, r_cut, skin) cells per side."""
         _dev_rows(pos, "pos")
         _dev_rows(vel, "vel")
         sp = _split_of(split)
         self._check(lib().hacc_subcycle_ml(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0],
-                                           _ptr(pos), _ptr(vel), float(dt), int(d), int(lmax), float(skin),
-                                           _ptr(levels), self._stream(stream)), "hacc_subcycle_ml")
+                                           _ptr(pos), _ptr(vel), float(dt), int(d), int(lmin), int(lmax),
+                                           float(skin), _ptr(levels), self._stream(stream)), "hacc_subcycle_ml")
 
     def step(self, box: Box, split, pm: PM, pos, vel, dt: float, n_c: int, stream=None):
         _dev_rows(pos, "pos")

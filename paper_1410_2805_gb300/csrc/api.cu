@@ -866,11 +866,12 @@ cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, 
 }  // namespace
 
 hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, float *pos_m,
-                             float *vel, double dt, int32_t d, int32_t lmax, float skin, int32_t *level_out,
-                             hacc_stream_t stream) {
+                             float *vel, double dt, int32_t d, int32_t lmin, int32_t lmax, float skin,
+                             int32_t *level_out, hacc_stream_t stream) {
     HACC_TRY(enter(ctx));
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     if (lmax < 1 || lmax > kMaxLevels) return set_error(ctx, HACC_EINVAL, "lmax must be in [1, 16]");
+    if (lmin < 1 || lmin > lmax) return set_error(ctx, HACC_EINVAL, "lmin must be in [1, lmax]");
     if (!std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
     if (!(skin >= 0) || !std::isfinite(skin)) return set_error(ctx, HACC_EINVAL, "skin must be finite and >= 0");
     Geometry g;
@@ -918,7 +919,7 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     // kick counts from the cell densities at the start of the step
     HACC_CUDA(bin_build(g, n, pos_in, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
     HACC_CUDA(cudaMemsetAsync(w.present, 0, sizeof(int) * (kMaxLevels + 1), s), "memset");
-    HACC_CUDA(ml_levels(g, n, w.b, d, lmax, lev_s, w.present, s), "kick counts");
+    HACC_CUDA(ml_levels(g, n, w.b, d, lmin, lmax, lev_s, w.present, s), "kick counts");
     if (level_out)
         HACC_CUDA(cudaMemcpyAsync(level_out, lev_s, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "levels out");
     HACC_TRY(rebin(pos_in, true));

@@ -592,10 +592,10 @@ __global__ void __launch_bounds__(kBlock) k_ci_to_f64(int64_t n, const int32_t *
 
 // ---- multi-level stepping ------------------------------------------------
 // Kick count of every particle from its cell's density (Eq. (kicks)):
-// l = floor(floor(count nc^3 / n) / d) + 1, capped at lmax (d <= 0: lmax);
+// l = floor(floor(count nc^3 / n) / d) + 1, clamped to [lmin, lmax] (d <= 0: lmax);
 // present[l] = 1 for the counts that occur.
 __global__ void __launch_bounds__(kBlock) k_levels(int64_t n, int64_t ncell, const int32_t *__restrict__ key,
-                                                    const uint32_t *__restrict__ count, int d, int lmax,
+                                                    const uint32_t *__restrict__ count, int d, int lmin, int lmax,
                                                     int32_t *__restrict__ level, int *__restrict__ present) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int l = 0;   // 0: no particle on this lane
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kBlock) k_levels(int64_t n, int64_t ncell, con
             q = ratio / d + 1;
             if (q > lmax) q = lmax;
         }
-        l = (int)q;
+        l = (int)(q < lmin ? lmin : q);
         level[i] = l;
     }
     // particles per kick count, one atomic per distinct count in the warp
@@ -757,10 +757,10 @@ cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const flo
     return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s);
 }
 
-cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmax, int32_t *level,
+cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmin, int lmax, int32_t *level,
                       int *present, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_levels<<<blocks_for(n), kBlock, 0, s>>>(n, g.ncell, b.key, b.count, d, lmax, level, present);
+    k_levels<<<blocks_for(n), kBlock, 0, s>>>(n, g.ncell, b.key, b.count, d, lmin, lmax, level, present);
     note_launch();
     return cudaGetLastError();
 }

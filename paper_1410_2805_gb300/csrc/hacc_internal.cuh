@@ -219,7 +219,7 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
 // sorted positions with the largest drift from the binned ones; the rebinning
 // gather; and work items of the current binning for the cells that hold a
 // particle kicked now (keys and kick counts in one common order).
-cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmax, int32_t *level,
+cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmin, int lmax, int32_t *level,
                       int *present, cudaStream_t s);
 cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift, const float4 *p0, unsigned *disp,
                           cudaStream_t s);

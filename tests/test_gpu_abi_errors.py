@@ -55,11 +55,15 @@ def test_entry_points_refuse_bad_arguments(env, split_params):
                                                 0, s)),
         ("NULL vel", lambda: lib.hacc_subcycle(h, ctypes.byref(box), ctypes.byref(sp), n, _p(pos), None, 0.01, 2, s)),
         ("lmax = 0", lambda: lib.hacc_subcycle_ml(h, ctypes.byref(box), ctypes.byref(sp), n, _p(pos), _p(vel), 0.01,
-                                                  1, 0, ctypes.c_float(0.05), None, s)),
+                                                  1, 1, 0, ctypes.c_float(0.05), None, s)),
         ("lmax = 17", lambda: lib.hacc_subcycle_ml(h, ctypes.byref(box), ctypes.byref(sp), n, _p(pos), _p(vel), 0.01,
-                                                   1, 17, ctypes.c_float(0.05), None, s)),
+                                                   1, 1, 17, ctypes.c_float(0.05), None, s)),
+        ("lmin = 0", lambda: lib.hacc_subcycle_ml(h, ctypes.byref(box), ctypes.byref(sp), n, _p(pos), _p(vel), 0.01,
+                                                  1, 0, 2, ctypes.c_float(0.05), None, s)),
+        ("lmin > lmax", lambda: lib.hacc_subcycle_ml(h, ctypes.byref(box), ctypes.byref(sp), n, _p(pos), _p(vel),
+                                                     0.01, 1, 3, 2, ctypes.c_float(0.05), None, s)),
         ("dt = nan", lambda: lib.hacc_subcycle_ml(h, ctypes.byref(box), ctypes.byref(sp), n, _p(pos), _p(vel),
-                                                  float("nan"), 1, 2, ctypes.c_float(0.05), None, s)),
+                                                  float("nan"), 1, 1, 2, ctypes.c_float(0.05), None, s)),
         ("variant 4", lambda: lib.hacc_set_variant(h, hacc.FORCE_VARIANTS)),
         ("variant -1", lambda: lib.hacc_set_variant(h, -1)),
         ("stencil 0", lambda: lib.hacc_set_stencil(h, 0)),

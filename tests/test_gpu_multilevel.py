@@ -21,8 +21,10 @@ def env():
     ctx.close()
 
 
-@pytest.mark.parametrize("d,lmax", [(2, 4), (1, 3), (0, 3), (1000, 4)])
-def test_multilevel_step_against_oracle(env, split_params, d, lmax):
+# (d, lmin, lmax); (2, 2, 4) is the paper's test: every particle at least two
+# kicks, up to two more levels in the dense cells
+@pytest.mark.parametrize("d,lmin,lmax", [(2, 1, 4), (1, 1, 3), (0, 1, 3), (1000, 1, 4), (2, 2, 4), (1000, 3, 4)])
+def test_multilevel_step_against_oracle(env, split_params, d, lmin, lmax):
     torch, hacc, ctx = env
     L = 20.0
     n = 6000
@@ -31,13 +33,14 @@ def test_multilevel_step_against_oracle(env, split_params, d, lmax):
     sp = dict(split_params, eps=float(np.float32(0.01)))
     sp["r_cut"] = float(np.float32(sp["r_cut"]))
     nc = hacc.ml_mesh_cells(L, sp["r_cut"], 0.05)
-    lev_o = oracle.ml_levels(pos, L, nc, d, lmax)
+    lev_o = oracle.ml_levels(pos, L, nc, d, lmax, lmin=lmin)
     xo, vo = oracle.subcycle_ml(pos, vel, L, sp, 0.1, lmax, lev_o)
     p, v = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
     lev = torch.zeros(n, dtype=torch.int32, device="cuda")
-    ctx.subcycle_ml(hacc.Box(L=L), sp, p, v, 0.1, d, lmax, levels=lev)
+    ctx.subcycle_ml(hacc.Box(L=L), sp, p, v, 0.1, d, lmax, levels=lev, lmin=lmin)
     ctx.sync()
     assert np.array_equal(lev.cpu().numpy(), lev_o)          # integer decision, bit-exact
+    assert lev_o.min() >= lmin
     if d not in (0, 1000):
         assert len(np.unique(lev_o)) > 1
     x = p.cpu().numpy().astype(np.float64)

@@ -26,7 +26,11 @@ def test_levels_follow_cell_density(split_params):
         cnt = np.bincount(cell, minlength=nc ** 3)
         ratio = (cnt[cell].astype(np.int64) * nc ** 3) // len(pos)
         assert np.array_equal(lev, np.minimum(ratio // d + 1, lmax))
+        for lmin in (2, lmax):
+            lev = oracle.ml_levels(pos, L, nc, d, lmax, lmin=lmin)
+            assert np.array_equal(lev, np.clip(ratio // d + 1, lmin, lmax))
     assert np.all(oracle.ml_levels(pos, L, nc, 0, 3) == 3)
+    assert np.all(oracle.ml_levels(pos, L, nc, 0, 3, lmin=2) == 3)
 
 
 def test_single_kick_is_one_sks_step(split_params):
