@@ -330,7 +330,7 @@ hacc_status hacc_server_tick(hacc_server *sv, hacc_stream_t stream, hacc_server_
  * HACC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  The caller owns pos_m
  * (n rows, not modified) and acc (n rows, receives (ax, ay, az, 0)).
- *   - Limit: about 48 bytes per particle plus 32 bytes per chaining-mesh cell
+ *   - Limit: about 49 bytes per particle plus 32 bytes per chaining-mesh cell
  *     must fit in the array (e.g. 262144 particles with up to 100000 cells);
  *     larger problems return HACC_ENOMEM before anything is enqueued.
  *   - Works on the current CUDA device.  Its first call on a device looks up
@@ -371,6 +371,28 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
  * served, multi-level, cell/offset and allocation-free paths always use 27
  * cells.  HACC_EINVAL for other values. */
 hacc_status hacc_set_stencil(hacc_ctx *ctx, int32_t cells_per_rcut);
+
+/* Work items of the pair kernel in the single-box force paths (hacc_sr_force,
+ * hacc_subcycle, hacc_step, hacc_diagnostics, hacc_tune and their host forms),
+ * the batched and served paths and the multi-level step (whose small events
+ * split every cell into smaller items still); the cell/offset paths and
+ * hacc_sr_force_noalloc use cap = 0.  A work item is a set of particles of
+ * one chaining-mesh cell that one warp runs against the cell's neighbours; a
+ * neighbour particle farther than r_cut from the item's bounding box is
+ * skipped, so items that cover a small part of their cell evaluate fewer
+ * pairs, but every item stages all of its neighbours.
+ * cap in [16, 160]: within each cell of up to 512 particles the particles are
+ * ordered by their 4x4x4 sub-cell (Morton order, ties by input row; larger
+ * cells by input row alone), and a cell of m <= split_max particles becomes
+ * ceil(m / cap) items of consecutive particles of near-equal size; a denser
+ * cell becomes ceil(m / 160) items (split_max = 0: no such limit).
+ * cap = 0: input row order within cells and items of up to 160 particles.
+ * cap = -1 (the default): 48 for calls of up to 2^22 particles (short
+ * launches, whose tail the longest items of dense cells set) and 0 above.
+ * The forces are sums over the same pairs for every setting (the summation
+ * order differs, so results differ by FP32 rounding).  HACC_EINVAL for a cap
+ * outside {-1, 0} and [16, 160] or split_max < 0. */
+hacc_status hacc_set_item_cap(hacc_ctx *ctx, int32_t cap, int32_t split_max);
 
 /* Select the pair-kernel variant by hand (0 <= variant < HACC_FORCE_VARIANTS). */
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant);

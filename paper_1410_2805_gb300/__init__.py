@@ -167,6 +167,7 @@ def lib():
             "hacc_tune": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, i32,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
             "hacc_set_variant": (st, [p, i32]),
+            "hacc_set_item_cap": (st, [p, i32, i32]),
             "hacc_set_stencil": (st, [p, i32]),
             "hacc_batch_subcycle": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, i32, i32,
                                          p]),
@@ -326,6 +327,13 @@ class Context:
 
     def set_variant(self, variant: int):
         self._check(lib().hacc_set_variant(self._h, int(variant)), "hacc_set_variant")
+
+    def set_item_cap(self, cap: int, split_max: int = 0):
+        """Particles per force work item at most: 16..160 with the cell's particles in sub-cell
+        order (cells above split_max particles keep items of up to 160, 0 = no such limit),
+        0 for input-row order and items of up to 160, or -1 (default): 48 for calls of up to
+        2^22 particles, else 0."""
+        self._check(lib().hacc_set_item_cap(self._h, int(cap), int(split_max)), "hacc_set_item_cap")
 
     def set_stencil(self, cells_per_rcut: int):
         """1: cells >= r_cut, 27-cell search (default); 2: cells >= r_cut/2, 125-cell search."""

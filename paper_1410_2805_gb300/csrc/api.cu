@@ -390,6 +390,16 @@ hacc_status hacc_set_stencil(hacc_ctx *ctx, int32_t cells_per_rcut) {
     return HACC_OK;
 }
 
+hacc_status hacc_set_item_cap(hacc_ctx *ctx, int32_t cap, int32_t split_max) {
+    HACC_TRY(enter(ctx));
+    if (cap != -1 && cap != 0 && (cap < kItemCapMin || cap > kItemMax))
+        return set_error(ctx, HACC_EINVAL, "item cap must be -1, 0 or in [16, 160]");
+    if (split_max < 0) return set_error(ctx, HACC_EINVAL, "split_max must be >= 0");
+    ctx->item_cap = cap;
+    ctx->split_max = split_max ? split_max : kDefaultSplitMax;
+    return HACC_OK;
+}
+
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant) {
     HACC_TRY(enter(ctx));
     if (variant < 0 || variant >= kForceVariants) return set_error(ctx, HACC_EINVAL, "variant out of range");
@@ -411,7 +421,8 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Work w;
     HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
-    HACC_CUDA(bin_build(g, n, reinterpret_cast<const float4 *>(pos_m), nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s),
+    HACC_CUDA(bin_build(g, n, reinterpret_cast<const float4 *>(pos_m), nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s,
+                        item_cap_for(ctx, n), ctx->split_max),
               "binning");
     HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
     cudaEvent_t e0, e1;
@@ -498,7 +509,7 @@ hacc_status hacc_bin(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n,
     // scratch: everything of BinBuffers except the caller-owned outputs
     auto carve = [&](char *base, BinBuffers *b) {
         Carver c(base);
-        carve_bin(c, n, g.ncell, b);
+        carve_bin(c, n, g.ncell, b, false);
         return c.off + 256;
     };
     BinBuffers b;
@@ -526,7 +537,9 @@ hacc_status hacc_sr_force(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
     Work w;
     HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
     const float4 *src = reinterpret_cast<const float4 *>(pos_m);
-    HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s), "binning");
+    HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s, item_cap_for(ctx, n),
+                        ctx->split_max),
+              "binning");
     HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
     unsigned long long *within = nullptr;
     if (pair_counts) {
@@ -566,7 +579,7 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
         // stream h/2 (first sub-cycle only; later ones were fused into the
         // previous kick) + wrap + rebin
         HACC_CUDA(bin_build(g, n, first ? pos_in : w.P, first ? vel_in : nullptr, h2, w.P, w.b, ctx->d_flags, true,
-                            s),
+                            s, item_cap_for(ctx, n), ctx->split_max),
                   "binning");
         HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, first ? vel_in : w.V, w.Vs, first ? nullptr : w.ID, w.IDs,
                                 s),
@@ -701,6 +714,12 @@ struct MlEvent {
 
 // Events (2k+1)/(2l) dt, k < l, over the kick counts l that occur, in time
 // order with duplicates merged (exact reduced fractions).
+// Dense cells keep large items at events that use the context's own item
+// cap; smaller events split every cell (more warps for the launch).
+int ml_split_max(const hacc_ctx *ctx, int icap, int cap) {
+    return (icap && cap >= icap) ? ctx->split_max : INT32_MAX;
+}
+
 std::vector<MlEvent> ml_schedule(const int *present, int lmax, double dt) {
     std::vector<std::pair<int64_t, int64_t>> ev;
     for (int l = 1; l <= lmax; ++l) {
@@ -832,7 +851,8 @@ cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, 
             cudaSuccess)
             break;
         const int64_t b0 = ctx->launches;
-        cudaError_t eb = bin_build(g, m.n, m.Ps, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, cs2);
+        cudaError_t eb = bin_build(g, m.n, m.Ps, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, cs2,
+                                   item_cap_for(ctx, m.n), ctx->split_max);
         if (eb == cudaSuccess)
             eb = gather_ml(m.n, w.b.perm, w.P, m.Ps, m.Ref, m.Vs, m.Vt, m.lev_s, m.lev_t, m.id_s, m.id_t, w.b.key,
                            w.Ks, cs2);
@@ -843,7 +863,9 @@ cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, 
         e = cudaStreamEndCapture(cs2, &bg);
         if (eb != cudaSuccess) e = eb;
         if (e != cudaSuccess) break;
-        if ((e = items_active(g, m.n, w.Ks, m.lev_s, ev[k].kt, w.cell_active, w.b, caps[k], cs)) != cudaSuccess) break;
+        if ((e = items_active(g, m.n, w.Ks, m.lev_s, ev[k].kt, w.cell_active, w.b, caps[k],
+                              ml_split_max(ctx, item_cap_for(ctx, m.n), caps[k]), cs)) != cudaSuccess)
+            break;
         if ((e = sr_force_launch(g, fc, ml_force(ctx, w, m, ev[k].kt), ctx->num_sms, cs)) != cudaSuccess) break;
         ctx->force_launches++;
     }
@@ -904,9 +926,12 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     const double half = 0.5 * (g.Ld / g.nc - (double)split->r_cut);
     float4 *Ps = w.Ps, *Vs = w.Vs, *Vt = w.V2, *Ref = w.R;
     int32_t *lev_s = w.IDs, *lev_t = w.ID, *id_s = w.I1, *id_t = w.I2;   // kick counts start in lev_s, input order
+    const int icap = item_cap_for(ctx, n);
     // bin src (wrapped into w.P), then gather every array into its other buffer and swap the two
     auto rebin = [&](const float4 *src, bool first) -> hacc_status {
-        if (!first) HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
+        if (!first)
+            HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s, icap, ctx->split_max),
+                      "binning");
         HACC_CUDA(gather_ml(n, w.b.perm, w.P, Ps, Ref, first ? V : Vs, Vt, lev_s, lev_t, first ? nullptr : id_s, id_t,
                             w.b.key, w.Ks, s),
                   "gather");
@@ -917,7 +942,8 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         return HACC_OK;
     };
     // kick counts from the cell densities at the start of the step
-    HACC_CUDA(bin_build(g, n, pos_in, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s), "binning");
+    HACC_CUDA(bin_build(g, n, pos_in, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s, icap, ctx->split_max),
+              "binning");
     HACC_CUDA(cudaMemsetAsync(w.present, 0, sizeof(int) * (kMaxLevels + 1), s), "memset");
     HACC_CUDA(ml_levels(g, n, w.b, d, lmin, lmax, lev_s, w.present, s), "kick counts");
     if (level_out)
@@ -937,6 +963,7 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
             if (ev[k].kt.h[l] != 0.0f) kicked += present[l];
         const int64_t per_item = kicked / ((int64_t)ctx->num_sms * 64);
         caps[k] = (int)std::max<int64_t>(kItemMin, std::min<int64_t>(kItemMax, per_item / 32 * 32));
+        if (icap) caps[k] = std::min(caps[k], icap);
     }
 
     // Without timing or counting the event loop runs as one cached CUDA graph
@@ -956,6 +983,8 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
             for (int l = 0; l <= kMaxLevels; ++l) key = mixk(key, fbits(ev[k].kt.h[l]));
             key = mixk(key, (uint64_t)caps[k]);
         }
+        key = mixk(key, (uint64_t)ctx->item_cap);
+        key = mixk(key, (uint64_t)ctx->split_max);
         uint64_t db;
         std::memcpy(&db, &dt, 8);
         key = mixk(key, db);
@@ -1005,7 +1034,9 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
             HACC_TRY(rebin(Ps, false));
             ctx->ml_rebins++;
         }
-        HACC_CUDA(items_active(g, n, w.Ks, lev_s, e.kt, w.cell_active, w.b, caps[k], s), "work items");
+        HACC_CUDA(items_active(g, n, w.Ks, lev_s, e.kt, w.cell_active, w.b, caps[k], ml_split_max(ctx, icap, caps[k]),
+                               s),
+                  "work items");
         const MlLoop m{n, Ps, Vs, Vt, Ref, pos_in, V, lev_s, lev_t, id_s, id_t, disp_bits, half_lim};
         HACC_TRY(launch_force(ctx, g, fc, ml_force(ctx, w, m, e.kt), true, s));
     }
@@ -1033,7 +1064,9 @@ hacc_status hacc_diagnostics(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
         return HACC_OK;
     }
     const float4 *src = reinterpret_cast<const float4 *>(pos_m);
-    HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s), "binning");
+    HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s, item_cap_for(ctx, n),
+                        ctx->split_max),
+              "binning");
     HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, reinterpret_cast<const float4 *>(vel), w.Vs, nullptr, nullptr, s),
               "gather");
     HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModePotential, nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr,

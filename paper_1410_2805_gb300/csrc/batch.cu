@@ -111,7 +111,7 @@ hacc_status ensure_staging(hacc_ctx *ctx, size_t bytes) {
 hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const BoxDev *tab, float4 *pos_pool,
                      float4 *vel_pool, const BatchWork &w, cudaStream_t s) {
     HACC_CUDA_RETURN(bin_build_batch(pl.nbox, tab, pl.n_total, pl.ncell_total, pos_pool, vel_pool, w.P, w.ID, w.b,
-                                     ctx->d_flags, s),
+                                     ctx->d_flags, s, item_cap_for(ctx, pl.n_total), ctx->split_max),
                      "batched binning");
     HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.b.perm, w.P, w.Ps, nullptr, nullptr, w.ID, w.IDs, s), "gather");
     HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.IDs, vel_pool, w.Vs, nullptr, nullptr, nullptr, nullptr, s),
@@ -290,6 +290,8 @@ extern "C" hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *spli
     key = mix(key, (uint64_t)(uintptr_t)ctx->scratch.base);
     key = mix(key, (uint64_t)ctx->variant);
     key = mix(key, (uint64_t)ctx->counting);
+    key = mix(key, (uint64_t)ctx->item_cap);
+    key = mix(key, (uint64_t)ctx->split_max);
     key = mix(key, (uint64_t)(uintptr_t)s);
     if (!ctx->graph_exec || ctx->graph_key != key) {
         if (ctx->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->graph_exec));

@@ -4,14 +4,17 @@
 //
 // Pipeline (all HBM-bound, one pass each):
 //   k_key     wrap (after an optional drift), exact cell id, per-cell count
-//             and arrival slot (atomic)                    read 16-32 B, write 24 B
+//             and arrival slot (atomic), [sub-cell]        read 16-32 B, write 24-25 B
 //   scan      exclusive scan of (count, work-item count) packed in 64 bits
-//   k_place   perm_tmp[start[c] + slot] = i                 read 12 B, write 4 B
-//   k_order   within each cell, sort perm by input row (stable order)
+//   k_place   perm_tmp[start[c] + slot] = i, [its sub-cell] read 12-13 B, write 4-5 B
+//   k_order   within each cell, sort perm by input row (stable order) or by
+//             (sub-cell, input row)
 //   k_items   cell starts and force work items
 //   gather    sorted copies of positions / velocities / ids
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "hacc_internal.cuh"
 
@@ -37,11 +40,23 @@ __device__ __forceinline__ int cell1(float x, float inv_w, double Ld, int nc) {
     return k;
 }
 
+// Morton index of the 4x4x4 sub-cell of a particle from its in-cell
+// fractions (z, y, x bits of the halves, then of the quarters), used only to
+// order particles within a cell.
+__device__ __forceinline__ uint8_t sub_cell(float fx, float fy, float fz) {
+    const int qx = min(max((int)(fx * 4.0f), 0), 3);
+    const int qy = min(max((int)(fy * 4.0f), 0), 3);
+    const int qz = min(max((int)(fz * 4.0f), 0), 3);
+    return (uint8_t)(((qz >> 1) << 5) | ((qy >> 1) << 4) | ((qx >> 1) << 3) | ((qz & 1) << 2) | ((qy & 1) << 1) |
+                     (qx & 1));
+}
+
 __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restrict__ src,
                                                  const float4 *__restrict__ vel, float drift,
                                                  float4 *dst, float Lf, float inv_w, double Ld, int nc,
                                                  int32_t *__restrict__ key, int32_t *__restrict__ rank,
-                                                 uint32_t *__restrict__ count, int *flags, int *mass_flag) {
+                                                 uint32_t *__restrict__ count, int *flags, int *mass_flag,
+                                                 uint8_t *__restrict__ sub) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = src[i];
@@ -60,6 +75,7 @@ __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restr
     int32_t c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
     dst[i] = p;
     key[i] = c;
+    if (sub) sub[i] = sub_cell(p.x * inv_w - (float)cx, p.y * inv_w - (float)cy, p.z * inv_w - (float)cz);
     rank[i] = (int32_t)atomicAdd(&count[c], 1u);
 }
 
@@ -83,14 +99,22 @@ __device__ __forceinline__ int item_shape(uint32_t n) {
     return 5;
 }
 
-// Work items of a cell of cnt particles, at most cap (kItemMin..kItemMax) per item.
-__device__ __forceinline__ uint32_t items_of(uint32_t cnt, uint32_t cap) {
+// How cells are cut into work items: a cell of cnt particles becomes
+// ceil(cnt / cap) items, or ceil(cnt / kItemMax) when cnt > split_max (dense
+// cells: their particles crowd into a few sub-cells, so smaller items would
+// not shrink the bounds, only repeat the staging of the neighbours).
+struct ItemRule {
+    uint32_t cap, split_max;
+};
+
+__device__ __forceinline__ uint32_t items_of(uint32_t cnt, ItemRule r) {
+    const uint32_t cap = cnt > r.split_max ? (uint32_t)kItemMax : r.cap;
     return cnt == 0 ? 0u : (cnt <= cap ? 1u : (cnt + cap - 1) / cap);
 }
 
 __global__ void __launch_bounds__(kBlock) k_pack(int64_t ncell, const uint32_t *__restrict__ count,
                                                   const int *__restrict__ cell_active,
-                                                  unsigned long long *__restrict__ packed, uint32_t cap) {
+                                                  unsigned long long *__restrict__ packed, ItemRule cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     uint32_t k = count[c];
@@ -182,58 +206,129 @@ cudaError_t scan_exclusive(unsigned long long *data, int64_t len, unsigned long 
 __global__ void __launch_bounds__(kBlock) k_place(int64_t n, const int32_t *__restrict__ key,
                                                    const int32_t *__restrict__ rank,
                                                    const unsigned long long *__restrict__ packed,
-                                                   int32_t *__restrict__ perm_tmp) {
+                                                   int32_t *__restrict__ perm_tmp, const uint8_t *__restrict__ sub,
+                                                   unsigned long long *__restrict__ order_tmp) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t c = key[i];
     uint32_t start = (uint32_t)(packed[c] & 0xffffffffull);
-    perm_tmp[start + (uint32_t)rank[i]] = (int32_t)i;
+    const uint32_t at = start + (uint32_t)rank[i];
+    // with sub-cells the row and its sub-cell go out as one 8-byte word (one
+    // scattered write, as for the row alone)
+    if (sub) order_tmp[at] = ((unsigned long long)sub[i] << 32) | (uint32_t)i;
+    else perm_tmp[at] = (int32_t)i;
 }
 
 // One warp per cell: the arrival order from the atomics is arbitrary, so each
-// element's final slot is the number of smaller input rows in its cell (the
-// rows are distinct), which gives ascending input row within the cell.
-// Cells of more than kBigCell particles go to a list sorted by k_order_big.
+// element's final slot is the number of smaller keys in its cell.  The key is
+// the input row (distinct), which gives ascending input row within the cell,
+// or with SUB the pair (Morton sub-cell, input row), which groups the cell's
+// particles by sub-cell; when the cell's rows span less than 2^26 the pair is
+// ranked as one 32-bit key (sub-cell << 26 | row - smallest row).  Cells of
+// more than kBigCell particles go to a list sorted by input row by
+// k_order_big.
 constexpr uint32_t kBigCell = 512;
 
+struct RowOf32 {
+    __device__ int32_t operator()(int32_t k) const { return k; }
+};
+struct RowOf64 {
+    __device__ int32_t operator()(unsigned long long k) const { return (int32_t)(uint32_t)k; }
+};
+struct RowOfPacked {
+    uint32_t base;
+    __device__ int32_t operator()(uint32_t k) const { return (int32_t)((k & 0x3ffffffu) + base); }
+};
+
+// Rank of each lane's key among the cell's cnt <= 32 keys (lanes >= cnt hold
+// the largest key); out[rank] = its row.
+template <class Key, class Row>
+__device__ __forceinline__ void rank_warp(Key v, int cnt, int lane, int32_t *out, Row row) {
+    int r = 0;
+    for (int q = 0; q < cnt; ++q) {
+        const Key u = __shfl_sync(0xffffffffu, v, q);
+        r += (u < v);
+    }
+    if (lane < cnt) out[r] = row(v);
+}
+
+// The same for the cnt keys in the warp's shared array w.
+template <class Key, class Row>
+__device__ __forceinline__ void rank_shared(const Key *w, uint32_t cnt, int lane, int32_t *out, Row row) {
+    __syncwarp();
+    for (uint32_t e = lane; e < cnt; e += 32) {
+        const Key v = w[e];
+        uint32_t r = 0;
+        for (uint32_t q = 0; q < cnt; ++q) r += (w[q] < v);
+        out[r] = row(v);
+    }
+}
+
+template <bool SUB>
 __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t *__restrict__ count,
                                                    const unsigned long long *__restrict__ packed,
-                                                   const int32_t *__restrict__ perm_tmp,
+                                                   int32_t *__restrict__ perm_tmp,
                                                    int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
-                                                   int *__restrict__ big_count) {
+                                                   int *__restrict__ big_count,
+                                                   const unsigned long long *__restrict__ order_tmp) {
     int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (c >= ncell) return;
     uint32_t cnt = count[c];
     if (cnt == 0) return;
+    uint32_t s = (uint32_t)(packed[c] & 0xffffffffull);
     if (cnt > kBigCell) {
+        // big cells are ordered by row alone, from perm_tmp
+        if (SUB)
+            for (uint32_t e = lane; e < cnt; e += 32) perm_tmp[s + e] = (int32_t)(uint32_t)order_tmp[s + e];
         if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)c;
         return;
     }
-    uint32_t s = (uint32_t)(packed[c] & 0xffffffffull);
-    const int32_t *seg = perm_tmp + s;
-    if (cnt <= 32) {
-        int32_t v = lane < (int)cnt ? seg[lane] : 0x7fffffff;
-        int r = 0;
-        for (int q = 0; q < (int)cnt; ++q) {
-            int32_t u = __shfl_sync(0xffffffffu, v, q);
-            r += (u < v);
+    int32_t *out = perm + s;
+    if (!SUB) {
+        const int32_t *seg = perm_tmp + s;
+        if (cnt <= 32) {
+            rank_warp(lane < (int)cnt ? seg[lane] : 0x7fffffff, (int)cnt, lane, out, RowOf32{});
+            return;
         }
-        if (lane < (int)cnt) perm[s + r] = v;
+        // larger cells: the keys go to shared memory once, then every lane
+        // ranks its keys against them (broadcast reads)
+        __shared__ int32_t ids[kBlock / 32][kBigCell];
+        int32_t *w = ids[threadIdx.x >> 5];
+        for (uint32_t e = lane; e < cnt; e += 32) w[e] = seg[e];
+        rank_shared(w, cnt, lane, out, RowOf32{});
         return;
     }
-    // larger cells: the ids go to shared memory once, then every lane ranks
-    // its ids against them (broadcast reads)
-    __shared__ int32_t ids[kBlock / 32][kBigCell];
-    int32_t *w = ids[threadIdx.x >> 5];
-    for (uint32_t e = lane; e < cnt; e += 32) w[e] = seg[e];
-    __syncwarp();
+    const unsigned long long *seg = order_tmp + s;
+    uint32_t lo = 0xffffffffu, hi = 0u;
     for (uint32_t e = lane; e < cnt; e += 32) {
-        const int32_t v = w[e];
-        uint32_t r = 0;
-        for (uint32_t q = 0; q < cnt; ++q) r += (w[q] < v);
-        perm[s + r] = v;
+        const uint32_t r = (uint32_t)seg[e];
+        lo = min(lo, r);
+        hi = max(hi, r);
     }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    __shared__ unsigned long long keys[kBlock / 32][kBigCell];
+    unsigned long long *w = keys[threadIdx.x >> 5];
+    if (hi - lo < (1u << 26)) {
+        const RowOfPacked row{lo};
+        if (cnt <= 32) {
+            uint32_t v = 0xffffffffu;
+            if (lane < (int)cnt) v = ((uint32_t)(seg[lane] >> 32) << 26) | ((uint32_t)seg[lane] - lo);
+            rank_warp(v, (int)cnt, lane, out, row);
+            return;
+        }
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(w);
+        for (uint32_t e = lane; e < cnt; e += 32) w32[e] = ((uint32_t)(seg[e] >> 32) << 26) | ((uint32_t)seg[e] - lo);
+        rank_shared(w32, cnt, lane, out, row);
+        return;
+    }
+    if (cnt <= 32) {
+        rank_warp(lane < (int)cnt ? seg[lane] : ~0ull, (int)cnt, lane, out, RowOf64{});
+        return;
+    }
+    for (uint32_t e = lane; e < cnt; e += 32) w[e] = seg[e];
+    rank_shared(w, cnt, lane, out, RowOf64{});
 }
 
 // Big cells, one block per cell (grid-stride over the list): sort chunks of
@@ -312,7 +407,7 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
                                                    int32_t *__restrict__ cell_start, int4 *__restrict__ items,
                                                    int32_t *__restrict__ n_items, int make_items,
                                                    const BoxDev *__restrict__ boxes, int nbox,
-                                                   const int *__restrict__ cell_active, uint32_t cap) {
+                                                   const int *__restrict__ cell_active, ItemRule cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) {
         cell_start[ncell] = (int32_t)n;
@@ -340,11 +435,11 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
         }
         box = lo;
     }
+    // m near-equal runs: run q is [cnt q / m, cnt (q+1) / m)
     uint32_t m = items_of(cnt, cap);
     for (uint32_t q = 0; q < m; ++q) {
-        uint32_t ni = cnt - q * cap;
-        ni = ni > cap ? cap : ni;
-        items[it + q] = make_int4((int)c, (int)(s + q * cap), (int)ni, (box << 8) | item_shape(ni));
+        const uint32_t a = (uint32_t)((uint64_t)cnt * q / m), e = (uint32_t)((uint64_t)cnt * (q + 1) / m);
+        items[it + q] = make_int4((int)c, (int)(s + a), (int)(e - a), (box << 8) | item_shape(e - a));
     }
 }
 
@@ -354,7 +449,7 @@ __global__ void __launch_bounds__(kBlock) k_bkey(int64_t n_total, int nbox, cons
                                                   const float4 *__restrict__ vel_pool, float4 *__restrict__ dst,
                                                   int32_t *__restrict__ id, int32_t *__restrict__ key,
                                                   int32_t *__restrict__ rank, uint32_t *__restrict__ count, int *flags,
-                                                  int *mass_flag) {
+                                                  int *mass_flag, uint8_t *__restrict__ sub) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_total) return;
     int lo = 0, hi = nbox - 1;
@@ -383,6 +478,7 @@ __global__ void __launch_bounds__(kBlock) k_bkey(int64_t n_total, int nbox, cons
     dst[t] = p;
     id[t] = (int32_t)row;
     key[t] = c;
+    if (sub) sub[t] = sub_cell(p.x * bx.inv_w - (float)cx, p.y * bx.inv_w - (float)cy, p.z * bx.inv_w - (float)cz);
     rank[t] = (int32_t)atomicAdd(&count[c], 1u);
 }
 
@@ -693,9 +789,9 @@ size_t scan_tmp_elems(int64_t len) {
     return total + 1;
 }
 
-int64_t max_items(int64_t n, int64_t ncell) { return ncell + n / kItemMin + 1; }
+int64_t max_items(int64_t n, int64_t ncell) { return ncell + n / kItemCapMin + 1; }
 
-void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
+void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_order) {
     b->key = c.take<int32_t>(n);
     b->rank = c.take<int32_t>(n);
     b->count = c.take<uint32_t>(ncell);
@@ -710,24 +806,36 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b) {
     b->mass_flag = c.take<int>(1);
     b->big_list = c.take<int32_t>(n / (kBigCell + 1) + 1);
     b->big_count = c.take<int>(1);
+    b->sub = sub_order ? c.take<uint8_t>(n) : nullptr;
+    b->order_tmp = sub_order ? c.take<unsigned long long>(n) : nullptr;
 }
 
 namespace {
+ItemRule item_rule(int item_cap, int split_max) {
+    if (!item_cap) return ItemRule{(uint32_t)kItemMax, 0xffffffffu};
+    return ItemRule{(uint32_t)item_cap, (uint32_t)split_max};
+}
+
 // Counting sort by key and work items, shared by the single-box and batched passes.
 cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_items, const BoxDev *boxes, int nbox,
-                     cudaStream_t s, const int *cell_active = nullptr) {
+                     cudaStream_t s, const int *cell_active = nullptr, ItemRule cap = {kItemMax, 0xffffffffu},
+                     const uint8_t *sub = nullptr) {
     cudaError_t e;
-    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, cell_active, b.packed, (uint32_t)kItemMax);
+    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, cell_active, b.packed, cap);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(b.packed, ncell, b.scan_tmp, s)) != cudaSuccess) return e;
     if (n > 0) {
-        k_place<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, b.rank, b.packed, b.perm_tmp);
+        k_place<<<blocks_for(n), kBlock, 0, s>>>(n, b.key, b.rank, b.packed, b.perm_tmp, sub, b.order_tmp);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(b.big_count, 0, sizeof(int), s)) != cudaSuccess) return e;
-        k_order<<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list,
-                                                          b.big_count);
+        if (sub)
+            k_order<true><<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm,
+                                                                    b.big_list, b.big_count, b.order_tmp);
+        else
+            k_order<false><<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm,
+                                                                     b.big_list, b.big_count, nullptr);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (n > (int64_t)kBigCell) {
@@ -737,24 +845,28 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
         }
     }
     k_items<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items,
-                                                 make_items ? 1 : 0, boxes, nbox, cell_active, (uint32_t)kItemMax);
+                                                 make_items ? 1 : 0, boxes, nbox, cell_active, cap);
     note_launch();
     return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
-                      float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s) {
+                      float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s,
+                      int item_cap, int split_max) {
+    if (item_cap != 0 && (item_cap < kItemCapMin || item_cap > kItemMax)) return cudaErrorInvalidValue;
+    if (split_max < 1 || (item_cap && !b.sub)) return cudaErrorInvalidValue;
+    uint8_t *sub = item_cap ? b.sub : nullptr;
     cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
     if (n > 0) {
         k_key<<<blocks_for(n), kBlock, 0, s>>>(n, src, vel, drift, dst, g.Lf, g.inv_w, g.Ld, g.nc, b.key,
-                                               b.rank, b.count, d_flags, b.mass_flag);
+                                               b.rank, b.count, d_flags, b.mass_flag, sub);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s);
+    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s, nullptr, item_rule(item_cap, split_max), sub);
 }
 
 cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmin, int lmax, int32_t *level,
@@ -791,8 +903,9 @@ cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift
 
 // Work items of the current binning, only for cells marked active.
 cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
-                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, cudaStream_t s) {
-    if (cap < kItemMin || cap > kItemMax) return cudaErrorInvalidValue;
+                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, int split_max,
+                         cudaStream_t s) {
+    if (cap < kItemCapMin || cap > kItemMax || split_max < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(cell_active, 0, sizeof(int) * g.ncell, s);
     if (e != cudaSuccess) return e;
     if (n > 0) {
@@ -800,12 +913,13 @@ cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_pack<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, b.count, cell_active, b.packed, (uint32_t)cap);
+    const ItemRule rule{(uint32_t)cap, (uint32_t)split_max};
+    k_pack<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, b.count, cell_active, b.packed, rule);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(b.packed, g.ncell, b.scan_tmp, s)) != cudaSuccess) return e;
     k_items<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items, 1,
-                                                   nullptr, 1, cell_active, (uint32_t)cap);
+                                                   nullptr, 1, cell_active, rule);
     note_launch();
     return cudaGetLastError();
 }
@@ -813,17 +927,20 @@ cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const
 
 cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int64_t ncell_total,
                             const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
-                            const BinBuffers &b, int *d_flags, cudaStream_t s) {
+                            const BinBuffers &b, int *d_flags, cudaStream_t s, int item_cap, int split_max) {
+    if (item_cap != 0 && (item_cap < kItemCapMin || item_cap > kItemMax)) return cudaErrorInvalidValue;
+    if (split_max < 1 || (item_cap && !b.sub)) return cudaErrorInvalidValue;
+    uint8_t *sub = item_cap ? b.sub : nullptr;
     cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * ncell_total, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
     if (n_total > 0) {
         k_bkey<<<blocks_for(n_total), kBlock, 0, s>>>(n_total, nbox, boxes, pos_pool, vel_pool, dst, id, b.key,
-                                                      b.rank, b.count, d_flags, b.mass_flag);
+                                                      b.rank, b.count, d_flags, b.mass_flag, sub);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s);
+    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s, nullptr, item_rule(item_cap, split_max), sub);
 }
 
 cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,

@@ -19,10 +19,14 @@ enum DeviceFlag : int {
 };
 
 // Chunking of a chaining-mesh cell into force work items: a cell of n
-// particles is one item when n <= 160, else ceil(n/160) items of up to 160
-// particles; each item is processed by one warp (see item_shape in bin.cu).
+// particles is one item when n <= cap, else ceil(n/cap) items of near-equal
+// size; each item is processed by one warp (see item_shape in bin.cu).
 constexpr int kItemMax = 160;   // particles per work item at most (5 per lane)
-constexpr int kItemMin = 32;    // smallest item cap (smaller launches split cells finer)
+constexpr int kItemMin = 32;    // smallest per-event item cap of the multi-level step
+constexpr int kItemCapMin = 16; // smallest item cap of any path (sizes the item arrays)
+constexpr int kDefaultItemCap = 48;  // item cap of the automatic choice for small calls
+constexpr int64_t kAutoItemCapMaxN = (int64_t)1 << 22;  // largest call that the automatic choice splits
+constexpr int kDefaultSplitMax = INT32_MAX;  // cells above this keep items of up to kItemMax
 
 struct Scratch {
     char *base = nullptr;
@@ -51,6 +55,8 @@ struct hacc_ctx {
     int64_t ml_rebins = 0;
     int variant = 0;                          // pair-kernel variant (hacc_tune)
     int stencil = 1;                          // single-box force paths: 1 (27 cells) or 2 (125 cells of half width)
+    int item_cap = -1;                        // work-item cap of the force paths (0: cell-wide items, -1: auto)
+    int split_max = hacc::kDefaultSplitMax;   // cells above this many particles keep items of up to kItemMax
     double force_ms = 0.0;
     unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -73,6 +79,17 @@ struct hacc_ctx {
     void *io_ev[3] = {nullptr, nullptr, nullptr};
     bool ml_graph_off = false;   // set when the device refused the graph once
 };
+
+namespace hacc {
+// Item cap of a force call over n particles (hacc_set_item_cap): the set
+// value, or automatically kDefaultItemCap up to kAutoItemCapMaxN particles
+// (short launches, where the longest items of dense cells set the tail) and
+// cell-wide items above.
+inline int item_cap_for(const hacc_ctx *ctx, int64_t n) {
+    if (ctx->item_cap >= 0) return ctx->item_cap;
+    return n <= kAutoItemCapMaxN ? kDefaultItemCap : 0;
+}
+}  // namespace hacc
 
 namespace hacc {
 
@@ -193,26 +210,39 @@ struct BinBuffers {
     int *mass_flag;        // [1] device: nonzero if some mass differs from the first
     int32_t *big_list;     // cells too large for the warp-level ordering
     int *big_count;
+    uint8_t *sub;                  // [n] Morton sub-cell of each input row (item_cap > 0), or null
+    unsigned long long *order_tmp; // [n] (sub-cell << 32 | row) in the slots of perm_tmp, or null
 };
 
 size_t scan_tmp_elems(int64_t len);
 int64_t max_items(int64_t n, int64_t ncell);
-void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b);
+// sub_order = false leaves out the sub-cell arrays (item_cap must then be 0).
+void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_order = true);
 
 // Wrap (optionally after a drift x += d v) src into dst and compute keys,
-// counts, stable permutation, cell starts and force work items.
-// vel may be null (no drift).  dst may equal src.
+// counts, the permutation, cell starts and force work items.  vel may be
+// null (no drift).  dst may equal src.  item_cap = 0: ascending input row
+// within each cell (the stable counting sort) and items of up to kItemMax;
+// item_cap in [kItemCapMin, kItemMax]: within each cell of up to kBigCell
+// particles the rows are ordered by the particle's 4x4x4 sub-cell (Morton
+// order, z bit first; ties by input row), and the work items are runs of at
+// most item_cap particles of that order, so an item covers a compact part of
+// its cell; cells of more than split_max particles get items of up to
+// kItemMax.
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
-                      float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s);
+                      float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s,
+                      int item_cap = 0, int split_max = kDefaultSplitMax);
 
 // Batched binning of nbox boxes (table `boxes` on the device, ascending
 // part_base and cell_base): for every tick-scratch index t the particle at
 // pool row boxes[b].row_off + t - part_base is streamed by pre, wrapped,
 // binned into global cell cell_base + local id; dst[t] = its position,
-// id[t] = its pool row.  Work items carry the box in item.w >> 8.
+// id[t] = its pool row.  Work items carry the box in item.w >> 8.  item_cap
+// as for bin_build (ties in the sub-cell order by scratch index).
 cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int64_t ncell_total,
                             const float4 *pos_pool, const float4 *vel_pool, float4 *dst, int32_t *id,
-                            const BinBuffers &b, int *d_flags, cudaStream_t s);
+                            const BinBuffers &b, int *d_flags, cudaStream_t s, int item_cap = 0,
+                            int split_max = kDefaultSplitMax);
 
 // Multi-level stepping: kick counts from the cell densities of the last
 // binning (keys/counts in b; present[l] += particles with l kicks); in-place stream of
@@ -237,7 +267,8 @@ cudaError_t ml_commit(int64_t n, const float4 *v_from, float4 *v_to, const int32
                       const int32_t *id_from, int32_t *id_to, unsigned *disp_bits, unsigned body_launches,
                       unsigned long long *launches, cudaStream_t s);
 cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
-                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, cudaStream_t s);
+                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, int split_max,
+                         cudaStream_t s);
 
 // Precision variant: positions as (cell id, FP32 in-cell offset, mass).
 // bin_build_ci optionally streams (FP64 on the global position) first.

@@ -72,7 +72,7 @@ size_t carve_noalloc(char *base, int64_t n, int64_t ncell, float4 **P, float4 **
     *Ps = c.take<float4>(n);
     *counter = c.take<int>(1);
     *flags = c.take<int>(4);
-    carve_bin(c, n, ncell, b);
+    carve_bin(c, n, ncell, b, false);
     return c.off;
 }
 

@@ -67,6 +67,10 @@ def test_entry_points_refuse_bad_arguments(env, split_params):
         ("variant 4", lambda: lib.hacc_set_variant(h, hacc.FORCE_VARIANTS)),
         ("variant -1", lambda: lib.hacc_set_variant(h, -1)),
         ("stencil 0", lambda: lib.hacc_set_stencil(h, 0)),
+        ("item cap 8", lambda: lib.hacc_set_item_cap(h, 8, 0)),
+        ("item cap 161", lambda: lib.hacc_set_item_cap(h, 161, 0)),
+        ("item cap -2", lambda: lib.hacc_set_item_cap(h, -2, 0)),
+        ("split_max -1", lambda: lib.hacc_set_item_cap(h, 48, -1)),
         ("n_c = 0", lambda: lib.hacc_step(h, ctypes.byref(box), ctypes.byref(sp), ctypes.byref(hacc.PM()._c()), n,
                                           _p(pos), _p(vel), 0.01, 0, s)),
         ("NULL stats", lambda: lib.hacc_stats_read(h, None, 0)),

@@ -280,6 +280,47 @@ def test_bounding_box_cull_counts(torch, hacc, ctx, split_params):
     assert within < ev < 0.9 * cand
 
 
+@pytest.mark.parametrize("case", ["zeldovich", "blob"])
+def test_item_caps_against_oracle(torch, hacc, ctx, split_params, case):
+    # every item cap sums the same pairs: forces within the bar of the oracle,
+    # the same candidate and inside-cutoff counts; items that cover part of a
+    # cell (sub-cell order) evaluate no more pairs than cell-wide ones when
+    # every cell is a single cell-wide item, and fewer at the smallest cap
+    if case == "zeldovich":
+        L, pos = 32.0, synth.zeldovich(32, seed=95, L=32.0, sigma_delta=0.7)
+    else:   # dense cells of several hundred and over 512 particles among sparse ones
+        L, pos = 24.0, synth.blob_mixture(12000, 24.0, seed=96, n_blobs=3, sigma=0.35)
+    sp = dict(split_params)
+    a_ref, within_ref = oracle.force_mesh(pos, L, sp)
+    nc = hacc.mesh_cells(L, sp["r_cut"])
+    _, cell_o, _ = oracle.wrap_cell(pos, L, nc)
+    count_o, _, _ = oracle.bin_cells(cell_o, nc)
+    if case == "blob":
+        assert count_o.max() > 512
+    p = _dev(torch, pos)
+    res = {}
+    try:
+        for cap, split_max in ((0, 0), (16, 100000), (24, 0), (40, 64), (160, 0)):
+            ctx.set_item_cap(cap, split_max)
+            a = ctx.sr_force(hacc.Box(L=L), sp, p).cpu().numpy()
+            assert _force_err(a, a_ref) <= FORCE_TOL, (cap, _force_err(a, a_ref))
+            ctx.stats_read(reset=True)
+            ctx.stats_enable(counting=True)
+            ctx.sr_force(hacc.Box(L=L), sp, p)
+            st = ctx.stats_read(reset=True)
+            ctx.stats_enable()
+            res[cap] = (st["candidate_pairs"], st["within_pairs"], st["evaluated_pairs"])
+    finally:
+        ctx.set_item_cap(-1, 0)
+    cand = oracle.candidates(count_o, nc)
+    for cap, (c, w, e) in res.items():
+        assert c == cand and w == res[0][1] and w <= e <= c, cap
+    assert abs(res[0][1] - within_ref) <= max(2, within_ref // 200000)
+    if count_o.max() <= 160:
+        assert all(res[cap][2] <= res[0][2] for cap in res)
+        assert res[16][2] < 0.9 * res[0][2]
+
+
 def _candidates_numpy(pos, L, nc, R):
     # sum over cells of n_c times the particles of the (2R+1)^3 cells around it
     _, cell_o, _ = oracle.wrap_cell(pos, L, nc)
