@@ -190,7 +190,7 @@ struct Work {
     unsigned long long *within;
     float *phi;
     double *diag;
-    int *cell_active;   // multi-level: cells with a particle kicked at this event
+    int4 *ml_items;     // multi-level: work items of an event (at most one per particle)
     int *present;       // multi-level: kick counts that occur
     // multi-level: binned reference positions, a second velocity buffer,
     // input rows (two buffers) and cell ids in sorted order
@@ -216,7 +216,7 @@ size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w, bool 
     w->within = c.take<unsigned long long>(1);
     w->phi = c.take<float>(n);
     w->diag = c.take<double>(5);
-    w->cell_active = c.take<int>(ncell);
+    w->ml_items = ml ? c.take<int4>(n + 1) : nullptr;
     w->present = c.take<int>(kMaxLevels + 3);
     carve_bin(c, n, ncell, &w->b);
     return c.off + 256;
@@ -714,12 +714,6 @@ struct MlEvent {
 
 // Events (2k+1)/(2l) dt, k < l, over the kick counts l that occur, in time
 // order with duplicates merged (exact reduced fractions).
-// Dense cells keep large items at events that use the context's own item
-// cap; smaller events split every cell (more warps for the launch).
-int ml_split_max(const hacc_ctx *ctx, int icap, int cap) {
-    return (icap && cap >= icap) ? ctx->split_max : INT32_MAX;
-}
-
 std::vector<MlEvent> ml_schedule(const int *present, int lmax, double dt) {
     std::vector<std::pair<int64_t, int64_t>> ev;
     for (int l = 1; l <= lmax; ++l) {
@@ -775,7 +769,7 @@ struct MlLoop {
 ForceLaunch ml_force(hacc_ctx *ctx, Work &w, const MlLoop &m, const KickTable &kt) {
     ForceLaunch fl;
     fl.pos = m.Ps;
-    fl.items = w.b.items;
+    fl.items = w.ml_items;
     fl.n_items = w.b.n_items;
     fl.cell_start = w.b.cell_start;
     fl.work_counter = w.counter;
@@ -852,7 +846,7 @@ cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, 
             break;
         const int64_t b0 = ctx->launches;
         cudaError_t eb = bin_build(g, m.n, m.Ps, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, cs2,
-                                   item_cap_for(ctx, m.n), ctx->split_max);
+                                   item_cap_for(ctx, m.n), ctx->split_max, m.lev_s);
         if (eb == cudaSuccess)
             eb = gather_ml(m.n, w.b.perm, w.P, m.Ps, m.Ref, m.Vs, m.Vt, m.lev_s, m.lev_t, m.id_s, m.id_t, w.b.key,
                            w.Ks, cs2);
@@ -863,8 +857,8 @@ cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, 
         e = cudaStreamEndCapture(cs2, &bg);
         if (eb != cudaSuccess) e = eb;
         if (e != cudaSuccess) break;
-        if ((e = items_active(g, m.n, w.Ks, m.lev_s, ev[k].kt, w.cell_active, w.b, caps[k],
-                              ml_split_max(ctx, item_cap_for(ctx, m.n), caps[k]), cs)) != cudaSuccess)
+        if ((e = items_kicked(g.ncell, w.b, m.lev_s, ev[k].kt, caps[k], w.ml_items, (int32_t)(m.n + 1),
+                              ctx->d_flags, cs)) != cudaSuccess)
             break;
         if ((e = sr_force_launch(g, fc, ml_force(ctx, w, m, ev[k].kt), ctx->num_sms, cs)) != cudaSuccess) break;
         ctx->force_launches++;
@@ -930,7 +924,8 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     // bin src (wrapped into w.P), then gather every array into its other buffer and swap the two
     auto rebin = [&](const float4 *src, bool first) -> hacc_status {
         if (!first)
-            HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s, icap, ctx->split_max),
+            HACC_CUDA(bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, s, icap, ctx->split_max,
+                                lev_s),
                       "binning");
         HACC_CUDA(gather_ml(n, w.b.perm, w.P, Ps, Ref, first ? V : Vs, Vt, lev_s, lev_t, first ? nullptr : id_s, id_t,
                             w.b.key, w.Ks, s),
@@ -1034,8 +1029,7 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
             HACC_TRY(rebin(Ps, false));
             ctx->ml_rebins++;
         }
-        HACC_CUDA(items_active(g, n, w.Ks, lev_s, e.kt, w.cell_active, w.b, caps[k], ml_split_max(ctx, icap, caps[k]),
-                               s),
+        HACC_CUDA(items_kicked(g.ncell, w.b, lev_s, e.kt, caps[k], w.ml_items, (int32_t)(n + 1), ctx->d_flags, s),
                   "work items");
         const MlLoop m{n, Ps, Vs, Vt, Ref, pos_in, V, lev_s, lev_t, id_s, id_t, disp_bits, half_lim};
         HACC_TRY(launch_force(ctx, g, fc, ml_force(ctx, w, m, e.kt), true, s));

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restr
                                                  float4 *dst, float Lf, float inv_w, double Ld, int nc,
                                                  int32_t *__restrict__ key, int32_t *__restrict__ rank,
                                                  uint32_t *__restrict__ count, int *flags, int *mass_flag,
-                                                 uint8_t *__restrict__ sub) {
+                                                 uint8_t *__restrict__ sub, const int32_t *__restrict__ sub_level) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = src[i];
@@ -75,7 +75,11 @@ __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restr
     int32_t c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
     dst[i] = p;
     key[i] = c;
-    if (sub) sub[i] = sub_cell(p.x * inv_w - (float)cx, p.y * inv_w - (float)cy, p.z * inv_w - (float)cz);
+    if (sub) {
+        const uint8_t m = sub_cell(p.x * inv_w - (float)cx, p.y * inv_w - (float)cy, p.z * inv_w - (float)cz);
+        // with kick counts: (kick count, octant), else the 4x4x4 Morton sub-cell
+        sub[i] = sub_level ? (uint8_t)((min(sub_level[i], 31) << 3) | (m >> 3)) : m;
+    }
     rank[i] = (int32_t)atomicAdd(&count[c], 1u);
 }
 
@@ -113,12 +117,11 @@ __device__ __forceinline__ uint32_t items_of(uint32_t cnt, ItemRule r) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_pack(int64_t ncell, const uint32_t *__restrict__ count,
-                                                  const int *__restrict__ cell_active,
                                                   unsigned long long *__restrict__ packed, ItemRule cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     uint32_t k = count[c];
-    const uint32_t it = (cell_active && !cell_active[c]) ? 0u : items_of(k, cap);
+    const uint32_t it = items_of(k, cap);
     packed[c] = (unsigned long long)k | ((unsigned long long)it << 32);
 }
 
@@ -406,15 +409,13 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
                                                    const unsigned long long *__restrict__ packed,
                                                    int32_t *__restrict__ cell_start, int4 *__restrict__ items,
                                                    int32_t *__restrict__ n_items, int make_items,
-                                                   const BoxDev *__restrict__ boxes, int nbox,
-                                                   const int *__restrict__ cell_active, ItemRule cap) {
+                                                   const BoxDev *__restrict__ boxes, int nbox, ItemRule cap) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) {
         cell_start[ncell] = (int32_t)n;
         if (make_items) {
             unsigned long long last = packed[ncell - 1];
-            const bool on = !cell_active || cell_active[ncell - 1];
-            *n_items = (int32_t)((last >> 32) + (on ? items_of(count[ncell - 1], cap) : 0u));
+            *n_items = (int32_t)((last >> 32) + items_of(count[ncell - 1], cap));
         }
     }
     if (c >= ncell) return;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(kBlock) k_items(int64_t ncell, int64_t n, cons
     if (!make_items) return;
     uint32_t cnt = count[c];
     uint32_t it = (uint32_t)(p >> 32);
-    if (cnt == 0 || (cell_active && !cell_active[c])) return;
+    if (cnt == 0) return;
     int box = 0;
     if (boxes) {  // last box whose first cell is <= c
         int lo = 0, hi = nbox - 1;
@@ -765,13 +766,59 @@ __global__ void __launch_bounds__(kBlock) k_ml_commit(int64_t n, const float4 *_
     id_to[i] = id_from[i];
 }
 
-// Cells that hold a particle kicked at this event.
-__global__ void __launch_bounds__(kBlock) k_mark_active(int64_t n, const int32_t *__restrict__ key,
-                                                         const int32_t *__restrict__ level, KickTable kt,
-                                                         int *__restrict__ cell_active) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (kt.h[level[i]] != 0.0f) cell_active[key[i]] = 1;
+// Work items of one multi-level event, one warp per cell: the particles
+// kicked now form runs of consecutive sorted particles (the binning orders
+// each cell by kick count); the warp reads the cell 32 particles at a time,
+// finds the runs in the ballot of kicked lanes, and cuts each run into
+// ceil(run / cap) items of near-equal size.  Items are appended through
+// n_items (their order only changes which warp takes which item, not any sum).
+__device__ __forceinline__ void emit_run(int64_t c, int32_t lo, int32_t hi, uint32_t cap, int lane, int4 *items,
+                                         int32_t *n_items, int32_t max_items, int *flags) {
+    const uint32_t cnt = (uint32_t)(hi - lo);
+    const uint32_t m = (cnt + cap - 1) / cap;
+    int32_t it = 0;
+    if (lane == 0) it = atomicAdd(n_items, (int32_t)m);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it + (int64_t)m > max_items) {   // cannot happen: every item holds a particle
+        if (lane == 0) atomicOr(flags, kFlagDomain);
+        return;
+    }
+    for (uint32_t k = lane; k < m; k += 32) {
+        const uint32_t a = (uint32_t)((uint64_t)cnt * k / m), e = (uint32_t)((uint64_t)cnt * (k + 1) / m);
+        items[it + k] = make_int4((int)c, (int)(lo + a), (int)(e - a), item_shape(e - a));
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_items_kicked(int64_t ncell, const int32_t *__restrict__ cell_start,
+                                                          const int32_t *__restrict__ level, KickTable kt,
+                                                          uint32_t cap, int4 *__restrict__ items,
+                                                          int32_t *__restrict__ n_items, int32_t max_items,
+                                                          int *flags) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncell) return;
+    const int32_t a = cell_start[c], b = cell_start[c + 1];
+    int32_t open = -1;   // start of the run in progress
+    for (int32_t base = a; base < b; base += 32) {
+        const int32_t q = base + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, q < b && kt.h[level[q]] != 0.0f);
+        const int len = min(32, b - base);
+        int pos = 0;
+        while (pos < len) {
+            if (open < 0) {
+                const unsigned rest = m >> pos;
+                if (!rest) break;
+                pos += __ffs(rest) - 1;
+                open = base + pos;
+            }
+            const unsigned gap = ~m >> pos;   // lanes >= len are never kicked
+            if (!gap) break;                  // the run goes on into the next 32
+            pos += __ffs(gap) - 1;
+            emit_run(c, open, base + pos, cap, lane, items, n_items, max_items, flags);
+            open = -1;
+        }
+    }
+    if (open >= 0) emit_run(c, open, b, cap, lane, items, n_items, max_items, flags);
 }
 
 
@@ -818,10 +865,9 @@ ItemRule item_rule(int item_cap, int split_max) {
 
 // Counting sort by key and work items, shared by the single-box and batched passes.
 cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_items, const BoxDev *boxes, int nbox,
-                     cudaStream_t s, const int *cell_active = nullptr, ItemRule cap = {kItemMax, 0xffffffffu},
-                     const uint8_t *sub = nullptr) {
+                     cudaStream_t s, ItemRule cap = {kItemMax, 0xffffffffu}, const uint8_t *sub = nullptr) {
     cudaError_t e;
-    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, cell_active, b.packed, cap);
+    k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, b.packed, cap);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(b.packed, ncell, b.scan_tmp, s)) != cudaSuccess) return e;
@@ -845,7 +891,7 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
         }
     }
     k_items<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items,
-                                                 make_items ? 1 : 0, boxes, nbox, cell_active, cap);
+                                                 make_items ? 1 : 0, boxes, nbox, cap);
     note_launch();
     return cudaGetLastError();
 }
@@ -853,20 +899,20 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
 
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s,
-                      int item_cap, int split_max) {
+                      int item_cap, int split_max, const int32_t *sub_level) {
     if (item_cap != 0 && (item_cap < kItemCapMin || item_cap > kItemMax)) return cudaErrorInvalidValue;
-    if (split_max < 1 || (item_cap && !b.sub)) return cudaErrorInvalidValue;
-    uint8_t *sub = item_cap ? b.sub : nullptr;
+    if (split_max < 1 || ((item_cap || sub_level) && !b.sub)) return cudaErrorInvalidValue;
+    uint8_t *sub = (item_cap || sub_level) ? b.sub : nullptr;
     cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * g.ncell, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
     if (n > 0) {
         k_key<<<blocks_for(n), kBlock, 0, s>>>(n, src, vel, drift, dst, g.Lf, g.inv_w, g.Ld, g.nc, b.key,
-                                               b.rank, b.count, d_flags, b.mass_flag, sub);
+                                               b.rank, b.count, d_flags, b.mass_flag, sub, sub_level);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s, nullptr, item_rule(item_cap, split_max), sub);
+    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s, item_rule(item_cap, split_max), sub);
 }
 
 cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmin, int lmax, int32_t *level,
@@ -901,25 +947,14 @@ cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift
     return cudaGetLastError();
 }
 
-// Work items of the current binning, only for cells marked active.
-cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
-                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, int split_max,
-                         cudaStream_t s) {
-    if (cap < kItemCapMin || cap > kItemMax || split_max < 1) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(cell_active, 0, sizeof(int) * g.ncell, s);
+// Work items of one multi-level event from the runs of kicked particles.
+cudaError_t items_kicked(int64_t ncell, const BinBuffers &b, const int32_t *level, const KickTable &kt, int cap,
+                         int4 *items, int32_t max_items, int *d_flags, cudaStream_t s) {
+    if (cap < kItemCapMin || cap > kItemMax) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(b.n_items, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    if (n > 0) {
-        k_mark_active<<<blocks_for(n), kBlock, 0, s>>>(n, key, level, kt, cell_active);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const ItemRule rule{(uint32_t)cap, (uint32_t)split_max};
-    k_pack<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, b.count, cell_active, b.packed, rule);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = scan_exclusive(b.packed, g.ncell, b.scan_tmp, s)) != cudaSuccess) return e;
-    k_items<<<blocks_for(g.ncell), kBlock, 0, s>>>(g.ncell, n, b.count, b.packed, b.cell_start, b.items, b.n_items, 1,
-                                                   nullptr, 1, cell_active, rule);
+    k_items_kicked<<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.cell_start, level, kt, (uint32_t)cap, items,
+                                                             b.n_items, max_items, d_flags);
     note_launch();
     return cudaGetLastError();
 }
@@ -940,7 +975,7 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s, nullptr, item_rule(item_cap, split_max), sub);
+    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s, item_rule(item_cap, split_max), sub);
 }
 
 cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,

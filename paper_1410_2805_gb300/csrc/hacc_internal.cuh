@@ -228,10 +228,12 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_orde
 // order, z bit first; ties by input row), and the work items are runs of at
 // most item_cap particles of that order, so an item covers a compact part of
 // its cell; cells of more than split_max particles get items of up to
-// kItemMax.
+// kItemMax.  sub_level (nullable, n kick counts aligned with src): order each
+// cell by (kick count, octant, input row) instead, so that the particles of a
+// kick count are consecutive.
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s,
-                      int item_cap = 0, int split_max = kDefaultSplitMax);
+                      int item_cap = 0, int split_max = kDefaultSplitMax, const int32_t *sub_level = nullptr);
 
 // Batched binning of nbox boxes (table `boxes` on the device, ascending
 // part_base and cell_base): for every tick-scratch index t the particle at
@@ -266,9 +268,11 @@ cudaError_t ml_decide(const unsigned *disp_bits, float half_lim, cudaGraphCondit
 cudaError_t ml_commit(int64_t n, const float4 *v_from, float4 *v_to, const int32_t *lev_from, int32_t *lev_to,
                       const int32_t *id_from, int32_t *id_to, unsigned *disp_bits, unsigned body_launches,
                       unsigned long long *launches, cudaStream_t s);
-cudaError_t items_active(const Geometry &g, int64_t n, const int32_t *key, const int32_t *level,
-                         const KickTable &kt, int *cell_active, const BinBuffers &b, int cap, int split_max,
-                         cudaStream_t s);
+// Work items of a multi-level event: the runs of particles kicked now (level:
+// kick counts in sorted order; cells ordered by kick count), in items of at
+// most cap particles written to items (room for max_items).
+cudaError_t items_kicked(int64_t ncell, const BinBuffers &b, const int32_t *level, const KickTable &kt, int cap,
+                         int4 *items, int32_t max_items, int *d_flags, cudaStream_t s);
 
 // Precision variant: positions as (cell id, FP32 in-cell offset, mass).
 // bin_build_ci optionally streams (FP64 on the global position) first.
