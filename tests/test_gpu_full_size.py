@@ -1,0 +1,168 @@
+"""GPU parity at the full sizes of the benchmark workloads, through the same
+launches the benchmark times: the 256^3 Zel'dovich box of the full step (pair
+force and PM force on seeded samples of particles that the oracle computes one
+by one; sub-cycles and the full step through properties that hold at any
+size), the 512^3 precision box (cell/offset forces on a sample), and the
+200-box batch (the smallest boxes stepped whole by the oracle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import pm as opm
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1410_2805_gb300 as hacc
+    from paper_1410_2805_gb300 import build
+    build.build()
+    ctx = hacc.Context()
+    yield torch, hacc, ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def zel256():
+    # the full-step workload: 256^3 particles from Zel'dovich displacements
+    # (P(k) ~ k^-2), box 256, Gaussian velocities sigma 0.1 (the benchmark's seed)
+    pos = synth.zeldovich(256, seed=2, L=256.0)
+    vel = synth.gaussian_velocities(len(pos), seed=2, sigma=0.1)
+    return pos, vel, 256.0
+
+
+def _f32_split(split_params):
+    sp = dict(split_params)
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    return sp
+
+
+def test_zeldovich256_pair_force_sampled(env, split_params, zel256):
+    torch, hacc, ctx = env
+    pos, _, L = zel256
+    sp = _f32_split(split_params)
+    p = torch.from_numpy(pos).cuda()
+    acc = ctx.sr_force(hacc.Box(L=L), sp, p)
+    cand, within = ctx.pair_counts(hacc.Box(L=L), sp, p)
+    a = acc.cpu().numpy()
+    sel = np.sort(np.random.default_rng(256).choice(len(pos), size=4096, replace=False))
+    ref, _ = oracle.force_mesh(pos, L, sp, sel=sel)
+    rms = np.sqrt((ref ** 2).sum(1).mean())
+    assert np.abs(a[sel, :3] - ref).max() / rms <= FORCE_TOL
+    assert np.all(a[:, 3] == 0) and np.isfinite(a).all()
+    nc = hacc.mesh_cells(L, sp["r_cut"])
+    _, cell_o, ok = oracle.wrap_cell(pos, L, nc)
+    count_o, _, _ = oracle.bin_cells(cell_o, nc)
+    assert ok and cand == oracle.candidates(count_o, nc)
+    assert 0 < within < cand
+    # every pair force enters i and j with opposite signs: no net force
+    m = pos[:, 3].astype(np.float64)
+    ma = m[:, None] * a[:, :3].astype(np.float64)
+    assert np.abs(ma.sum(0)).max() < 1e-5 * np.abs(ma).sum()
+
+
+def test_zeldovich256_pm_force_sampled(env, zel256):
+    torch, hacc, ctx = env
+    pos, _, L = zel256
+    ng = 256
+    a = ctx.pm_force(hacc.Box(L=L, ng=ng), hacc.PM(), torch.from_numpy(pos).cuda()).cpu().numpy()
+    sel = np.sort(np.random.default_rng(257).choice(len(pos), size=4096, replace=False))
+    x = pos[:, :3].astype(np.float64)
+    m = pos[:, 3].astype(np.float64)
+    ref = opm.pm_accel(x[sel], m[sel], L, ng, sources=(x, m))
+    rms = np.sqrt((ref ** 2).sum(1).mean())
+    assert np.abs(a[sel, :3] - ref).max() / rms <= FORCE_TOL
+    assert np.all(a[:, 3] == 0)
+
+
+def test_zeldovich256_subcycles_and_step_properties(env, split_params, zel256):
+    torch, hacc, ctx = env
+    pos, vel, L = zel256
+    box = hacc.Box(L=L)
+    # 5 sub-cycles of the step 0.5: antisymmetric kicks leave the momentum
+    # unchanged, positions stay wrapped, and the result is reproducible
+    p1, v1 = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
+    p2, v2 = p1.clone(), v1.clone()
+    ctx.subcycle(box, split_params, p1, v1, 0.5, 5)
+    ctx.subcycle(box, split_params, p2, v2, 0.5, 5)
+    ctx.sync()
+    assert torch.equal(p1, p2) and torch.equal(v1, v2)
+    x = p1.cpu().numpy()
+    assert np.isfinite(x).all() and np.all((x[:, :3] >= 0) & (x[:, :3] < L))
+    dv = v1.cpu().numpy()[:, :3].astype(np.float64) - vel[:, :3]
+    m = pos[:, 3].astype(np.float64)
+    assert np.abs((m[:, None] * dv).sum(0)).max() < 1e-5 * (m[:, None] * np.abs(dv)).sum()
+    # one full step (PM half kicks around the sub-cycles), twice from the same state
+    p1, v1 = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
+    p2, v2 = p1.clone(), v1.clone()
+    ctx.step(box, split_params, hacc.PM(), p1, v1, 0.5, 5)
+    ctx.step(box, split_params, hacc.PM(), p2, v2, 0.5, 5)
+    ctx.sync()
+    assert torch.equal(p1, p2) and torch.equal(v1, v2)
+    x, v = p1.cpu().numpy(), v1.cpu().numpy()
+    assert np.isfinite(x).all() and np.isfinite(v).all()
+    assert np.all((x[:, :3] >= 0) & (x[:, :3] < L))
+
+
+def test_precision512_cell_offset_sampled(env, split_params):
+    # the precision workload: 512^3 Zel'dovich particles, box 512, as (cell id,
+    # FP32 in-cell offset) from FP64 positions, against the FP64 oracle
+    torch, hacc, ctx = env
+    L = 512.0
+    x64 = synth.zeldovich(512, seed=3, L=L, return_f64=True)
+    n = len(x64)
+    sp = _f32_split(split_params)
+    box = hacc.Box(L=L)
+    cell, off = ctx.ci_from_f64(box, sp["r_cut"], torch.from_numpy(x64).cuda())
+    a = ctx.sr_force_ci(box, sp, cell, off).cpu().numpy()[:, :3].astype(np.float64)
+    del cell, off
+    torch.cuda.empty_cache()
+    sel = np.sort(np.random.default_rng(512).choice(n, size=8192, replace=False))
+    pos64 = np.concatenate([x64, np.ones((n, 1))], axis=1)
+    del x64
+    ref, _ = oracle.force_mesh(pos64, L, sp, sel=sel)
+    del pos64
+    rms = np.sqrt((ref ** 2).sum(1).mean())
+    d = np.sqrt(((a[sel] - ref) ** 2).sum(1))
+    amag = np.sqrt((ref ** 2).sum(1))
+    big = amag > 0.01 * rms
+    assert np.sqrt((d ** 2).mean()) / rms <= 1e-5
+    assert np.percentile(d[big] / amag[big], 99) <= 1e-4
+    assert np.isfinite(a).all()
+
+
+def test_batch200_smallest_boxes_against_oracle(env, split_params):
+    # the 200-box batch in one launch per sub-cycle; the oracle steps the
+    # three smallest boxes whole
+    torch, hacc, ctx = env
+    specs = synth.batch_boxes(200, seed=4)
+    pos, vel, boxes, off = [], [], [], 0
+    for s in specs:
+        pos.append(synth.blob_mixture_scaled(s.n, s.L, seed=s.seed))
+        vel.append(synth.gaussian_velocities(s.n, seed=s.seed))
+        boxes.append((off, s.n, s.L))
+        off += s.n
+    sp = dict(_f32_split(split_params), eps=float(np.float32(0.01)))
+    P = torch.from_numpy(np.concatenate(pos)).cuda()
+    V = torch.from_numpy(np.concatenate(vel)).cuda()
+    ctx.batch_subcycle(sp, [hacc.BatchBox(L=L, offset=o, n=k, dt=0.05) for (o, k, L) in boxes], P, V, n_sub=4)
+    ctx.sync()
+    for b in np.argsort([k for (_, k, _) in boxes])[:3]:
+        o, k, L = boxes[b]
+        xo, vo = oracle.subcycle(pos[b], vel[b], L, sp, 0.05, 4)
+        d = P[o:o + k, :3].cpu().numpy().astype(np.float64) - xo
+        d -= L * np.round(d / L)
+        assert np.abs(d).max() < 2e-5 * L
+        vscale = np.sqrt((vo ** 2).sum(1).mean())
+        assert np.abs(V[o:o + k, :3].cpu().numpy() - vo).max() < 1e-3 * vscale
+    x = P.cpu().numpy()
+    assert np.isfinite(x).all()
