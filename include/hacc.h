@@ -176,8 +176,9 @@ hacc_status hacc_step(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
  * The mesh is kept while the particles move (as the paper keeps its tree):
  * at each event the largest per-axis drift from the binned positions is
  * checked, and only when it passes half the cell's excess width over r_cut
- * are the particles rebinned.  At an event only the cells holding a kicked
- * particle get work items.  One host synchronisation per step reads which
+ * are the particles rebinned (each cell then ordered by kick count).  At an
+ * event only the particles kicked then get work items (as i; every particle
+ * stays a j).  One host synchronisation per step reads which
  * kick counts occur; the events then run as one CUDA graph cached by the
  * context (the rebinnings are conditional nodes decided on the device), or,
  * with statistics timing or counting on, from the host with one
