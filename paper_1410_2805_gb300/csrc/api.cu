@@ -192,10 +192,10 @@ struct Work {
     double *diag;
     int4 *ml_items;     // multi-level: work items of an event (at most one per particle)
     int *present;       // multi-level: kick counts that occur
-    // multi-level: binned reference positions, a second velocity buffer,
-    // input rows (two buffers) and cell ids in sorted order
+    // multi-level: binned reference positions, a second velocity buffer and
+    // input rows (two buffers)
     float4 *R, *V2;
-    int32_t *I1, *I2, *Ks;
+    int32_t *I1, *I2;
     BinBuffers b;
 };
 
@@ -205,7 +205,6 @@ size_t carve_work(char *base, int64_t n, int64_t ncell, bool dyn, Work *w, bool 
     w->V2 = ml ? c.take<float4>(n) : nullptr;
     w->I1 = ml ? c.take<int32_t>(n) : nullptr;
     w->I2 = ml ? c.take<int32_t>(n) : nullptr;
-    w->Ks = ml ? c.take<int32_t>(n) : nullptr;
     w->P = c.take<float4>(n);
     w->Ps = c.take<float4>(n);
     w->V = dyn ? c.take<float4>(n) : nullptr;
@@ -848,8 +847,7 @@ cudaError_t ml_capture(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, 
         cudaError_t eb = bin_build(g, m.n, m.Ps, nullptr, 0.0f, w.P, w.b, ctx->d_flags, false, cs2,
                                    item_cap_for(ctx, m.n), ctx->split_max, m.lev_s);
         if (eb == cudaSuccess)
-            eb = gather_ml(m.n, w.b.perm, w.P, m.Ps, m.Ref, m.Vs, m.Vt, m.lev_s, m.lev_t, m.id_s, m.id_t, w.b.key,
-                           w.Ks, cs2);
+            eb = gather_ml(m.n, w.b.perm, w.P, m.Ps, m.Ref, m.Vs, m.Vt, m.lev_s, m.lev_t, m.id_s, m.id_t, cs2);
         body = ctx->launches - b0 + 1;
         if (eb == cudaSuccess)
             eb = ml_commit(m.n, m.Vt, m.Vs, m.lev_t, m.lev_s, m.id_t, m.id_s, m.disp_bits, (unsigned)body,
@@ -928,7 +926,7 @@ hacc_status hacc_subcycle_ml(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
                                 lev_s),
                       "binning");
         HACC_CUDA(gather_ml(n, w.b.perm, w.P, Ps, Ref, first ? V : Vs, Vt, lev_s, lev_t, first ? nullptr : id_s, id_t,
-                            w.b.key, w.Ks, s),
+                            s),
                   "gather");
         std::swap(Vs, Vt);
         std::swap(lev_s, lev_t);

@@ -502,8 +502,7 @@ __global__ void __launch_bounds__(kBlock) k_gather_ml(int64_t n, const int32_t *
                                                        float4 *__restrict__ ref_out, const float4 *__restrict__ v_in,
                                                        float4 *__restrict__ v_out, const int32_t *__restrict__ lev_in,
                                                        int32_t *__restrict__ lev_out, const int32_t *__restrict__ id_in,
-                                                       int32_t *__restrict__ id_out, const int32_t *__restrict__ key,
-                                                       int32_t *__restrict__ key_out) {
+                                                       int32_t *__restrict__ id_out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int32_t i = perm[k];
@@ -513,7 +512,6 @@ __global__ void __launch_bounds__(kBlock) k_gather_ml(int64_t n, const int32_t *
     v_out[k] = v_in[i];
     lev_out[k] = lev_in[i];
     id_out[k] = id_in ? id_in[i] : i;
-    key_out[k] = key[i];
 }
 
 __global__ void __launch_bounds__(kBlock) k_scatter(int64_t n, const int32_t *__restrict__ id,
@@ -1030,10 +1028,10 @@ cudaError_t gather_sorted(int64_t n, const int32_t *perm, const float4 *p_in, fl
 
 cudaError_t gather_ml(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, float4 *ref_out,
                       const float4 *v_in, float4 *v_out, const int32_t *lev_in, int32_t *lev_out, const int32_t *id_in,
-                      int32_t *id_out, const int32_t *key, int32_t *key_out, cudaStream_t s) {
+                      int32_t *id_out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_gather_ml<<<blocks_for(n), kBlock, 0, s>>>(n, perm, p_in, p_out, ref_out, v_in, v_out, lev_in, lev_out, id_in,
-                                                 id_out, key, key_out);
+                                                 id_out);
     note_launch();
     return cudaGetLastError();
 }

@@ -249,15 +249,15 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
 // Multi-level stepping: kick counts from the cell densities of the last
 // binning (keys/counts in b; present[l] += particles with l kicks); in-place stream of
 // sorted positions with the largest drift from the binned ones; the rebinning
-// gather; and work items of the current binning for the cells that hold a
-// particle kicked now (keys and kick counts in one common order).
+// gather (positions, reference positions, velocities, kick counts, input
+// rows); the work items of an event are built by items_kicked below.
 cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmin, int lmax, int32_t *level,
                       int *present, cudaStream_t s);
 cudaError_t stream_sorted(int64_t n, float4 *pos, const float4 *vel, float drift, const float4 *p0, unsigned *disp,
                           cudaStream_t s);
 cudaError_t gather_ml(int64_t n, const int32_t *perm, const float4 *p_in, float4 *p_out, float4 *ref_out,
                       const float4 *v_in, float4 *v_out, const int32_t *lev_in, int32_t *lev_out, const int32_t *id_in,
-                      int32_t *id_out, const int32_t *key, int32_t *key_out, cudaStream_t s);
+                      int32_t *id_out, cudaStream_t s);
 // Graph form of the drift check: set the conditional node `handle` to
 // whether the largest drift passed `half_lim` (and count the rebinning in
 // *rebins); a non-finite drift raises the domain flag instead.  ml_commit
