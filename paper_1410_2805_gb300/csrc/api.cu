@@ -368,6 +368,7 @@ hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream) {
     HACC_CUDA(cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost), "reading device flags");
     HACC_CUDA(cudaMemset(ctx->d_flags, 0, sizeof flags), "clearing device flags");
     if (flags[0] & kFlagTimeout) return set_error(ctx, HACC_ETIMEOUT, "a device-side wait gave up");
+    if (flags[0] & kFlagItems) return set_error(ctx, HACC_ECUDA, "internal: a work-item list ran out of room");
     if (flags[0] & kFlagDomain)
         return set_error(ctx, HACC_EDOMAIN, "a coordinate was outside [-L, 2L) or not finite");
     return HACC_OK;

@@ -778,7 +778,7 @@ __device__ __forceinline__ void emit_run(int64_t c, int32_t lo, int32_t hi, uint
     if (lane == 0) it = atomicAdd(n_items, (int32_t)m);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it + (int64_t)m > max_items) {   // cannot happen: every item holds a particle
-        if (lane == 0) atomicOr(flags, kFlagDomain);
+        if (lane == 0) atomicOr(flags, kFlagItems);
         return;
     }
     for (uint32_t k = lane; k < m; k += 32) {

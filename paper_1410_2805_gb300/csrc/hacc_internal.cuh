@@ -16,6 +16,7 @@ namespace hacc {
 enum DeviceFlag : int {
     kFlagDomain = 1,   // a coordinate outside [-L, 2L) or not finite
     kFlagTimeout = 2,  // a bounded device wait gave up
+    kFlagItems = 4,    // a work-item list ran out of room (an internal bound failed)
 };
 
 // Chunking of a chaining-mesh cell into force work items: a cell of n
