@@ -1,10 +1,13 @@
 """Pins for the oracle's multi-level stepping (Sec. 3.1, Eq. (kicks)).
 
-Fixed by: the density rule recomputed by hand (numpy cell counts), the
+Fixed by: kick counts computed by hand for a box of known cell densities
+(tests/golden/ml_kick_counts.txt), the
 reduction to one SKS step when every particle takes one kick, the reduction
 to n SKS sub-cycles when every particle takes n kicks, and time reversibility
 of the symmetric event schedule with fixed kick counts.
 """
+import os
+
 import numpy as np
 
 import oracle
@@ -17,20 +20,53 @@ def _setup(n=1500, L=16.0, seed=61):
     return pos, vel, L
 
 
-def test_levels_follow_cell_density(split_params):
-    pos, _, L = _setup()
-    nc = 5
-    for d, lmax in ((1, 4), (3, 3), (20, 4)):
-        lev = oracle.ml_levels(pos, L, nc, d, lmax)
-        _, cell, ok = oracle.wrap_cell(pos, L, nc)
-        cnt = np.bincount(cell, minlength=nc ** 3)
-        ratio = (cnt[cell].astype(np.int64) * nc ** 3) // len(pos)
-        assert np.array_equal(lev, np.minimum(ratio // d + 1, lmax))
-        for lmin in (2, lmax):
-            lev = oracle.ml_levels(pos, L, nc, d, lmax, lmin=lmin)
-            assert np.array_equal(lev, np.clip(ratio // d + 1, lmin, lmax))
-    assert np.all(oracle.ml_levels(pos, L, nc, 0, 3) == 3)
-    assert np.all(oracle.ml_levels(pos, L, nc, 0, 3, lmin=2) == 3)
+def _golden_kick_counts():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ml_kick_counts.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            head, levels, _ = line.split("|")
+            d, lmin, lmax = (int(v) for v in head.split())
+            rows.append((d, lmin, lmax, [int(v) for v in levels.split()]))
+    return rows
+
+
+def _class_box():
+    """The box of the golden file: L = 8, 4^3 cells of width 2; 37 cells with 2
+    particles, 24 empty, and cells with 4, 10 and 40; returns the FP32 rows and
+    the class (0: mean, 1: x2, 2: x5, 3: x20) of every particle."""
+    rng = np.random.default_rng(5)
+    counts = {}
+    cells = [(ix, iy, iz) for iz in range(4) for iy in range(4) for ix in range(4)]
+    order = rng.permutation(len(cells))
+    special = {cells[order[0]]: (4, 1), cells[order[1]]: (10, 2), cells[order[2]]: (40, 3)}
+    for k in order[3:40]:
+        counts[cells[k]] = (2, 0)
+    counts.update(special)
+    rows, cls = [], []
+    for (ix, iy, iz), (m, c) in counts.items():
+        # strictly inside the cell: (0.1, 1.9) of its width 2
+        u = rng.uniform(0.1, 1.9, (m, 3))
+        rows.append(u + 2.0 * np.array([ix, iy, iz], dtype=np.float64))
+        cls += [c] * m
+    x = np.concatenate(rows)
+    perm = rng.permutation(len(x))
+    pos = np.ones((len(x), 4), np.float32)
+    pos[:, :3] = x[perm]
+    return pos, np.array(cls)[perm]
+
+
+def test_kick_counts_match_hand_computed_values():
+    pos, cls = _class_box()
+    assert len(pos) == 128 and np.bincount(cls).tolist() == [74, 4, 10, 40]
+    rows = _golden_kick_counts()
+    assert len(rows) >= 10
+    for d, lmin, lmax, want in rows:
+        lev = oracle.ml_levels(pos, 8.0, 4, d, lmax, lmin=lmin)
+        got = [sorted(set(lev[cls == c].tolist())) for c in range(4)]
+        assert got == [[w] for w in want], (d, lmin, lmax, got, want)
 
 
 def test_single_kick_is_one_sks_step(split_params):
