@@ -37,9 +37,10 @@
  *
  * Errors: argument and domain errors are returned before anything is
  * enqueued.  Errors found on the device (a coordinate outside [-L, 2L) or
- * not finite, a device-side wait that gave up) raise a flag that the next
- * hacc_ctx_sync returns (and clears); affected outputs are then undefined
- * but every memory access stays in bounds.  hacc_last_error gives a message.
+ * not finite) raise a flag that the next hacc_ctx_sync returns (and clears);
+ * affected outputs are then undefined but every memory access stays in
+ * bounds.  No kernel of the library waits on another kernel, a flag or a
+ * peer, so no call can hang on the device.  hacc_last_error gives a message.
  */
 #ifndef HACC_H
 #define HACC_H
@@ -61,7 +62,8 @@ typedef enum {
                           outside [-L, 2L) / not finite (reported by hacc_ctx_sync) */
     HACC_ENOMEM = 3,   /* scratch would exceed the context's HBM budget, or cudaMalloc failed */
     HACC_ECUDA = 4,    /* a CUDA runtime / cuFFT call failed */
-    HACC_ETIMEOUT = 5  /* a bounded device-side wait gave up (reported by hacc_ctx_sync) */
+    HACC_ETIMEOUT = 5  /* reserved for a bounded device-side wait that gave up; no call
+                          returns it (the library has no device-side waits) */
 } hacc_status;
 
 /* Periodic box.  L: side in grid units; must be exactly representable in FP32
@@ -108,7 +110,7 @@ void hacc_ctx_destroy(hacc_ctx *ctx);
 const char *hacc_last_error(const hacc_ctx *ctx);
 
 /* Wait for `stream`, then return and clear any flag raised on the device
- * (HACC_EDOMAIN, HACC_ETIMEOUT) or a pending CUDA error. */
+ * (HACC_EDOMAIN) or a pending CUDA error. */
 hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream);
 
 /* Bytes of scratch the context currently holds. */
@@ -225,11 +227,19 @@ hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split 
  * The paper's runs keep absolute positions in single precision; at box sides
  * of hundreds of cells FP32 rounds positions to ~3e-5 cells and every stream
  * adds that much again.  Here a position is stored as the int32 chaining-mesh
- * cell id of the box (nc from the box, as for hacc_bin) plus an FP32 offset in
- * [-w/2, w/2] from the cell's centre (w = L/nc), with the mass as the fourth float
- * of off_m: resolution ~1e-7 cells at any L.  Pair arithmetic and accumulation
- * stay FP32 (a j's offset is moved into i's cell frame by whole cell steps);
- * FP64 is used only inside the stream, on the global position c w + off.
+ * cell id of the box (nc from the box, as for hacc_bin) plus an FP32 offset
+ * from the cell's centre, with the mass as the fourth float of off_m:
+ * resolution ~1e-7 cells at any L.  The cells step by W = fl32(L / nc), the
+ * FP32 value nearest the width: cell c (per axis) covers [c W, (c+1) W) and
+ * the last cell [(nc-1) W, L), absorbing the remainder L - nc W (a few ulp of
+ * W, of either sign); a coordinate is (c + 1/2) W + off, off in [-W/2, W/2]
+ * (last cell: up to W/2 + L - nc W).  Because W is an FP32 value, moving a
+ * neighbour's offset into i's cell frame by whole steps is exact for every
+ * pair close enough to matter, so pair separations carry one rounding at most;
+ * the wrap remainder is applied to i's offset, also exactly.  Pair arithmetic
+ * and accumulation stay FP32; FP64 is used only inside the stream, on the
+ * global position.  Requires W >= r_cut and W + (L - nc W) >= r_cut
+ * (HACC_EDOMAIN otherwise).
  * pos64: n x 3 doubles (x, y, z); mass: n floats or NULL (all 1). */
 hacc_status hacc_ci_from_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, int64_t n, const double *pos64,
                              const float *mass, int32_t *cell, float *off_m, hacc_stream_t stream);
@@ -288,14 +298,22 @@ hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, int32_t nbox
 /* ---- Serving: continuous batching of short-range runs -------------------
  * A server owns a device pool of `pool_bytes` (32 bytes per particle: one pos
  * and one vel row) and queues runs (a box of n particles, sub-cycle step h,
- * `steps` sub-cycles).  Each hacc_server_tick admits queued runs in arrival
- * order while their rows fit in the pool (first-fit, coalescing free list)
- * and, if max_active_particles > 0, while the particles advanced per tick stay
- * within it; copies admitted inputs to the device; advances every resident run
- * by one sub-cycle with hacc_batch_tick; copies finished runs back into their
- * host arrays (in place) and releases their rows; then waits for `stream`.
- * The host arrays passed to hacc_server_submit must stay valid until the run
- * has finished.  Server calls must not overlap other calls on its context. */
+ * `steps` sub-cycles).  A queued run is admitted, in arrival order, while
+ *   - its rows fit in the pool (first-fit, coalescing free list),
+ *   - the particles advanced per tick stay within max_active_particles (if > 0),
+ *   - and, when the context was created with an HBM budget, the pool plus the
+ *     scratch that the batched tick of all resident runs takes from the
+ *     context (hacc_batch_scratch_bytes; the larger of that and the arena the
+ *     context already holds) plus the context's host-copy staging stay within
+ *     the budget.
+ * Each hacc_server_tick admits queued runs; advances every resident run by one
+ * sub-cycle with hacc_batch_tick on `stream`; meanwhile admits further runs for
+ * the next tick and copies their inputs to the device on a stream of the
+ * server's own (so the upload overlaps the pass); copies runs whose last
+ * sub-cycle ran back into their host arrays (in place) and releases their
+ * rows; then waits for both streams.  The host arrays passed to
+ * hacc_server_submit must stay valid until the run has been reported finished.
+ * Server calls must not overlap other calls on its context. */
 typedef struct hacc_server hacc_server;
 
 typedef struct {
@@ -311,13 +329,23 @@ hacc_status hacc_server_create(hacc_server **out, hacc_ctx *ctx, const hacc_spli
                                int64_t max_active_particles);
 void hacc_server_destroy(hacc_server *sv);
 /* Queue a run.  pos_host / vel_host: n rows each (host memory; page-locked
- * memory copies fastest), read at admission and overwritten with the result. */
+ * memory copies fastest), read at admission and overwritten with the result.
+ * HACC_ENOMEM if the run alone exceeds the pool, the per-tick cap or the
+ * budget. */
 hacc_status hacc_server_submit(hacc_server *sv, int64_t id, double L, int64_t n, float *pos_host, float *vel_host,
                                double h, int32_t steps);
 /* One tick (see above).  finished_ids (nullable, host, finished_cap entries)
- * receives the ids of the runs retired by this tick. */
+ * receives the ids of the runs retired by this tick: at most finished_cap runs
+ * are retired per tick; further finished runs stay resident (not advanced)
+ * and are retired and reported by the next tick.  finished_ids NULL: every
+ * finished run is retired.  info->finished counts the runs retired. */
 hacc_status hacc_server_tick(hacc_server *sv, hacc_stream_t stream, hacc_server_tick_info *info,
                              int64_t *finished_ids, int32_t finished_cap);
+
+/* Bytes of context scratch one batched tick (hacc_batch_tick) over these boxes
+ * takes (the exact carving of its buffers; host arithmetic only, no device
+ * call).  Boxes with n = 0 are skipped; 0 if none remain or a box is invalid. */
+size_t hacc_batch_scratch_bytes(const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes);
 
 /* Size of the fixed device scratch behind hacc_sr_force_noalloc (16 MiB). */
 #define HACC_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
@@ -334,9 +362,10 @@ hacc_status hacc_server_tick(hacc_server *sv, hacc_stream_t stream, hacc_server_
  *   - Limit: about 49 bytes per particle plus 32 bytes per chaining-mesh cell
  *     must fit in the array (e.g. 262144 particles with up to 100000 cells);
  *     larger problems return HACC_ENOMEM before anything is enqueued.
- *   - Works on the current CUDA device.  Its first call on a device looks up
- *     the array's device address (once per device); make that first call
- *     before any stream capture.
+ *   - Works on the current CUDA device; `stream` must belong to it
+ *     (HACC_EINVAL otherwise, nothing enqueued).  Its first call on a device
+ *     looks up the array's device address (once per device); make that first
+ *     call before any stream capture.
  *   - All calls share the array and leave their data in it; calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on it and
  *     give wrong results, so serialise them.
@@ -408,10 +437,13 @@ typedef struct {
     uint64_t evaluated_pairs; /* ordered pairs the pair kernel evaluated: the candidates left after
                                  dropping j farther than r_cut from the item's bounds (counting on) */
     int64_t ml_rebins;        /* rebinnings inside multi-level steps after their first binning */
+    double build_ms;          /* summed CUDA-event durations of the chaining-mesh builds (binning and
+                                 the gather into cell order) of hacc_subcycle / hacc_step (timing on) */
+    int64_t builds;           /* builds timed into build_ms */
 } hacc_stats;
 
 /* timing != 0: record a CUDA event pair on the call's stream around every
- * pair-force launch.  counting != 0: run the counting variant of the pair
+ * pair-force launch and every chaining-mesh build of the sub-cycle loop.  counting != 0: run the counting variant of the pair
  * kernel (bitwise the same forces) and accumulate pair counts.  Both off by
  * default. */
 hacc_status hacc_stats_enable(hacc_ctx *ctx, int timing, int counting);

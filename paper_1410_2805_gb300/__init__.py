@@ -45,7 +45,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("force_launches", ctypes.c_int64),
                 ("force_ms", ctypes.c_double), ("candidate_pairs", ctypes.c_uint64),
                 ("within_pairs", ctypes.c_uint64), ("evaluated_pairs", ctypes.c_uint64),
-                ("ml_rebins", ctypes.c_int64)]
+                ("ml_rebins", ctypes.c_int64), ("build_ms", ctypes.c_double), ("builds", ctypes.c_int64)]
 
 
 class _BatchBox(ctypes.Structure):
@@ -177,6 +177,7 @@ def lib():
             "hacc_server_submit": (st, [p, i64, d, i64, p, p, d, i32]),
             "hacc_server_tick": (st, [p, p, ctypes.POINTER(_TickInfo), ctypes.POINTER(i64), i32]),
             "hacc_stats_read": (st, [p, ctypes.POINTER(_Stats), ctypes.c_int]),
+            "hacc_batch_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -202,6 +203,12 @@ def mesh_cells(L: float, r_cut: float) -> int:
 def ml_mesh_cells(L: float, r_cut: float, skin: float = 0.05) -> int:
     """Cells per side of the multi-level step's chaining mesh (box nc = 0)."""
     return int(lib().hacc_ml_mesh_cells(float(L), float(r_cut), float(skin)))
+
+
+def batch_scratch_bytes(split, boxes) -> int:
+    """Context scratch of one batched tick over `boxes` (host arithmetic only)."""
+    sp = _split_of(split)
+    return int(lib().hacc_batch_scratch_bytes(ctypes.byref(sp._c()), len(boxes), _boxes_c(boxes)))
 
 
 def _split_of(split) -> Split:
@@ -347,7 +354,7 @@ class Context:
         self._check(lib().hacc_stats_read(self._h, ctypes.byref(st), int(reset)), "hacc_stats_read")
         return dict(kernel_launches=st.kernel_launches, force_launches=st.force_launches, force_ms=st.force_ms,
                     candidate_pairs=st.candidate_pairs, within_pairs=st.within_pairs, evaluated_pairs=st.evaluated_pairs,
-                    ml_rebins=st.ml_rebins)
+                    ml_rebins=st.ml_rebins, build_ms=st.build_ms, builds=st.builds)
 
     def scratch_bytes(self) -> int:
         return int(lib().hacc_ctx_scratch_bytes(self._h))
@@ -474,6 +481,7 @@ class Server:
                                             int(max_active_particles)), "hacc_server_create")
         self._keep = {}
         self._ids = (ctypes.c_int64 * 4096)()
+        self._ids_cap = len(self._ids)
 
     def close(self):
         if self._h:
@@ -495,9 +503,10 @@ class Server:
 
     def tick(self, stream=None) -> dict:
         info = _TickInfo()
+        cap = max(0, min(int(self._ids_cap), len(self._ids)))
         self.ctx._check(lib().hacc_server_tick(self._h, self.ctx._stream(stream), ctypes.byref(info), self._ids,
-                                               len(self._ids)), "hacc_server_tick")
-        done = [int(self._ids[i]) for i in range(min(info.finished, len(self._ids)))]
+                                               cap), "hacc_server_tick")
+        done = [int(self._ids[i]) for i in range(min(info.finished, cap))]
         for rid in done:
             self._keep.pop(rid, None)
         return dict(admitted=info.admitted, finished=info.finished, active=info.active, queued=info.queued,

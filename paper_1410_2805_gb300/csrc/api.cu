@@ -98,6 +98,16 @@ hacc_status make_sr_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Ge
     return HACC_OK;
 }
 
+// Geometry of the (cell, offset) paths: cells step by the FP32 width
+// ci_step(g), the last one absorbs the remainder; both widths must reach r_cut.
+hacc_status make_ci_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geometry *g) {
+    HACC_STATUS_RETURN(make_geometry(ctx, box, r_cut, g));
+    const double W = ci_step(*g);
+    if (W < (double)r_cut || W + ci_rem(*g) < (double)r_cut)
+        return set_error(ctx, HACC_EDOMAIN, "FP32 cell width of the cell/offset mesh is below r_cut");
+    return HACC_OK;
+}
+
 static double binom(int n, int k) {
     double r = 1.0;
     for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
@@ -269,28 +279,41 @@ hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts
     return launch_force(ctx, g, fc, fl, mode != kModePotential, s);
 }
 
+// Event pair around a stretch of work on s (statistics timing): begin takes
+// a pair from the free list and records its first event; end records the
+// second and files the pair under `kind` (0 pair force, 1 chaining-mesh build).
+hacc_status timing_begin(hacc_ctx *ctx, cudaStream_t s, std::pair<cudaEvent_t, cudaEvent_t> *ev) {
+    *ev = {nullptr, nullptr};
+    if (!ctx->timing) return HACC_OK;
+    if (ctx->ev_free.empty()) {
+        cudaEvent_t a, b;
+        HACC_CUDA(cudaEventCreate(&a), "cudaEventCreate");
+        HACC_CUDA(cudaEventCreate(&b), "cudaEventCreate");
+        ctx->ev_free.emplace_back(a, b);
+    }
+    *ev = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+    HACC_CUDA(cudaEventRecord(ev->first, s), "cudaEventRecord");
+    return HACC_OK;
+}
+
+hacc_status timing_end(hacc_ctx *ctx, cudaStream_t s, const std::pair<cudaEvent_t, cudaEvent_t> &ev, int kind) {
+    if (!ev.first) return HACC_OK;
+    HACC_CUDA(cudaEventRecord(ev.second, s), "cudaEventRecord");
+    ctx->ev_used.push_back(ev);
+    ctx->ev_kind.push_back(kind);
+    if (kind == 1) ctx->builds++;
+    return HACC_OK;
+}
+
 // One pair-kernel launch; timed with an event pair when timing is on.
 hacc_status launch_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, bool counted,
                          cudaStream_t s) {
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (ctx->timing && counted) {
-        if (ctx->ev_free.empty()) {
-            cudaEvent_t a, b;
-            HACC_CUDA(cudaEventCreate(&a), "cudaEventCreate");
-            HACC_CUDA(cudaEventCreate(&b), "cudaEventCreate");
-            ctx->ev_free.emplace_back(a, b);
-        }
-        ev = ctx->ev_free.back();
-        ctx->ev_free.pop_back();
-        HACC_CUDA(cudaEventRecord(ev.first, s), "cudaEventRecord");
-    }
+    if (counted) HACC_TRY(timing_begin(ctx, s, &ev));
     HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch");
     if (counted) ctx->force_launches++;
-    if (ev.first) {
-        HACC_CUDA(cudaEventRecord(ev.second, s), "cudaEventRecord");
-        ctx->ev_used.push_back(ev);
-    }
-    return HACC_OK;
+    return timing_end(ctx, s, ev, 0);
 }
 
 }  // namespace
@@ -367,7 +390,6 @@ hacc_status hacc_ctx_sync(hacc_ctx *ctx, hacc_stream_t stream) {
     int flags[4] = {0, 0, 0, 0};
     HACC_CUDA(cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost), "reading device flags");
     HACC_CUDA(cudaMemset(ctx->d_flags, 0, sizeof flags), "clearing device flags");
-    if (flags[0] & kFlagTimeout) return set_error(ctx, HACC_ETIMEOUT, "a device-side wait gave up");
     if (flags[0] & kFlagItems) return set_error(ctx, HACC_ECUDA, "internal: a work-item list ran out of room");
     if (flags[0] & kFlagDomain)
         return set_error(ctx, HACC_EDOMAIN, "a coordinate was outside [-L, 2L) or not finite");
@@ -471,13 +493,15 @@ hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset) {
     HACC_TRY(enter(ctx));
     if (!out) return set_error(ctx, HACC_EINVAL, "out is NULL");
     HACC_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
-    for (auto &e : ctx->ev_used) {
+    for (size_t k = 0; k < ctx->ev_used.size(); ++k) {
+        auto &e = ctx->ev_used[k];
         float ms = 0.f;
         HACC_CUDA(cudaEventElapsedTime(&ms, e.first, e.second), "cudaEventElapsedTime");
-        ctx->force_ms += ms;
+        (ctx->ev_kind[k] == 1 ? ctx->build_ms : ctx->force_ms) += ms;
         ctx->ev_free.push_back(e);
     }
     ctx->ev_used.clear();
+    ctx->ev_kind.clear();
     // candidates, inside the cutoff, evaluated; multi-level graph rebinnings and their kernel launches
     unsigned long long pairs[5] = {0, 0, 0, 0, 0};
     HACC_CUDA(cudaMemcpy(pairs, ctx->d_pairs, sizeof pairs, cudaMemcpyDeviceToHost), "reading pair counts");
@@ -488,11 +512,15 @@ hacc_status hacc_stats_read(hacc_ctx *ctx, hacc_stats *out, int reset) {
     out->within_pairs = pairs[1];
     out->evaluated_pairs = pairs[2];
     out->ml_rebins = ctx->ml_rebins + (int64_t)pairs[3];
+    out->build_ms = ctx->build_ms;
+    out->builds = ctx->builds;
     if (reset) {
         ctx->ml_rebins = 0;
         ctx->launches = 0;
         ctx->force_launches = 0;
         ctx->force_ms = 0.0;
+        ctx->build_ms = 0.0;
+        ctx->builds = 0;
         HACC_CUDA(cudaMemset(ctx->d_pairs, 0, sizeof pairs), "clearing pair counts");
     }
     return HACC_OK;
@@ -578,12 +606,15 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
         const bool first = k == 0, last = k == n_sub - 1;
         // stream h/2 (first sub-cycle only; later ones were fused into the
         // previous kick) + wrap + rebin
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        HACC_TRY(timing_begin(ctx, s, &ev));
         HACC_CUDA(bin_build(g, n, first ? pos_in : w.P, first ? vel_in : nullptr, h2, w.P, w.b, ctx->d_flags, true,
                             s, item_cap_for(ctx, n), ctx->split_max),
                   "binning");
         HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, first ? vel_in : w.V, w.Vs, first ? nullptr : w.ID, w.IDs,
                                 s),
                   "gather");
+        HACC_TRY(timing_end(ctx, s, ev, 1));
         // kick h, then stream h (fused halves) or h/2 (closing the last sub-cycle);
         // positions of this sub-cycle's sorted order go to w.P
         HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModeKickDrift, nullptr, nullptr, w.Vs, w.P, h, last ? h2 : h,
@@ -600,7 +631,7 @@ hacc_status hacc_ci_from_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, in
                              const float *mass, int32_t *cell, float *off_m, hacc_stream_t stream) {
     HACC_TRY(enter(ctx));
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, r_cut, &g));
+    HACC_TRY(make_ci_geometry(ctx, box, r_cut, &g));
     HACC_TRY(check_particles(ctx, n, off_m, nullptr));
     if (n > 0 && (!pos64 || !cell)) return set_error(ctx, HACC_EINVAL, "pos64 or cell is NULL");
     HACC_CUDA(ci_from_f64(g, n, pos64, mass, cell, reinterpret_cast<float4 *>(off_m), ctx->d_flags,
@@ -613,7 +644,7 @@ hacc_status hacc_ci_to_f64(hacc_ctx *ctx, const hacc_box *box, float r_cut, int6
                            const float *off_m, double *pos64, hacc_stream_t stream) {
     HACC_TRY(enter(ctx));
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, r_cut, &g));
+    HACC_TRY(make_ci_geometry(ctx, box, r_cut, &g));
     HACC_TRY(check_particles(ctx, n, off_m, nullptr));
     if (n > 0 && (!pos64 || !cell)) return set_error(ctx, HACC_EINVAL, "pos64 or cell is NULL");
     HACC_CUDA(ci_to_f64(g, n, cell, reinterpret_cast<const float4 *>(off_m), pos64,
@@ -645,8 +676,8 @@ hacc_status ci_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, Wo
     fl.vel_pool = vel;
     fl.flags = ctx->d_flags;
     fl.cell_offset = true;
-    fl.w = (float)(g.Ld / g.nc);
-    fl.w_lo = (float)(g.Ld / g.nc - (double)fl.w);
+    fl.w = (float)ci_step(g);
+    fl.delta = (float)ci_rem(g);
     HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "short-range force launch (cell/offset)");
     ctx->force_launches++;
     return HACC_OK;
@@ -658,7 +689,7 @@ hacc_status hacc_sr_force_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     HACC_TRY(enter(ctx));
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    HACC_TRY(make_ci_geometry(ctx, box, split->r_cut, &g));
     ForceConsts fc;
     HACC_TRY(make_force_consts(ctx, split, g, &fc));
     HACC_TRY(check_particles(ctx, n, off_m, acc));
@@ -681,7 +712,7 @@ hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     if (n_sub < 1 || !std::isfinite(dt)) return set_error(ctx, HACC_EINVAL, "n_sub >= 1 and finite dt required");
     Geometry g;
-    HACC_TRY(make_geometry(ctx, box, split->r_cut, &g));
+    HACC_TRY(make_ci_geometry(ctx, box, split->r_cut, &g));
     ForceConsts fc;
     HACC_TRY(make_force_consts(ctx, split, g, &fc));
     HACC_TRY(check_particles(ctx, n, off_m, vel));

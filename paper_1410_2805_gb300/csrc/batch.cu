@@ -163,6 +163,11 @@ uint64_t mix(uint64_t h, uint64_t v) {
 
 }  // namespace
 
+size_t batch_tick_scratch_bytes(int64_t n_total, int64_t ncell_total, int64_t nbox) {
+    BatchWork w;
+    return carve_batch(nullptr, n_total, ncell_total, nbox, &w);
+}
+
 void batch_destroy(hacc_ctx *ctx) {
     if (ctx->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->graph_exec));
     ctx->graph_exec = nullptr;
@@ -177,6 +182,13 @@ void batch_destroy(hacc_ctx *ctx) {
 }  // namespace hacc
 
 using namespace hacc;
+
+extern "C" size_t hacc_batch_scratch_bytes(const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes) {
+    if (!split) return 0;
+    Plan pl;
+    if (make_plan(nullptr, split, nbox, boxes, &pl) != HACC_OK || pl.nbox == 0) return 0;
+    return batch_tick_scratch_bytes(pl.n_total, pl.ncell_total, pl.nbox);
+}
 
 extern "C" hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
                                        const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,

@@ -597,12 +597,21 @@ __global__ void __launch_bounds__(kBlock) k_candidates(int nc, int R, const int3
 }
 
 // ---- positions as (cell, in-cell offset): the precision variant ------------
+// The cells step by W = fl32(L / nc), an FP32 value, so that moving an offset
+// by one cell is exact for the close pairs that decide the force; cell c
+// covers [c W, (c+1) W) and the last cell [(nc-1) W, L), i.e. it absorbs the
+// remainder L - nc W (a few ulp of W, of either sign).  A position is
+// (c + 1/2) W + off.
 // Cell of a global FP64 coordinate x in [0, L) and its FP32 offset from the
-// cell centre, x - (c + 1/2) w, in [-w/2, w/2].
-__device__ __forceinline__ int ci_split(double x, double inv_w, double w, int nc, float &off) {
-    int c = (int)floor(x * inv_w);
+// cell centre, x - (c + 1/2) W, in [-W/2, W/2] (last cell: up to W/2 + L - nc W).
+__device__ __forceinline__ int ci_split(double x, double W, double iW, int nc, float &off) {
+    int c = (int)floor(x * iW);
     c = c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
-    off = (float)(x - ((double)c + 0.5) * w);
+    // the estimate may land one cell off next to a face: decide with exact
+    // products (c W is exact in FP64: W has 24 bits, c fewer than 11)
+    if (c > 0 && (double)c * W > x) --c;
+    else if (c < nc - 1 && (double)(c + 1) * W <= x) ++c;
+    off = (float)(x - ((double)c + 0.5) * W);
     return c;
 }
 
@@ -617,14 +626,16 @@ __device__ __forceinline__ bool wrap64(double &x, double L) {
     return true;
 }
 
-// Optional stream x += drift * v in FP64 on the global position (c w + off),
-// then re-split into (cell, offset) in place; with key != null also the
-// counting-sort keys (the cell) and the sorted-copy source dst = (off, m).
+// Optional stream x += drift * v in FP64 on the global position
+// ((c + 1/2) W + off), then re-split into (cell, offset) in place; with key !=
+// null also the counting-sort keys (the cell) and the sorted-copy source
+// dst = (off, m).
 __global__ void __launch_bounds__(kBlock) k_key_ci(int64_t n, int32_t *__restrict__ cell, float4 *__restrict__ off,
                                                     const float4 *__restrict__ vel, double drift, int nc, double L,
-                                                    double w, double inv_w, float4 *__restrict__ dst,
-                                                    int32_t *__restrict__ key, int32_t *__restrict__ rank,
-                                                    uint32_t *__restrict__ count, int *flags, int *mass_flag) {
+                                                    double W, double iW, float4 *__restrict__ dst,
+                                                    int32_t *__restrict__ key,
+                                                    int32_t *__restrict__ rank, uint32_t *__restrict__ count,
+                                                    int *flags, int *mass_flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t c = cell[i];
@@ -632,8 +643,8 @@ __global__ void __launch_bounds__(kBlock) k_key_ci(int64_t n, int32_t *__restric
     if (vel) {
         const float4 v = vel[i];
         int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-        double x = fma((double)cx + 0.5, w, (double)o.x), y = fma((double)cy + 0.5, w, (double)o.y),
-               z = fma((double)cz + 0.5, w, (double)o.z);
+        double x = fma((double)cx + 0.5, W, (double)o.x), y = fma((double)cy + 0.5, W, (double)o.y),
+               z = fma((double)cz + 0.5, W, (double)o.z);
         x = fma(drift, (double)v.x, x);
         y = fma(drift, (double)v.y, y);
         z = fma(drift, (double)v.z, z);
@@ -641,9 +652,9 @@ __global__ void __launch_bounds__(kBlock) k_key_ci(int64_t n, int32_t *__restric
         ok &= wrap64(y, L);
         ok &= wrap64(z, L);
         if (!ok) atomicOr(flags, kFlagDomain);
-        cx = ci_split(x, inv_w, w, nc, o.x);
-        cy = ci_split(y, inv_w, w, nc, o.y);
-        cz = ci_split(z, inv_w, w, nc, o.z);
+        cx = ci_split(x, W, iW, nc, o.x);
+        cy = ci_split(y, W, iW, nc, o.y);
+        cz = ci_split(z, W, iW, nc, o.z);
         c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
         cell[i] = c;
         off[i] = o;
@@ -656,9 +667,10 @@ __global__ void __launch_bounds__(kBlock) k_key_ci(int64_t n, int32_t *__restric
 }
 
 __global__ void __launch_bounds__(kBlock) k_ci_from_f64(int64_t n, const double *__restrict__ x64,
-                                                         const float *__restrict__ mass, int nc, double L, double w,
-                                                         double inv_w, int32_t *__restrict__ cell,
-                                                         float4 *__restrict__ off, int *flags) {
+                                                         const float *__restrict__ mass, int nc, double L, double W,
+                                                         double iW, int32_t *__restrict__ cell,
+                                                         float4 *__restrict__ off,
+                                                         int *flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x = x64[3 * i], y = x64[3 * i + 1], z = x64[3 * i + 2];
@@ -667,22 +679,22 @@ __global__ void __launch_bounds__(kBlock) k_ci_from_f64(int64_t n, const double 
     ok &= wrap64(z, L);
     if (!ok) atomicOr(flags, kFlagDomain);
     float4 o;
-    int cx = ci_split(x, inv_w, w, nc, o.x), cy = ci_split(y, inv_w, w, nc, o.y), cz = ci_split(z, inv_w, w, nc, o.z);
+    int cx = ci_split(x, W, iW, nc, o.x), cy = ci_split(y, W, iW, nc, o.y), cz = ci_split(z, W, iW, nc, o.z);
     o.w = mass ? mass[i] : 1.0f;
     cell[i] = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
     off[i] = o;
 }
 
 __global__ void __launch_bounds__(kBlock) k_ci_to_f64(int64_t n, const int32_t *__restrict__ cell,
-                                                       const float4 *__restrict__ off, int nc, double w,
+                                                       const float4 *__restrict__ off, int nc, double W,
                                                        double *__restrict__ x64) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t c = cell[i];
     const float4 o = off[i];
-    x64[3 * i] = fma((double)(c % nc) + 0.5, w, (double)o.x);
-    x64[3 * i + 1] = fma((double)((c / nc) % nc) + 0.5, w, (double)o.y);
-    x64[3 * i + 2] = fma((double)(c / (nc * nc)) + 0.5, w, (double)o.z);
+    x64[3 * i] = fma((double)(c % nc) + 0.5, W, (double)o.x);
+    x64[3 * i + 1] = fma((double)((c / nc) % nc) + 0.5, W, (double)o.y);
+    x64[3 * i + 2] = fma((double)(c / (nc * nc)) + 0.5, W, (double)o.z);
 }
 
 // ---- multi-level stepping ------------------------------------------------
@@ -982,9 +994,8 @@ cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *of
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.mass_flag, 0, sizeof(int), s)) != cudaSuccess) return e;
     if (n > 0) {
-        const double w = g.Ld / g.nc;
-        k_key_ci<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, vel, drift, g.nc, g.Ld, w, g.nc / g.Ld, dst, b.key,
-                                                  b.rank, b.count, d_flags, b.mass_flag);
+        k_key_ci<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, vel, drift, g.nc, g.Ld, ci_step(g), 1.0 / ci_step(g),
+                                                  dst, b.key, b.rank, b.count, d_flags, b.mass_flag);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -994,9 +1005,8 @@ cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *of
 cudaError_t drift_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,
                      int *d_flags, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const double w = g.Ld / g.nc;
-    k_key_ci<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, vel, drift, g.nc, g.Ld, w, g.nc / g.Ld, nullptr, nullptr,
-                                              nullptr, nullptr, d_flags, nullptr);
+    k_key_ci<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, vel, drift, g.nc, g.Ld, ci_step(g), 1.0 / ci_step(g),
+                                              nullptr, nullptr, nullptr, nullptr, d_flags, nullptr);
     note_launch();
     return cudaGetLastError();
 }
@@ -1004,8 +1014,8 @@ cudaError_t drift_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, c
 cudaError_t ci_from_f64(const Geometry &g, int64_t n, const double *x64, const float *mass, int32_t *cell,
                         float4 *off, int *d_flags, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const double w = g.Ld / g.nc;
-    k_ci_from_f64<<<blocks_for(n), kBlock, 0, s>>>(n, x64, mass, g.nc, g.Ld, w, g.nc / g.Ld, cell, off, d_flags);
+    k_ci_from_f64<<<blocks_for(n), kBlock, 0, s>>>(n, x64, mass, g.nc, g.Ld, ci_step(g), 1.0 / ci_step(g), cell, off,
+                                                   d_flags);
     note_launch();
     return cudaGetLastError();
 }
@@ -1013,7 +1023,7 @@ cudaError_t ci_from_f64(const Geometry &g, int64_t n, const double *x64, const f
 cudaError_t ci_to_f64(const Geometry &g, int64_t n, const int32_t *cell, const float4 *off, double *x64,
                       cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_ci_to_f64<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, g.nc, g.Ld / g.nc, x64);
+    k_ci_to_f64<<<blocks_for(n), kBlock, 0, s>>>(n, cell, off, g.nc, ci_step(g), x64);
     note_launch();
     return cudaGetLastError();
 }

@@ -15,7 +15,6 @@ namespace hacc {
 // Device-side status flags (one int each, OR-ed by kernels).
 enum DeviceFlag : int {
     kFlagDomain = 1,   // a coordinate outside [-L, 2L) or not finite
-    kFlagTimeout = 2,  // a bounded device wait gave up
     kFlagItems = 4,    // a work-item list ran out of room (an internal bound failed)
 };
 
@@ -59,8 +58,11 @@ struct hacc_ctx {
     int item_cap = -1;                        // work-item cap of the force paths (0: cell-wide items, -1: auto)
     int split_max = hacc::kDefaultSplitMax;   // cells above this many particles keep items of up to kItemMax
     double force_ms = 0.0;
+    double build_ms = 0.0;                    // event-timed chaining-mesh builds (binning + sorted gather)
+    int64_t builds = 0;
     unsigned long long *d_pairs = nullptr;   // [2] candidate, within (device)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+    std::vector<int> ev_kind;                 // per ev_used entry: 0 pair-force launch, 1 chaining-mesh build
     // batches (batch.cu): pinned staging of box tables, cached CUDA graph
     void *stage = nullptr;
     size_t stage_cap = 0;
@@ -129,6 +131,11 @@ hacc_status hacc_enter(hacc_ctx *ctx);
 #define HACC_CUDA_RETURN(x, what) HACC_STATUS_RETURN(::hacc::check_cuda(ctx, (x), what))
 
 void batch_destroy(hacc_ctx *ctx);
+// Scratch bytes one batched tick (hacc_batch_tick) takes from the context's
+// arena for n_total particles in ncell_total cells of nbox boxes (the carving
+// the tick itself uses, plus its alignment slack).
+size_t batch_tick_scratch_bytes(int64_t n_total, int64_t ncell_total, int64_t nbox);
+int32_t default_nc(double L, double r_cut);
 hacc_status check_cuda(hacc_ctx *ctx, cudaError_t e, const char *what);
 hacc_status ensure_scratch(hacc_ctx *ctx, size_t bytes, cudaStream_t stream);
 
@@ -143,6 +150,14 @@ struct Geometry {
 };
 
 hacc_status make_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Geometry *g);
+
+// Cell step of the (cell, offset) precision variant: W = fl32(L / nc), an FP32
+// value, so that whole cell steps added to an FP32 offset are exact where it
+// matters (close pairs).  Cell c covers [c W, (c+1) W), the last cell
+// [(nc-1) W, L): it absorbs the remainder L - nc W, which is exact in FP64 and
+// an FP32 value (a multiple of ulp(W) below nc ulp(W)).
+inline double ci_step(const Geometry &g) { return (double)(float)(g.Ld / g.nc); }
+inline double ci_rem(const Geometry &g) { return g.Ld - (double)g.nc * ci_step(g); }
 
 // Force constants in the form the kernel evaluates.
 struct ForceConsts {
@@ -341,10 +356,11 @@ struct ForceLaunch {
     // kModeKickLevels: kick count of each sorted particle, kick table
     const int32_t *levels = nullptr;
     KickTable kick{};
-    // positions are in-cell offsets (precision variant); w = fl(L / nc)
+    // positions are in-cell offsets (precision variant): cell step w = ci_step,
+    // and the remainder delta = L - nc w that a periodic wrap adds (ci_rem)
     bool cell_offset = false;
     float w = 0.0f;
-    float w_lo = 0.0f;                // (L / nc) - w, the FP32 remainder of the cell width
+    float delta = 0.0f;
     int variant = 0;            // pair-kernel variant (autotuned), 0..kForceVariants-1
 };
 

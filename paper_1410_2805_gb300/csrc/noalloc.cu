@@ -102,6 +102,14 @@ extern "C" hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_spl
         return HACC_ENOMEM;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HACC_ECUDA;
+    // the array's address belongs to the current device: a stream of another
+    // device would run the kernels there with this device's address
+    int stream_dev = -1;
+    if (cudaStreamGetDevice(reinterpret_cast<cudaStream_t>(stream), &stream_dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HACC_EINVAL;
+    }
+    if (stream_dev != dev) return HACC_EINVAL;
     DeviceSetup *ds = nullptr;
     if (setup_device(dev, &ds) != cudaSuccess) return HACC_ECUDA;
     carve_noalloc(ds->base, n, g.ncell, &P, &Ps, &counter, &flags, &b);

@@ -5,13 +5,18 @@
 //   1. admits queued runs in arrival order while they fit: their rows come
 //      from one device pool (first-fit over a free list of row ranges,
 //      coalesced on release -- a long-lived form of the phase-scoped pool of
-//      Sec. 2.7) and, optionally, a cap on the particles advanced per tick;
-//      admitted inputs are copied host -> device into their rows;
+//      Sec. 2.7), the particles advanced per tick stay within an optional cap,
+//      and, when the context has an HBM budget, the row pool plus the scratch
+//      that the batched tick of the resident runs will take from the context
+//      stay within it;
 //   2. advances EVERY resident run by one SKS sub-cycle in one batched pass
 //      (hacc_batch_tick: one binning pass, one persistent pair-kernel launch
 //      over all boxes), so runs that arrive while others are on the GPU join
 //      at the next tick and their work overlaps with the others';
-//   3. retires runs whose last sub-cycle ran: copies their rows back to the
+//   3. while that pass runs, admits more queued runs for the next tick and
+//      uploads their inputs on a second stream (their rows are not touched by
+//      the running pass);
+//   4. retires runs whose last sub-cycle ran: copies their rows back to the
 //      caller's host arrays and releases the rows.
 // The tick waits for the device before returning, so results of retired runs
 // are in host memory when it returns.  A run's result does not depend on what
@@ -31,20 +36,24 @@ struct hacc_server {
     hacc_split split{};
     float4 *pos = nullptr, *vel = nullptr;   // pool, `rows` rows each
     int64_t rows = 0;
+    size_t pool_bytes = 0;
     int64_t max_active = 0;                  // 0: no cap
     std::map<int64_t, int64_t> free_rows;    // offset -> length
     struct Run {
         int64_t id;
         double L;
-        int64_t n;
+        int64_t n, ncell;
         float *pos_host, *vel_host;
         double h;
         int32_t steps, done;
         int64_t offset;
     };
     std::deque<Run> queue;
-    std::vector<Run> active;
-    int64_t active_particles = 0;
+    std::vector<Run> active;                 // resident: done < steps advance, done == steps await retirement
+    cudaStream_t copy = nullptr;             // admission uploads and retirement downloads
+    cudaEvent_t ev_up = nullptr;             // the last admission upload
+    cudaEvent_t ev_tick = nullptr;           // the end of the last batched pass
+    bool up_pending = false;
 };
 
 namespace {
@@ -78,6 +87,57 @@ void free_rows(hacc_server *sv, int64_t off, int64_t n) {
     }
 }
 
+// Particles, cells and boxes of the runs that the next batched pass advances.
+struct Load {
+    int64_t n = 0, ncell = 0, nbox = 0;
+    void add(const hacc_server::Run &r) {
+        n += r.n;
+        ncell += r.ncell;
+        ++nbox;
+    }
+};
+
+// Whether a run fits next to `load` (the runs of the same pass): the
+// per-tick particle cap and, with a context budget, the row pool plus the
+// context's scratch for that pass (its arena only grows, so the larger of the
+// arena held now and the pass's need).
+bool fits(const hacc_server *sv, const Load &load, const hacc_server::Run &r) {
+    if (sv->max_active && load.n + r.n > sv->max_active) return false;
+    const size_t budget = sv->ctx->budget;
+    if (!budget) return true;
+    size_t need = hacc::batch_tick_scratch_bytes(load.n + r.n, load.ncell + r.ncell, load.nbox + 1);
+    if (need < sv->ctx->scratch.cap) need = sv->ctx->scratch.cap;
+    return sv->pool_bytes + need + sv->ctx->io_cap <= budget;
+}
+
+// Admit queued runs in arrival order while they fit next to `load`; their
+// inputs go up on the copy stream.  On a failed copy the run goes back to
+// the front of the queue with its rows released.
+hacc_status admit(hacc_server *sv, Load &load, int32_t *admitted) {
+    hacc_ctx *ctx = sv->ctx;
+    while (!sv->queue.empty()) {
+        hacc_server::Run r = sv->queue.front();
+        if (!fits(sv, load, r)) break;
+        int64_t off;
+        if (!alloc_rows(sv, r.n, &off)) break;
+        r.offset = off;
+        cudaError_t e = cudaMemcpyAsync(sv->pos + off, r.pos_host, (size_t)r.n * 16, cudaMemcpyHostToDevice, sv->copy);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sv->vel + off, r.vel_host, (size_t)r.n * 16, cudaMemcpyHostToDevice, sv->copy);
+        if (e != cudaSuccess) {
+            free_rows(sv, off, r.n);
+            return hacc::check_cuda(ctx, e, "admission copy");
+        }
+        sv->queue.pop_front();
+        sv->active.push_back(r);
+        load.add(r);
+        sv->up_pending = true;
+        ++*admitted;
+    }
+    if (sv->up_pending) HACC_CUDA_RETURN(cudaEventRecord(sv->ev_up, sv->copy), "cudaEventRecord");
+    return HACC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -96,12 +156,20 @@ hacc_status hacc_server_create(hacc_server **out, hacc_ctx *ctx, const hacc_spli
     sv->ctx = ctx;
     sv->split = *split;
     sv->rows = rows;
+    sv->pool_bytes = (size_t)rows * 32;
     sv->max_active = max_active_particles;
     if (cudaMalloc(&sv->pos, (size_t)rows * 16) != cudaSuccess || cudaMalloc(&sv->vel, (size_t)rows * 16) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(sv->pos);
         delete sv;
         return hacc::set_error(ctx, HACC_ENOMEM, "cudaMalloc of the server pool failed");
+    }
+    if (cudaStreamCreateWithFlags(&sv->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->ev_up, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->ev_tick, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        hacc_server_destroy(sv);
+        return hacc::set_error(ctx, HACC_ECUDA, "stream or event creation of the server failed");
     }
     sv->free_rows[0] = rows;
     *out = sv;
@@ -114,6 +182,9 @@ void hacc_server_destroy(hacc_server *sv) {
     cudaDeviceSynchronize();
     cudaFree(sv->pos);
     cudaFree(sv->vel);
+    if (sv->ev_up) cudaEventDestroy(sv->ev_up);
+    if (sv->ev_tick) cudaEventDestroy(sv->ev_tick);
+    if (sv->copy) cudaStreamDestroy(sv->copy);
     delete sv;
 }
 
@@ -124,12 +195,14 @@ hacc_status hacc_server_submit(hacc_server *sv, int64_t id, double L, int64_t n,
     HACC_STATUS_RETURN(hacc::hacc_enter(ctx));
     if (n < 1 || steps < 1 || !pos_host || !vel_host || !(h == h))
         return hacc::set_error(ctx, HACC_EINVAL, "bad run (n >= 1, steps >= 1, host arrays, finite h)");
-    if (n > sv->rows || (sv->max_active && n > sv->max_active))
-        return hacc::set_error(ctx, HACC_ENOMEM, "run larger than the server pool or the per-tick cap");
     hacc_box hb{L, 0, 0};
     hacc::Geometry g;
     HACC_STATUS_RETURN(hacc::make_geometry(ctx, &hb, sv->split.r_cut, &g));
-    sv->queue.push_back({id, L, n, pos_host, vel_host, h, steps, 0, -1});
+    hacc_server::Run r{id, L, n, g.ncell, pos_host, vel_host, h, steps, 0, -1};
+    if (n > sv->rows || (sv->max_active && n > sv->max_active) || !fits(sv, Load{}, r))
+        return hacc::set_error(ctx, HACC_ENOMEM,
+                               "run larger than the server pool, the per-tick cap or the HBM budget");
+    sv->queue.push_back(r);
     return HACC_OK;
 }
 
@@ -138,28 +211,23 @@ hacc_status hacc_server_tick(hacc_server *sv, hacc_stream_t stream, hacc_server_
     if (!sv) return HACC_EINVAL;
     hacc_ctx *ctx = sv->ctx;
     HACC_STATUS_RETURN(hacc::hacc_enter(ctx));
+    if (finished_cap < 0) return hacc::set_error(ctx, HACC_EINVAL, "finished_cap must be >= 0");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int32_t admitted = 0;
-    // 1. admission, in arrival order
-    while (!sv->queue.empty()) {
-        hacc_server::Run r = sv->queue.front();
-        if (sv->max_active && sv->active_particles + r.n > sv->max_active) break;
-        int64_t off;
-        if (!alloc_rows(sv, r.n, &off)) break;
-        r.offset = off;
-        HACC_CUDA_RETURN(cudaMemcpyAsync(sv->pos + off, r.pos_host, (size_t)r.n * 16, cudaMemcpyHostToDevice, s),
-                         "admission copy");
-        HACC_CUDA_RETURN(cudaMemcpyAsync(sv->vel + off, r.vel_host, (size_t)r.n * 16, cudaMemcpyHostToDevice, s),
-                         "admission copy");
-        sv->active.push_back(r);
-        sv->active_particles += r.n;
-        sv->queue.pop_front();
-        ++admitted;
+    // 1. admission for this tick, next to the runs admitted ahead of it
+    Load load;
+    for (const auto &r : sv->active)
+        if (r.done < r.steps) load.add(r);
+    HACC_STATUS_RETURN(admit(sv, load, &admitted));
+    if (sv->up_pending) {
+        HACC_CUDA_RETURN(cudaStreamWaitEvent(s, sv->ev_up, 0), "cudaStreamWaitEvent");
+        sv->up_pending = false;
     }
-    // 2. one sub-cycle of every resident run
+    // 2. one sub-cycle of every resident run that has sub-cycles left
     std::vector<hacc_batch_box> boxes;
     boxes.reserve(sv->active.size());
     for (const auto &r : sv->active) {
+        if (r.done >= r.steps) continue;
         hacc_batch_box b;
         b.L = r.L;
         b.nc = 0;
@@ -169,34 +237,58 @@ hacc_status hacc_server_tick(hacc_server *sv, hacc_stream_t stream, hacc_server_
         b.dt = r.h;
         boxes.push_back(b);
     }
-    int64_t particles = sv->active_particles;
+    const int64_t particles = load.n;
     if (!boxes.empty())
         HACC_STATUS_RETURN(hacc_batch_tick(ctx, &sv->split, (int32_t)boxes.size(), boxes.data(),
                                            reinterpret_cast<float *>(sv->pos), reinterpret_cast<float *>(sv->vel),
                                            stream));
-    // 3. retire finished runs
-    int32_t finished = 0;
+    HACC_CUDA_RETURN(cudaEventRecord(sv->ev_tick, s), "cudaEventRecord");
+    // 3. runs for the next tick: those that keep going plus newly admitted ones,
+    //    uploaded while this pass runs (into rows the pass does not touch)
+    Load next;
+    for (const auto &r : sv->active)
+        if (r.done + 1 < r.steps) next.add(r);
+    const size_t n_before = sv->active.size();
+    HACC_STATUS_RETURN(admit(sv, next, &admitted));
+    // 4. retirement: runs whose last sub-cycle ran now or earlier, up to
+    //    finished_cap of them (the others stay resident for the next tick)
+    const int32_t cap = finished_ids ? finished_cap : INT32_MAX;
+    std::vector<size_t> retire;
+    for (size_t k = 0; k < n_before; ++k) {
+        const auto &r = sv->active[k];
+        const bool finished = r.done >= r.steps || (r.done + 1 == r.steps);
+        if (finished && (int32_t)retire.size() < cap) retire.push_back(k);
+    }
+    if (!retire.empty()) HACC_CUDA_RETURN(cudaStreamWaitEvent(sv->copy, sv->ev_tick, 0), "cudaStreamWaitEvent");
+    for (size_t k : retire) {
+        const auto &r = sv->active[k];
+        HACC_CUDA_RETURN(cudaMemcpyAsync(r.pos_host, sv->pos + r.offset, (size_t)r.n * 16, cudaMemcpyDeviceToHost,
+                                         sv->copy),
+                         "retire copy");
+        HACC_CUDA_RETURN(cudaMemcpyAsync(r.vel_host, sv->vel + r.offset, (size_t)r.n * 16, cudaMemcpyDeviceToHost,
+                                         sv->copy),
+                         "retire copy");
+    }
+    HACC_CUDA_RETURN(cudaStreamSynchronize(s), "tick synchronize");
+    HACC_CUDA_RETURN(cudaStreamSynchronize(sv->copy), "tick synchronize");
+    // every copy and the pass are done: only now change the server's state
+    for (size_t k = 0; k < n_before; ++k)
+        if (sv->active[k].done < sv->active[k].steps) sv->active[k].done++;
     std::vector<hacc_server::Run> keep;
     keep.reserve(sv->active.size());
-    std::vector<std::pair<int64_t, int64_t>> released;
-    for (auto &r : sv->active) {
-        r.done++;
-        if (r.done < r.steps) {
-            keep.push_back(r);
+    int32_t finished = 0;
+    for (size_t k = 0, q = 0; k < sv->active.size(); ++k) {
+        if (q < retire.size() && retire[q] == k) {
+            const auto &r = sv->active[k];
+            free_rows(sv, r.offset, r.n);
+            if (finished_ids) finished_ids[finished] = r.id;
+            ++finished;
+            ++q;
             continue;
         }
-        HACC_CUDA_RETURN(cudaMemcpyAsync(r.pos_host, sv->pos + r.offset, (size_t)r.n * 16, cudaMemcpyDeviceToHost, s),
-                         "retire copy");
-        HACC_CUDA_RETURN(cudaMemcpyAsync(r.vel_host, sv->vel + r.offset, (size_t)r.n * 16, cudaMemcpyDeviceToHost, s),
-                         "retire copy");
-        released.emplace_back(r.offset, r.n);
-        sv->active_particles -= r.n;
-        if (finished_ids && finished < finished_cap) finished_ids[finished] = r.id;
-        ++finished;
+        keep.push_back(sv->active[k]);
     }
     sv->active.swap(keep);
-    HACC_CUDA_RETURN(cudaStreamSynchronize(s), "tick synchronize");
-    for (auto &fr : released) free_rows(sv, fr.first, fr.second);
     if (info) {
         info->admitted = admitted;
         info->finished = finished;

@@ -65,7 +65,7 @@ struct KParams {
     unsigned long long *within;
     unsigned long long *evaluated;
     const int *mass_flag;
-    float w, w_lo, w_ratio;   // cell width w = w + w_lo (FP32 pair), w_ratio = w_lo / w
+    float w, delta;   // cell/offset form: cell step (an FP32 value) and the remainder L - nc w of a wrap
     const int32_t *levels;
     KickTable kick;
     const BoxDev *boxes;
@@ -186,8 +186,10 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
 //        offset j - t of its entries, shift bits, unused)
 //   shift bits: 1/2/4 add -L to the staged j's x/y/z, 8/16/32 add -L to
 //   the i side (runs of cells within R of a high face); with in-cell
-//   offsets (CI) bits 0-3 and 4-7 hold dy + 2 and dz + 2 instead, and
-//   B = (b1, b2, d0): the x cell step of entry j is d0 + (j >= b1) + (j >= b2).
+//   offsets (CI) bits 0-3 and 4-7 hold dy + 2 and dz + 2 instead, bits 8-13
+//   the same six wrap flags (there they move the i side by +delta for a low
+//   wrap and -delta for a high one), and B = (b1, b2, d0): the x cell step of
+//   entry j is d0 + (j >= b1) + (j >= b2).
 constexpr int kMaxRuns = 64;   // 2 (2R+1)^2 <= 50 for R <= 2
 
 struct RunTable {
@@ -255,15 +257,17 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
                 j = t + a.y;
                 v = P.pos[j];
                 if (CI) {
-                    // in-cell offsets: move j into the frame of i's cell (cell steps
-                    // of w = w_hi + w_lo, applied in two adds; the x step depends on
-                    // which of the run's cells j sits in)
+                    // in-cell offsets: move j into the frame of i's cell by whole
+                    // cell steps of the FP32 width w (the x step depends on which of
+                    // the run's cells j sits in).  For a j within reach of i's cell
+                    // the sum lands in a binade no finer than the offset's, so it is
+                    // exact: a close pair across a face gets its separation with one
+                    // rounding at most, like a pair inside a cell.
                     const int4 b = rt.B[cur];
                     const float dlt = (float)(b.z + (j >= b.x) + (j >= b.y));
-                    const float sy = (float)((a.z & 15) - 2) * P.w, sz = (float)(((a.z >> 4) & 15) - 2) * P.w;
-                    v.x = __fadd_rn(__fadd_rn(v.x, dlt * P.w), dlt * P.w_lo);
-                    v.y = __fadd_rn(__fadd_rn(v.y, sy), sy * P.w_ratio);
-                    v.z = __fadd_rn(__fadd_rn(v.z, sz), sz * P.w_ratio);
+                    v.x = __fadd_rn(v.x, dlt * P.w);
+                    v.y = __fadd_rn(v.y, (float)((a.z & 15) - 2) * P.w);
+                    v.z = __fadd_rn(v.z, (float)(((a.z >> 4) & 15) - 2) * P.w);
                 } else if (a.z & 7) {
                     if (a.z & 1) v.x = __fadd_rn(v.x, -L);
                     if (a.z & 2) v.y = __fadd_rn(v.y, -L);
@@ -338,11 +342,11 @@ __device__ __forceinline__ int build_runs(const KParams &P, const RunTable &rt, 
             const int rowi = q >> 1, r = q & 1;
             const int dz = rowi / span - R, dy = rowi % span - R;
             int rz = cz + dz, ry = cy + dy;
-            if (rz < 0) { rz += nc; bits |= 4; }
-            else if (rz >= nc) { rz -= nc; bits |= 32; }
-            if (ry < 0) { ry += nc; bits |= 2; }
-            else if (ry >= nc) { ry -= nc; bits |= 16; }
-            if (CI) bits = (dy + 2) | ((dz + 2) << 4);
+            int wb = 0;   // wrap flags: 1/2/4 low in x/y/z, 8/16/32 high
+            if (rz < 0) { rz += nc; wb |= 4; }
+            else if (rz >= nc) { rz -= nc; wb |= 32; }
+            if (ry < 0) { ry += nc; wb |= 2; }
+            else if (ry >= nc) { ry -= nc; wb |= 16; }
             const int32_t *row = P.cell_start + cbase + (rz * nc + ry) * nc;
             // cells lo..hi of this row: one run, or two when it wraps in x
             const int lo = cx - R, hi = cx + R;
@@ -350,13 +354,13 @@ __device__ __forceinline__ int build_runs(const KParams &P, const RunTable &rt, 
             if (lo < 0) {           // [0, hi], then [nc + lo, nc) with j shifted by -L
                 ja = r ? row[nc + lo] : row[0];
                 jb = r ? row[nc] : row[hi + 1];
-                if (r && !CI) bits |= 1;
+                if (r) wb |= 1;
                 b1 = r ? jb : row[1];
                 d0 = r ? -1 : 0;
             } else if (hi >= nc) {  // [lo, nc), then [0, hi - nc] with i shifted by -L
                 ja = r ? row[0] : row[lo];
                 jb = r ? row[hi - nc + 1] : row[nc];
-                if (r && !CI) bits |= 8;
+                if (r) wb |= 8;
                 b1 = r ? jb : row[nc - 1];
                 d0 = r ? 1 : -1;
             } else if (r == 0) {
@@ -366,6 +370,7 @@ __device__ __forceinline__ int build_runs(const KParams &P, const RunTable &rt, 
                 d0 = -1;
             }
             b2 = wraps ? jb : (r == 0 ? row[cx + 1] : 0);
+            bits = CI ? ((dy + 2) | ((dz + 2) << 4) | (wb << 8)) : wb;
         }
         // exclusive ends of the runs in the concatenated stream
         int e = jb - ja;
@@ -495,15 +500,31 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
     const int R = P.boxes ? 1 : P.R;
     const int nrun = build_runs<CI>(P, rt, cbase, nc, cx, cy, cz, R, lane);
     // Tiles run on across all runs unless a run shifts the i side (cells
-    // within R of the high faces): then every run ends its own tile.
-    const bool carry = CI || (cx + R < nc && cy + R < nc && cz + R < nc);
+    // within R of the high faces; with in-cell offsets, cells next to any face
+    // when the mesh has a wrap remainder): then every run ends its own tile.
+    const bool carry = CI ? (P.delta == 0.0f || (cx >= R && cy >= R && cz >= R && cx + R < nc && cy + R < nc &&
+                                                 cz + R < nc))
+                          : (cx + R < nc && cy + R < nc && cz + R < nc);
     int fill = 0;
 #pragma unroll 1
     for (int q = 0; q < nrun;) {
         // all runs at once, or one run with its own i shift
         const int q1 = carry ? nrun : q + 1;
         const int bits = carry ? 0 : rt.A[q].z;
-        const float tx = (bits & 8) ? -L : 0.0f, ty = (bits & 16) ? -L : 0.0f, tz = (bits & 32) ? -L : 0.0f;
+        float tx, ty, tz;
+        if (CI) {
+            // a wrapped neighbour lies L - nc w beyond the whole cell steps:
+            // moving i by it instead keeps the j side exact (the shifted i is
+            // exact too for any i within reach of the face)
+            const int wb = bits >> 8;
+            tx = (wb & 1) ? P.delta : ((wb & 8) ? -P.delta : 0.0f);
+            ty = (wb & 2) ? P.delta : ((wb & 16) ? -P.delta : 0.0f);
+            tz = (wb & 4) ? P.delta : ((wb & 32) ? -P.delta : 0.0f);
+        } else {
+            tx = (bits & 8) ? -L : 0.0f;
+            ty = (bits & 16) ? -L : 0.0f;
+            tz = (bits & 32) ? -L : 0.0f;
+        }
         if (rt.A[q1 - 1].x > (q > 0 ? rt.A[q - 1].x : 0))   // not empty
             process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, q, q1, L, tx, ty, tz, iself, i0 + ni, lg, grp, bb,
                                                          xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
@@ -663,8 +684,7 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.w = fl.w;
     P.levels = fl.levels;
     P.kick = fl.kick;
-    P.w_lo = fl.w_lo;
-    P.w_ratio = fl.w != 0.0f ? fl.w_lo / fl.w : 0.0f;
+    P.delta = fl.delta;
     const bool eps0 = !(fc.eps > 0.0f);
     const bool pot = fl.mode == kModePotential;
     const bool count = fl.within != nullptr;

@@ -72,3 +72,21 @@ def test_ml_mesh_cells_rule():
     # never below 3 cells: a 3-cell box keeps 3
     assert hacc.ml_mesh_cells(10.0, rc, 0.5) == 3
     assert hacc.ml_mesh_cells(8.0, rc, 0.05) == -1
+
+
+def test_batch_scratch_bytes_is_host_arithmetic():
+    # the serving admission's footprint query runs without a device
+    import paper_1410_2805_gb300 as hacc
+    from paper_1410_2805_gb300 import build
+    build.build()
+    sp = hacc.default_split()
+    one = [hacc.BatchBox(L=18.0, offset=0, n=5000, dt=0.01)]
+    two = one + [hacc.BatchBox(L=24.0, offset=5000, n=12000, dt=0.01)]
+    s1, s2 = hacc.batch_scratch_bytes(sp, one), hacc.batch_scratch_bytes(sp, two)
+    assert 5000 * 64 < s1 < s2
+    # per particle about 83 bytes plus 32 per cell at large sizes
+    big = hacc.batch_scratch_bytes(sp, [hacc.BatchBox(L=256.0, offset=0, n=256 ** 3, dt=0.01)])
+    assert 75 * 256 ** 3 < big < 95 * 256 ** 3
+    assert hacc.batch_scratch_bytes(sp, []) == 0
+    assert hacc.batch_scratch_bytes(sp, [hacc.BatchBox(L=18.0, offset=0, n=0, dt=0.01)]) == 0
+    assert hacc.batch_scratch_bytes(sp, [hacc.BatchBox(L=5.0, offset=0, n=10, dt=0.01)]) == 0   # < 3 cells

@@ -40,17 +40,76 @@ def _sp(split_params):
     return sp
 
 
+def _decode(cell, off, L, nc):
+    """FP64 positions of stored (cell, FP32 offset) rows: (c + 1/2) W + off per
+    axis, W = the FP32 value nearest L / nc (the storage definition)."""
+    W = float(np.float32(L / nc))
+    c = cell.astype(np.int64)
+    idx = np.stack([c % nc, (c // nc) % nc, c // (nc * nc)], axis=1).astype(np.float64)
+    return (idx + 0.5) * W + off[:, :3].astype(np.float64)
+
+
 def test_cell_offset_round_trip(env, split_params):
     torch, hacc, ctx = env
     L = 512.0
     x = _f64_positions(50000, L, 1)
+    # add points on the last cell and next to the box faces
+    x[:6] = [[L - 1e-9, 0.0, 1e-12], [L - 1.5, L - 3.0, L - 0.25], [0.0, L / 2, L - 1e-6],
+             [1e-9, 1e-9, 1e-9], [L * (1 - 1e-12), 3.1, 6.2], [255.0, 256.0, 257.0]]
     box = hacc.Box(L=L)
+    nc = hacc.mesh_cells(L, split_params["r_cut"])
     cell, off = ctx.ci_from_f64(box, split_params["r_cut"], torch.from_numpy(x).cuda())
     back = ctx.ci_to_f64(box, split_params["r_cut"], cell, off).cpu().numpy()
-    w = L / hacc.mesh_cells(L, split_params["r_cut"])
-    assert np.abs(back - x).max() < 2.5e-7 * w
-    o = off.cpu().numpy()
-    assert np.all(np.abs(o[:, :3]) <= np.float32(w / 2) * (1 + 1e-6)) and np.all(o[:, 3] == 1)
+    c, o = cell.cpu().numpy(), off.cpu().numpy()
+    W = float(np.float32(L / nc))
+    rem = L - nc * W
+    assert abs(rem) < nc * np.spacing(np.float32(W)) and float(np.float32(rem)) == rem
+    # the kernel's decode is the storage definition, and the storage rounds by
+    # half an ulp of the offset at most
+    assert np.array_equal(back, _decode(c, o, L, nc))
+    assert np.abs(back - x).max() <= 2.0 ** -24 * 2
+    # cells as defined: [c W, (c+1) W), the last one up to L
+    idx = np.stack([c % nc, (c // nc) % nc, c // (nc * nc)], axis=1)
+    lo = idx * W
+    hi = np.where(idx == nc - 1, L, (idx + 1) * W)
+    assert np.all((x >= lo) & (x < hi))
+    assert np.all(np.abs(o[:, :3]) <= W / 2 + max(rem, 0.0) + 1e-6) and np.all(o[:, 3] == 1)
+
+
+def test_cell_offset_close_pairs_across_faces_and_wrap(env, split_params):
+    # Pairs closer than a few softening lengths that straddle chaining-mesh
+    # faces, including the periodic wrap, on every axis: moving one offset into
+    # the other's cell frame must not add rounding, so each particle's force
+    # (dominated by its partner) matches the oracle on the stored positions to
+    # a few FP32 roundings of the pair arithmetic.
+    torch, hacc, ctx = env
+    L = 512.0
+    sp = _sp(split_params)
+    nc = hacc.mesh_cells(L, sp["r_cut"])
+    W = float(np.float32(L / nc))
+    rng = np.random.default_rng(11)
+    pts = []
+    for axis in range(3):
+        for face in [0.0, 1 * W, 57 * W, (nc - 1) * W, L]:   # 0 and L: the wrap
+            for _ in range(6):
+                sep = rng.uniform(0.005, 0.08)
+                a = rng.uniform(0.0, sep)
+                c = rng.uniform(20.0, L - 20.0, 3)
+                c[axis] = face
+                p, q = c.copy(), c.copy()
+                p[axis] = face - a
+                q[axis] = face - a + sep
+                pts += [np.mod(p, L), np.mod(q, L)]
+    x = np.array(pts)
+    n = len(x)
+    box = hacc.Box(L=L)
+    cell, off = ctx.ci_from_f64(box, sp["r_cut"], torch.from_numpy(x).cuda())
+    a = ctx.sr_force_ci(box, sp, cell, off).cpu().numpy()[:, :3].astype(np.float64)
+    xs = _decode(cell.cpu().numpy(), off.cpu().numpy(), L, nc)
+    ref, _ = oracle.force_mesh(np.concatenate([xs, np.ones((n, 1))], 1), L, sp)
+    amag = np.sqrt((ref ** 2).sum(1))
+    own = np.sqrt(((a - ref) ** 2).sum(1)) / amag
+    assert own.max() <= 2e-6, own.max()
 
 
 @pytest.mark.parametrize("L,n", [(32.0, 32768), (512.0, 60000)])
