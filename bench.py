@@ -60,8 +60,12 @@ def parse():
     ap.add_argument("--no-pm", action="store_true", help="short-range sub-cycles only (no PM half kicks)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (200 boxes) segment")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson stream) segment")
-    ap.add_argument("--served-window", type=float, default=6.0, help="seconds of arrivals in the served segment")
-    ap.add_argument("--served-cap", type=float, default=20.0, help="wall-time cap of the served segment")
+    ap.add_argument("--served-window", type=float, default=8.0,
+                    help="seconds of arrivals per served rate (the C5 stream is 60 s long; shortened to fit the run)")
+    ap.add_argument("--served-cap", type=float, default=16.0, help="wall-time cap of each served rate")
+    ap.add_argument("--served-rates", type=str, default="2,4,6,10,50", help="arrival rates (per s) of the served sweep")
+    ap.add_argument("--no-c1", action="store_true", help="skip the plain 32^3 segment")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 512^3 precision segment")
     ap.add_argument("--precision", action="store_true",
                     help="precision study instead: 512^3 Zel'dovich, FP32 absolute vs cell + offset positions")
     ap.add_argument("--precision-side", type=int, default=512)
@@ -180,6 +184,16 @@ def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
     return num_sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def workload_config(args, world):
+    """The `config` object of the JSON line, the same for both arms."""
+    cfg = CONFIGS[args.config]
+    n = cfg["side"] ** 3
+    return {"workload": args.config, "desc": cfg["desc"], "particles": n, "box": cfg["L"],
+            "sub_cycles_per_step": cfg["n_c"], "pm": not args.no_pm, "dt": cfg["dt"],
+            "l2": "inputs larger than L2 (working set ~%.1f GB)" % (n * 100 / 1e9),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def make_inputs(cfg):
     import synth
     pos = synth.zeldovich(cfg["side"], seed=cfg["seed"], L=cfg["L"])
@@ -243,13 +257,13 @@ def run_reference(args):
         tot_t += time.perf_counter() - t0
         tot_pairs += w
     value = tot_pairs / tot_t
-    sample = ("short-range force of %d random particles of the %s box per step (all %d particles as sources, "
-              "cell list rebuilt per call), FP64" % (m, cfg["desc"].split(",")[0], len(pos)))
+    sample = ("short-range force of %d random particles of the initial conditions of the %s box per step (all %d "
+              "particles as sources, cell list rebuilt per call), FP64" % (m, cfg["desc"].split(",")[0], len(pos)))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pair interactions/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.config, "desc": cfg["desc"]},
+            "config": workload_config(args, world),
             "cpu_baseline": {"value": value, "unit": "pair interactions/s", "cores": oracle.threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pair interactions/s", "h2d_bytes_per_step": 0,
@@ -263,7 +277,9 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
     """200 independent blob-mixture boxes (half uniform, half in blobs of 256,
     sigma 0.5), N log-uniform in [16^3, 128^3], box side N^(1/3), step 0.1 as
     10 SR sub-cycles, one batched launch per sub-cycle, all 10 captured as
-    one CUDA graph."""
+    one CUDA graph.  The launch shape (item cap x kernel variant) is picked by
+    the batched autotuner on the batch itself first; FP64 diagnostics of every
+    box before and after the timed steps."""
     import numpy as np
 
     import synth
@@ -278,6 +294,8 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
     with torch.cuda.stream(stream):
         P = torch.from_numpy(np.concatenate(pos)).cuda()
         V = torch.from_numpy(np.concatenate(vel)).cuda()
+        tune = ctx.batch_tune(split, boxes, P, V, reps=2, stream=stream)
+        d_start = ctx.batch_diagnostics(split, boxes, P, V, stream=stream).cpu().numpy()
         for _ in range(warmup):
             ctx.batch_subcycle(split, boxes, P, V, n_sub, use_graph=True, stream=stream)
         stream.synchronize()
@@ -292,6 +310,7 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
         ms = e0.elapsed_time(e1)
         st = ctx.stats_read(reset=True)
         fin_p, fin_v = P.clone(), V.clone()
+        d_end = ctx.batch_diagnostics(split, boxes, P, V, stream=stream).cpu().numpy()
         P.copy_(snap_p)
         V.copy_(snap_v)
         ctx.stats_enable(counting=True)
@@ -317,13 +336,30 @@ def run_batched(torch, hacc, ctx, split, steps=3, warmup=1, n_sub=10, seed=4):
     peak = fp32_peak_tflops(num_sms, float(peaks.get("sm_max_mhz") or 2070.0))
     force_s = tst["force_ms"] / 1e3
     ach = cnt["candidate_pairs"] * FLOPS_PER_PAIR / force_s / 1e12 if force_s > 0 else None
+    # per box: momentum change against the summed |m v|, and the change of
+    # kinetic + short-range potential energy against the kinetic energy
+    mv_scale = np.array([np.abs(v[:, :3]).sum() for v in vel])   # unit masses
+    mom = np.abs(d_end[:, :3] - d_start[:, :3]).max(1) / mv_scale
+    energy = np.abs((d_end[:, 3] + d_end[:, 4]) - (d_start[:, 3] + d_start[:, 4])) / d_start[:, 3]
+    default_k = hacc.FORCE_VARIANTS * hacc.BATCH_TUNE_CAPS.index(0)   # cell-wide items, variant 0
     return {"workload": "200 blob-mixture boxes, N log-uniform 16^3..128^3 (total %d), 10 SR sub-cycles per "
                         "step, one batched launch per sub-cycle, CUDA graph" % n,
+            "autotune": {"chosen_setting": tune["chosen"], "item_cap": tune["item_cap"], "variant": tune["variant"],
+                         "force_ms_chosen": tune["times_ms"][tune["chosen"]],
+                         "force_ms_cell_wide_variant0": tune["times_ms"][default_k],
+                         "gain_over_cell_wide_variant0": tune["times_ms"][default_k] / tune["times_ms"][tune["chosen"]],
+                         "settings": "item cap in %s x 4 kernel variants" % (list(hacc.BATCH_TUNE_CAPS),),
+                         "force_ms_by_setting": tune["times_ms"]},
+            "diagnostics": {"max_momentum_change_rel": float(mom.max()), "max_energy_change_rel_ke": float(energy.max()),
+                            "median_energy_change_rel_ke": float(np.median(energy)),
+                            "over": "%d steps of 10 sub-cycles (step 0.1), FP64 per-box sums" % (warmup + steps)},
             "pair_interactions_per_s": cnt["within_pairs"] / (ms / 1e3),
             "particle_steps_per_s": n * n_sub * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "gpu_launches": st["kernel_launches"], "replay_bitwise_equal": same,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": (ach / peak) if ach else None,
+                         "evaluated_frac": (cnt["evaluated_pairs"] * FLOPS_PER_PAIR / force_s / 1e12 / peak)
+                         if force_s > 0 else None,
                          "candidate_pairs_per_step": cnt["candidate_pairs"] / steps,
                          "evaluated_pairs_per_step": cnt["evaluated_pairs"] / steps,
                          "force_ms_per_step": tst["force_ms"] / steps,
@@ -451,89 +487,395 @@ def run_binning(torch, hacc, ctx, split, pos, L, reps=5):
             "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
 
-def run_served(torch, hacc, ctx, split, rate, window, cap_s, seed=5, max_active=64 << 20, pool_gb=150.0):
+class RequestBoxes:
+    """Each request's own seeded box: a blob mixture of its size class (one
+    seeded template per class) moved by the request's own seeded periodic shift,
+    with velocities of the template; built ahead of use by worker threads
+    (numpy releases the GIL in these array operations)."""
+
+    def __init__(self, seed, sides=(32, 64, 128, 256), workers=4):
+        import concurrent.futures as cf
+
+        import synth
+        self.templates = {}
+        for side in sides:
+            self.templates[side] = (synth.blob_mixture_scaled(side ** 3, float(side), seed=seed * 7 + side),
+                                    synth.gaussian_velocities(side ** 3, seed=seed * 7 + side))
+        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
+
+    def build(self, req):
+        import numpy as np
+        side = round(req.n ** (1.0 / 3.0))
+        p0, v0 = self.templates[side]
+        L = np.float32(req.L)
+        shift = np.random.default_rng(req.seed).uniform(0.0, float(L), 3).astype(np.float32)
+        p = p0.copy()
+        x = p[:, :3]
+        x += shift
+        x[x >= L] -= L
+        x[x >= L] = 0          # a sum that rounds up to L
+        return p, v0.copy()
+
+    def submit(self, req):
+        return self.pool.submit(self.build, req)
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+
+def run_served(torch, hacc, ctx, split, boxes, rate, window, cap_s, seed=5, max_active=64 << 20,
+               pool_gb=40.0, budget_gb=150.0, replay=False, peak=None, variant=0):
     """Poisson arrivals (rate/s over `window` s) of runs with N in {32^3, 64^3,
-    128^3, 256^3} (blob mixture, blobs of 256) and 5-50 SR sub-cycles of step
-    0.01; continuous batching (admission in
-    arrival order against the pool and a cap of particles per tick, one
-    batched sub-cycle of every resident run per tick).  Step latency = wall
-    time of the tick that advanced the run; pair counts inline (counting
-    kernel variant, slightly slower)."""
+    128^3, 256^3} (each its own seeded blob-mixture box, blobs of 256) and 5-50
+    SR sub-cycles of step 0.01; continuous batching (admission in arrival order
+    against the row pool, a cap of particles per tick and the context's HBM
+    budget, one batched sub-cycle of every resident run per tick).  Arrived runs
+    are handed to the server in arrival order while the server's queue holds
+    fewer than two per-tick caps of particles (it cannot admit more than one
+    cap per tick, so this bounds host memory without changing which run is
+    admitted when).  Step latency = wall time of the tick that advanced the
+    run (host, including its copies); device time of each tick from CUDA
+    events on the stream.  Request latency = finish - arrival; runs unfinished
+    at the cap count as finishing at the cap (censored; their number is given).
+    replay: run the same tick schedule again with the counting kernel (pair
+    counts; the timed session runs the plain kernel with the pair launches
+    timed by events)."""
     import collections
 
     import numpy as np
 
     import synth
     reqs = synth.request_stream(rate=rate, duration=window, seed=seed)
-    templates = {}
-    for side in (32, 64, 128, 256):
-        templates[side] = (synth.blob_mixture_scaled(side ** 3, float(side), seed=seed * 7 + side),
-                           synth.gaussian_velocities(side ** 3, seed=seed * 7 + side))
+    stream = torch.cuda.current_stream()
+    sctx = hacc.Context(ctx.device, hbm_budget_bytes=int(budget_gb * 1e9))
+    sctx.set_variant(variant)
     free_b = torch.cuda.mem_get_info()[0]
     pool = int(min(pool_gb * 1e9, free_b - 24e9))
-    srv = hacc.Server(ctx, split, pool_bytes=pool, max_active_particles=max_active)
-
-    def buffers(r):
-        # each run gets its own copy of its size class's seeded box (the
-        # server writes results back into these arrays)
-        side = round(r.n ** (1.0 / 3.0))
-        p0, v0 = templates[side]
-        return p0.copy(), v0.copy()
-
+    srv = hacc.Server(sctx, split, pool_bytes=pool, max_active_particles=max_active)
     pending = collections.deque(reqs)
-    arrived = collections.deque()
-    arrival, finished_at, lat, keep = {}, {}, [], {}
-    queued = 0
-    psteps = 0
+    futures = collections.deque()          # (request, future of its buffers), arrival order
+    in_queue = collections.deque()         # handed to the server, not yet admitted (FIFO)
+    arrival, finished_at, keep = {}, {}, {}
+    schedule = []                          # requests handed over before each tick
+    lat, dev_ms = [], []
+    psteps, queued_particles = 0, 0
     busy = 0.0
-    ctx.stats_read(reset=True)
-    ctx.stats_enable(counting=True)
+    lookahead = 8
+    sctx.stats_read(reset=True)
+    sctx.stats_enable(timing=True)
     t0 = time.perf_counter()
     while True:
         now = time.perf_counter() - t0
         if now > cap_s:
             break
-        while pending and pending[0].t_arrival <= now:
+        while pending and len(futures) < lookahead:
             r = pending.popleft()
+            futures.append((r, boxes.submit(r)))
+        handed = []
+        while futures and futures[0][0].t_arrival <= now and queued_particles < 2 * max_active:
+            r, fut = futures.popleft()
+            p, v = fut.result()
             arrival[r.rid] = r.t_arrival
-            arrived.append(r)
-        while arrived and queued < 2:
-            r = arrived.popleft()
-            p, v = buffers(r)
-            keep[r.rid] = (p, v)
+            keep[r.rid] = (p, v, r)
             srv.submit(r.rid, r.L, p, v, h=0.01, steps=r.steps)
-            queued += 1
-        if queued == 0 and not keep:
-            if not pending and not arrived:
+            queued_particles += r.n
+            in_queue.append(r)
+            handed.append(r.rid)
+        if not keep:
+            if not futures and not pending:
                 break
-            time.sleep(max(0.0, min(0.01, pending[0].t_arrival - now)) if pending else 0.001)
+            nxt = futures[0][0].t_arrival if futures else now
+            time.sleep(max(0.0, min(0.01, nxt - now)))
             continue
+        schedule.append(handed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ta = time.perf_counter()
+        e0.record(stream)
         t = srv.tick()
+        e1.record(stream)
         dt = time.perf_counter() - ta
         busy += dt
-        queued = t["queued"]
+        dev_ms.append((e0, e1))
         lat += [dt] * t["active"]
         psteps += t["particles"]
         tf = time.perf_counter() - t0
         for rid in t["finished_ids"]:
             finished_at[rid] = tf
             keep.pop(rid, None)
+        for _ in range(t["admitted"]):
+            queued_particles -= in_queue.popleft().n
     wall = time.perf_counter() - t0
-    ctx.stats_enable(counting=False)
-    ctx.sync()                # raises if a coordinate left [-L, 2L)
-    cnt = ctx.stats_read(reset=True)
+    torch.cuda.synchronize()
+    dev_total = sum(a.elapsed_time(b) for a, b in dev_ms) / 1e3
+    st = sctx.stats_read(reset=True)
+    sctx.stats_enable()
+    sctx.sync()                # raises if a coordinate left [-L, 2L)
     srv.close()
+    unfinished = [k for k in arrival if k not in finished_at]
     lat_ms = np.array(lat) * 1e3 if lat else np.zeros(1)
-    resp = np.array([finished_at[k] - arrival[k] for k in finished_at]) if finished_at else np.zeros(1)
-    return {"rate_per_s": rate, "arrival_window_s": window, "wall_s": wall, "busy_s": busy,
-            "requests_arrived": len(arrival), "requests_finished": len(finished_at),
-            "run_steps": len(lat), "p50_step_ms": float(np.percentile(lat_ms, 50)),
-            "p99_step_ms": float(np.percentile(lat_ms, 99)),
-            "p50_request_s": float(np.percentile(resp, 50)), "p99_request_s": float(np.percentile(resp, 99)),
-            "pair_interactions_per_s": cnt["within_pairs"] / max(busy, 1e-9),
-            "particle_steps_per_s": psteps / max(busy, 1e-9),
-            "max_active_particles": max_active, "pool_gb": pool / 1e9}
+    resp = np.array([finished_at[k] - arrival[k] for k in finished_at] +
+                    [wall - arrival[k] for k in unfinished]) if arrival else np.zeros(1)
+    out = {"rate_per_s": rate, "arrival_window_s": window, "cap_s": cap_s, "wall_s": wall, "busy_s": busy,
+           "device_s": dev_total, "requests_arrived": len(arrival), "requests_finished": len(finished_at),
+           "requests_unfinished_censored": len(unfinished), "ticks": len(dev_ms), "run_steps": len(lat),
+           "p50_step_ms": float(np.percentile(lat_ms, 50)), "p99_step_ms": float(np.percentile(lat_ms, 99)),
+           "p50_request_s": float(np.percentile(resp, 50)), "p99_request_s": float(np.percentile(resp, 99)),
+           "particle_steps_per_s_busy": psteps / max(busy, 1e-9),
+           "particle_steps_per_s_device": psteps / max(dev_total, 1e-9),
+           "force_ms": st["force_ms"], "max_active_particles": max_active, "pool_gb": pool / 1e9,
+           "hbm_budget_gb": budget_gb}
+    if replay:
+        # the same ticks again: same hand-over schedule, so the same admissions
+        # and the same batched passes, with the counting kernel
+        srv = hacc.Server(sctx, split, pool_bytes=pool, max_active_particles=max_active)
+        sctx.stats_read(reset=True)
+        sctx.stats_enable(counting=True)
+        by_id = {r.rid: r for r in reqs}
+        for handed in schedule:
+            for rid in handed:
+                r = by_id[rid]
+                p, v = boxes.build(r)
+                keep[rid] = (p, v, r)
+                srv.submit(rid, r.L, p, v, h=0.01, steps=r.steps)
+            t = srv.tick()
+            for rid in t["finished_ids"]:
+                keep.pop(rid, None)
+        sctx.stats_enable()
+        cnt = sctx.stats_read(reset=True)
+        srv.close()
+        out["pair_interactions_per_s_device"] = cnt["within_pairs"] / max(dev_total, 1e-9)
+        out["candidate_pairs"] = cnt["candidate_pairs"]
+        out["within_pairs"] = cnt["within_pairs"]
+        force_s = st["force_ms"] / 1e3
+        if peak and force_s > 0:
+            ach = cnt["candidate_pairs"] * FLOPS_PER_PAIR / force_s / 1e12
+            ev = cnt["evaluated_pairs"] * FLOPS_PER_PAIR / force_s / 1e12
+            out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                               "frac": ach / peak, "evaluated_frac": ev / peak,
+                               "basis": "29 flop per 27-cell candidate pair (counting replay of the same ticks) "
+                                        "over the event-timed batched pair launches of the timed session"}
+    sctx.close()
+    return out
+
+
+def run_served_sweep(torch, hacc, ctx, split, rates, window, cap_s, peak, seed=5, variant=0):
+    """The served segment at several arrival rates (the same seeded stream
+    generator, one seed per rate); the highest rate also gets the counting
+    replay (pair counts, roofline).  Saturation: the particle-steps a request
+    brings on average against the particle-steps per second the server
+    sustained at the highest rate."""
+    import synth
+    boxes = RequestBoxes(seed)
+    try:
+        rows = []
+        for k, rate in enumerate(sorted(rates)):
+            last = k == len(rates) - 1
+            rows.append(run_served(torch, hacc, ctx, split, boxes, rate, window, cap_s, seed=seed + 10 * k,
+                                   replay=last, peak=peak, variant=variant))
+    finally:
+        boxes.close()
+    reqs = synth.request_stream(rate=100.0, duration=60.0, seed=seed)
+    per_req = sum(r.n * r.steps for r in reqs) / len(reqs)
+    cap = rows[-1]["particle_steps_per_s_busy"]
+    return rows, {"mean_particle_steps_per_request": per_req, "capacity_particle_steps_per_s": cap,
+                  "saturation_rate_per_s": cap / per_req}
+
+
+def run_c1(torch, hacc, ctx, split, peak, reps=20):
+    """The plain 32^3 box: 32768 particles, L = 32, half uniform and half in 64
+    Gaussian blobs (sigma 0.5), seed 1.  Pair force call and its pair-kernel
+    launch (CUDA events), binning (hacc_bin), and the force error against the
+    FP64 oracle on every particle."""
+    import numpy as np
+
+    import oracle
+    import synth
+    L = 32.0
+    pos_np = synth.blob_mixture(32768, L, seed=1)
+    pos = torch.from_numpy(pos_np).cuda()
+    box = hacc.Box(L=L)
+    stream = torch.cuda.current_stream()
+    acc = ctx.sr_force(box, split, pos)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.stats_read(reset=True)
+    ctx.stats_enable(timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.sr_force(box, split, pos, acc=acc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    call_ms = e0.elapsed_time(e1) / reps
+    st = ctx.stats_read(reset=True)
+    ctx.stats_enable(counting=True)
+    ctx.sr_force(box, split, pos, acc=acc)
+    cnt = ctx.stats_read(reset=True)
+    ctx.stats_enable()
+    a = acc.cpu().numpy()[:, :3].astype(np.float64)
+    sp = split.as_dict()
+    ref, within_o = oracle.force_mesh(pos_np, L, sp)
+    rms = float(np.sqrt((ref ** 2).sum(1).mean()))
+    kern_ms = st["force_ms"] / max(1, st["force_launches"])
+    ach = cnt["candidate_pairs"] * FLOPS_PER_PAIR / (kern_ms / 1e3) / 1e12
+    b = run_binning(torch, hacc, ctx, split, pos, L, reps=reps)
+    return {"workload": "32^3 blob mixture (half uniform, 64 blobs sigma 0.5), box 32, seed 1",
+            "force_call_ms": call_ms, "pair_kernel_ms": kern_ms,
+            "candidate_pairs": cnt["candidate_pairs"], "within_pairs": cnt["within_pairs"],
+            "within_pairs_oracle": within_o,
+            "candidate_pairs_per_s": cnt["candidate_pairs"] / (call_ms / 1e3),
+            "within_pairs_per_s": cnt["within_pairs"] / (call_ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "basis": "29 flop per 27-cell candidate pair over the event-timed pair-kernel launch"},
+            "binning": {"ms_per_call": b["ms_per_call"], "achieved_gbs": b["achieved_gbs"], "frac": b["frac"]},
+            "max_err_rel_rms": float(np.abs(a - ref).max() / rms)}
+
+
+def precision_segment(torch, hacc, side=512, sample=1 << 20, reps=3):
+    """Precision study (C3): side^3 Zel'dovich particles (box side, seed 3) from
+    FP64 positions, stored as FP32 absolute coordinates and as (cell id, FP32
+    in-cell offset).  For each storage mode, the pair forces against the FP64
+    oracle on a seeded sample of particles (all particles as sources), twice:
+    on the positions the mode stores (decoded exactly in FP64: the kernel's
+    arithmetic alone) and on the FP64 generator positions (storage rounding
+    plus arithmetic); device times of the force and of 5 SKS sub-cycles."""
+    import numpy as np
+
+    import oracle
+    import synth
+    L = float(side)
+    x64 = synth.zeldovich(side, seed=3, L=L, return_f64=True)
+    n = len(x64)
+    p32 = np.ones((n, 4), np.float32)
+    p32[:, :3] = x64.astype(np.float32)
+    p32[:, :3][p32[:, :3] >= np.float32(L)] = 0
+    vel = synth.gaussian_velocities(n, seed=3, sigma=0.1)
+    ctx = hacc.Context(torch.cuda.current_device())
+    split = hacc.default_split()
+    box = hacc.Box(L=L)
+    stream = torch.cuda.current_stream()
+    nc = hacc.mesh_cells(L, split.r_cut)
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    out = {"particles": n, "box": L, "chaining_mesh": nc}
+    P = torch.from_numpy(p32).cuda()
+    X = torch.from_numpy(x64).cuda()
+    cell, off = ctx.ci_from_f64(box, split.r_cut, X)
+    del X
+    acc32 = ctx.sr_force(box, split, P)
+    out["force_ms_fp32_abs"] = timed(lambda: ctx.sr_force(box, split, P, acc=acc32), reps)
+    acc_ci = ctx.sr_force_ci(box, split, cell, off)
+    out["force_ms_cell_offset"] = timed(lambda: ctx.sr_force_ci(box, split, cell, off), reps)
+    ctx.sync()
+    a32 = acc32.cpu().numpy()[:, :3].astype(np.float64)
+    aci = acc_ci.cpu().numpy()[:, :3].astype(np.float64)
+    c = cell.cpu().numpy().astype(np.int64)
+    o = off.cpu().numpy()[:, :3].astype(np.float64)
+    P2, V2 = P.clone(), torch.from_numpy(vel).cuda()
+    C2, O2, V3 = cell.clone(), off.clone(), torch.from_numpy(vel).cuda()
+    out["subcycle5_ms_fp32_abs"] = timed(lambda: ctx.subcycle(box, split, P2, V2, 0.5, 5), 1)
+    out["subcycle5_ms_cell_offset"] = timed(lambda: ctx.subcycle_ci(box, split, C2, O2, V3, 0.5, 5), 1)
+    ctx.sync()
+    ctx.close()
+    del P, P2, V2, C2, O2, V3, acc32, acc_ci, cell, off
+    torch.cuda.empty_cache()
+    # the stored cell/offset positions, decoded in FP64: (c + 1/2) W + off, W = fl32(L / nc)
+    W = float(np.float32(L / nc))
+    xs = np.empty((n, 4))
+    xs[:, 0] = (c % nc + 0.5) * W + o[:, 0]
+    xs[:, 1] = ((c // nc) % nc + 0.5) * W + o[:, 1]
+    xs[:, 2] = (c // (nc * nc) + 0.5) * W + o[:, 2]
+    xs[:, 3] = 1.0
+    del c, o
+    d = xs[:, :3] - x64
+    d -= L * np.round(d / L)
+    out["storage_err_cell_offset_max"] = float(np.abs(d).max())
+    d = p32[:, :3].astype(np.float64) - x64
+    d -= L * np.round(d / L)
+    out["storage_err_fp32_abs_max"] = float(np.abs(d).max())
+    del d
+    sp = split.as_dict()
+    sel = np.sort(np.random.default_rng(33).choice(n, size=min(n, sample), replace=False))
+    t0 = time.perf_counter()
+    x4 = np.concatenate([x64, np.ones((n, 1))], axis=1)
+    del x64
+    ref64, _ = oracle.force_mesh(x4, L, sp, sel=sel)
+    del x4
+    ref_ci, _ = oracle.force_mesh(xs, L, sp, sel=sel)
+    del xs
+    ref_32, _ = oracle.force_mesh(p32, L, sp, sel=sel)
+    out["oracle_s"] = time.perf_counter() - t0
+    out["oracle_threads"] = oracle.threads()
+    out["sample"] = int(len(sel))
+
+    def errs(a, ref):
+        rms = float(np.sqrt((ref ** 2).sum(1).mean()))
+        amag = np.sqrt((ref ** 2).sum(1))
+        dd = np.sqrt(((a[sel] - ref) ** 2).sum(1))
+        big = amag > 0.01 * rms
+        return {"max_rel_rms": float(dd.max() / rms), "rms_rel_rms": float(np.sqrt((dd ** 2).mean()) / rms),
+                "p99_own_rel": float(np.percentile(dd[big] / amag[big], 99))}
+
+    out["cell_offset_vs_stored"] = errs(aci, ref_ci)
+    out["cell_offset_vs_f64"] = errs(aci, ref64)
+    out["fp32_abs_vs_stored"] = errs(a32, ref_32)
+    out["fp32_abs_vs_f64"] = errs(a32, ref64)
+    out["workload"] = "%d^3 Zel'dovich (P(k)~k^-2), box %d, seed 3; oracle on a %d-particle sample" % (
+        side, side, len(sel))
+    return out
+
+
+def summary(line):
+    """The headline figures of every segment, rounded, as the last key of the
+    line (short enough to survive a truncated log)."""
+    def r(x, d=3):
+        return float("%.*g" % (d, x)) if isinstance(x, (int, float)) and x is not None else x
+    out = {"c2_pairs_per_s": r(line["value"]), "c2_frac": r(line["roofline"]["frac"]),
+           "c2_eval_frac": r(line["roofline"]["evaluated_frac"]), "c2_e2e": r((line.get("e2e") or {}).get("value")),
+           "bin_frac": r(line["binning_roofline"]["frac"]), "bin_build_frac": r(line["binning_roofline"].get(
+               "full_build_frac"))}
+    b = line.get("batched")
+    if b:
+        out["c4_pairs_per_s"] = r(b["pair_interactions_per_s"])
+        out["c4_frac"] = r(b["roofline"]["frac"])
+        out["c4_eval_frac"] = r(b["roofline"].get("evaluated_frac"))
+    sv = line.get("served")
+    if sv:
+        out["c5_sat_rate"] = r(sv["saturation"]["saturation_rate_per_s"])
+        out["c5"] = [[r(x["rate_per_s"]), r(x["p50_step_ms"]), r(x["p99_step_ms"]), r(x["p50_request_s"]),
+                      r(x["p99_request_s"]), x["requests_finished"], x["requests_unfinished_censored"]]
+                     for x in sv["sweep"]]
+        out["c5_cols"] = "rate, p50/p99 step ms, p50/p99 request s, finished, censored"
+        top = sv["sweep"][-1]
+        out["c5_pairs_per_s"] = r(top.get("pair_interactions_per_s_device"))
+        out["c5_frac"] = r((top.get("roofline") or {}).get("frac"))
+        out["c5_vs_plain"] = r(sv.get("vs_plain_pairs_per_s"))
+    c1 = line.get("c1")
+    if c1:
+        out["c1_within_per_s"] = r(c1["within_pairs_per_s"])
+        out["c1_frac"] = r(c1["roofline"]["frac"])
+        out["c1_err"] = r(c1["max_err_rel_rms"])
+        out["c1_bin_gbs"] = r(c1["binning"]["achieved_gbs"])
+    pr = line.get("precision")
+    if pr:
+        out["c3_ci_vs_stored"] = r(pr["cell_offset_vs_stored"]["max_rel_rms"])
+        out["c3_ci_vs_f64"] = r(pr["cell_offset_vs_f64"]["max_rel_rms"])
+        out["c3_abs_vs_stored"] = r(pr["fp32_abs_vs_stored"]["max_rel_rms"])
+        out["c3_abs_vs_f64"] = r(pr["fp32_abs_vs_f64"]["max_rel_rms"])
+        out["c3_force_ms"] = [r(pr["force_ms_cell_offset"]), r(pr["force_ms_fp32_abs"])]
+    ml = line.get("multilevel_paper")
+    if ml:
+        out["ml_paper_speedup"] = r(ml["speedup"])
+    return out
 
 
 def run_ours(args):
@@ -665,14 +1007,25 @@ def run_ours(args):
                 "force_ms_per_launch": st["force_ms"] / max(1, st["force_launches"]),
                 "force_launches": st["force_launches"], "force_share_of_step": st["force_ms"] / ms if ms else None}
     binning = run_binning(torch, hacc, ctx, split, snap_p, L)
+    # the chaining-mesh build inside the timed sub-cycles (binning and the
+    # gather of positions, velocities and rows into cell order), event-timed:
+    # 96 algorithmic bytes per particle (read positions for the key, write the
+    # key, read it to count and to place, read positions and velocities and
+    # write the permutation and the sorted positions and velocities)
+    if st.get("builds"):
+        per = st["build_ms"] / st["builds"]
+        gbs = 96 * n / (per / 1e3) / 1e9
+        hbm = measured_peaks().get("hbm_gbs")
+        binning["full_build_ms"] = per
+        binning["full_build_bytes_per_particle"] = 96
+        binning["full_build_gbs"] = gbs
+        binning["full_build_frac"] = gbs / hbm if hbm else None
+        binning["full_build_share_of_step"] = st["build_ms"] / ms if ms else None
     line = {"metric": METRIC, "value": value, "unit": "pair interactions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.config, "desc": cfg["desc"], "particles": n, "box": L,
-                       "sub_cycles_per_step": n_c, "pm": use_pm, "dt": dt,
-                       "l2": "inputs larger than L2 (working set ~%.1f GB)" % (n * 100 / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": workload_config(args, world),
             "particle_steps_per_s": psteps,
             "candidate_pairs_per_s": world * cand / secs,
             "within_cutoff_pairs_per_step": within / args.steps,
@@ -681,8 +1034,11 @@ def run_ours(args):
             "replay_bitwise_equal": replay_ok,
             "gpu_launches": st["kernel_launches"],
             "roofline": roofline, "binning_roofline": binning, "e2e": e2e, "clocks": clk,
-            "autotune": {"variant": tuning["chosen"], "force_ms_by_variant": tuning["times_ms"],
-                         "variants": "(blocks/SM, inner loop) = (5,indexed), (4,indexed), (5,pointer-stepped), (4,pointer-stepped)"}}
+            "autotune": {"setting": tuning["chosen"], "variant": tuning["variant"], "item_cap": tuning["item_cap"],
+                         "ms_by_setting": tuning["times_ms"],
+                         "settings": "item cap in %s x variants (blocks/SM, inner loop) = (5,indexed), (4,indexed), "
+                                     "(5,pointer-stepped), (4,pointer-stepped); time = chaining-mesh build + pair "
+                                     "force" % (list(hacc.TUNE_CAPS),)}}
     if not args.no_batch:
         line["batched"] = run_batched(torch, hacc, ctx, split)
         # Zel'dovich box at a step where most particles drift a small part of
@@ -698,25 +1054,29 @@ def run_ours(args):
                                                   n_plain=5, dt=0.02, skin=0.1)
         line["fine_mesh"] = run_fine_mesh(torch, hacc, ctx, split, pos, L)
     if not args.no_served:
-        served = run_served(torch, hacc, ctx, split, rate=50.0, window=args.served_window, cap_s=args.served_cap)
-        served["vs_plain_pairs_per_s"] = served["pair_interactions_per_s"] / (within / secs)
-        line["served"] = served
-        low = run_served(torch, hacc, ctx, split, rate=5.0, window=args.served_window, cap_s=args.served_cap,
-                         seed=6)
-        low["vs_plain_pairs_per_s"] = low["pair_interactions_per_s"] / (within / secs)
-        line["served_low_rate"] = low
+        rates = [float(x) for x in args.served_rates.split(",") if x]
+        rows, sat = run_served_sweep(torch, hacc, ctx, split, rates, args.served_window, args.served_cap, peak,
+                                     variant=tuning["variant"])
+        top = rows[-1]
+        line["served"] = {"sweep": rows, "saturation": sat,
+                          "vs_plain_pairs_per_s": top.get("pair_interactions_per_s_device", 0.0) / (within / secs),
+                          "window_note": "arrival windows of %g s per rate (C5 specifies 60 s), each rate capped at "
+                                         "%g s of wall time" % (args.served_window, args.served_cap)}
+    if not args.no_c1:
+        line["c1"] = run_c1(torch, hacc, ctx, split, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import split as osplit
         sp = osplit.default_split()
         sp["r_cut"] = float(np.float32(sp["r_cut"]))
         sp["eps"] = float(np.float32(sp["eps"]))
-        host = snap_p.cpu().numpy()
+        # the initial conditions of the workload, the state the reference arm samples too
+        host = pos_np
         cb = cpu_oracle_rate(host, L, sp, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": cb["value"], "unit": "pair interactions/s", "cores": cb["threads"],
                                 "kind": "oracle",
-                                "sample": "FP64 short-range force of %d random particles of the warmed-up box "
+                                "sample": "FP64 short-range force of %d random particles of the initial conditions "
                                           "(all %d particles as sources, %.1f s)" % (cb["sample_particles"], n,
-                                                                                      cb["seconds"])}
+                                                                                     cb["seconds"])}
         # the same on one core (a shorter sample)
         import oracle
         all_threads = oracle.threads()
@@ -727,9 +1087,13 @@ def run_ours(args):
             oracle.set_threads(all_threads)
         line["cpu_baseline"]["single_core"] = {"value": c1["value"], "sample_particles": c1["sample_particles"],
                                                "seconds": c1["seconds"]}
+    ctx.close()
+    if not args.no_c3 and world == 1:
+        torch.cuda.empty_cache()
+        line["precision"] = precision_segment(torch, hacc)
+    line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

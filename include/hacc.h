@@ -250,6 +250,14 @@ hacc_status hacc_sr_force_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
                              const int32_t *cell, const float *off_m, float *acc, hacc_stream_t stream);
 /* SKS sub-cycles as hacc_subcycle on (cell, offset) positions, updated in place
  * (streams in FP64, kicks in FP32). */
+/* FP64 diagnostics of a box stored as (cell, offset): out (device, 8 doubles)
+ * receives [0..4] as hacc_diagnostics (sum m v, kinetic energy, short-range
+ * pair potential energy; the pair terms from the offsets moved into one cell
+ * frame, FP32) and [5..7] sum m x over the global positions (c + 1/2) W + off,
+ * formed and summed in FP64 (the centre of mass times the total mass). */
+hacc_status hacc_diagnostics_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                                const int32_t *cell, const float *off_m, const float *vel, double *out,
+                                hacc_stream_t stream);
 hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, int32_t *cell,
                              float *off_m, float *vel, double dt, int32_t n_sub, hacc_stream_t stream);
 
@@ -285,6 +293,34 @@ typedef struct {
 hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
                                 const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,
                                 int32_t n_sub, int32_t use_graph, hacc_stream_t stream);
+
+/* Autotuner of the batched launch (a tuning aid of the library; the paper has
+ * no counterpart).  Bins the batch as it is (no stream) once per work-item cap
+ * in {0 (cell-wide items), 32, 48, 64, 96} (see hacc_set_item_cap) and times
+ * every pair-kernel variant on it in force mode (reps launches after one
+ * warm-up, CUDA events on `stream`); setting k = cap index * HACC_FORCE_VARIANTS
+ * + variant.  The fastest setting is kept for this batch geometry (the boxes'
+ * sides, cells and sizes) and used by later hacc_batch_subcycle and
+ * hacc_batch_tick calls whose non-empty boxes have that geometry (other
+ * batches use the context's variant and item cap); a later tune replaces it.
+ * times_ms (nullable, host, HACC_BATCH_TUNE_SETTINGS doubles) receives each
+ * setting's mean launch time, *chosen (nullable) the setting kept.  The pools
+ * are only read.  Synchronises `stream`.  Every setting sums the same pairs. */
+#define HACC_BATCH_TUNE_SETTINGS 30
+hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes,
+                            const float *pos_pool, const float *vel_pool, int32_t reps, double *times_ms,
+                            int32_t *chosen, hacc_stream_t stream);
+
+/* FP64 diagnostics of every box of a batch (as hacc_diagnostics, per box):
+ * out (device, 5 doubles per entry of `boxes`, including boxes with n = 0,
+ * which get zeros) receives for box b at out[5 b]: sum m v (3), kinetic
+ * energy, short-range pair potential energy of the box's own pairs.  One
+ * batched binning pass and one pair-kernel launch over all boxes; each box's
+ * sums are reduced over its own particles in a fixed order, so they are
+ * bitwise the same alone or in any mix.  The pools are only read. */
+hacc_status hacc_batch_diagnostics(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                                   const hacc_batch_box *boxes, const float *pos_pool, const float *vel_pool,
+                                   double *out, hacc_stream_t stream);
 
 /* One sub-cycle of step boxes[b].dt for every box: stream h/2 first only if
  * HACC_TICK_FIRST (earlier ticks left positions streamed by h/2), kick h,
@@ -375,16 +411,23 @@ size_t hacc_batch_scratch_bytes(const hacc_split *split, int32_t nbox, const hac
 hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_split *split, int64_t n,
                                   const float *pos_m, float *acc, hacc_stream_t stream);
 
-/* Number of pair-kernel variants (register budget x unroll depth). */
-#define HACC_FORCE_VARIANTS 4
+/* Number of pair-kernel variants: register budget (96 or 128 per thread) x
+ * inner loop (indexed, pointer-stepped, packed FP32 pairs). */
+#define HACC_FORCE_VARIANTS 6
 
 /* Autotuner (a tuning aid of the library; the paper has no counterpart):
- * bins pos_m once, times every pair-kernel variant on it (reps launches each,
- * CUDA events on `stream`), and keeps the fastest for this context's later
- * calls.  times_ms (nullable, host, HACC_FORCE_VARIANTS doubles) receives
- * each variant's mean launch time, *chosen (nullable) the variant kept.
- * Synchronises `stream`.  Results of later calls do not depend on the
- * variant (all variants sum the same pairs in the same order). */
+ * for every work-item cap in {0 (cell-wide items), 16, 24, 32, 48} (see
+ * hacc_set_item_cap) times the chaining-mesh build of pos_m with that cap
+ * (binning and the gather into cell order) and every pair-kernel variant on
+ * it (reps launches each after a warm-up, CUDA events on `stream`); setting
+ * k = cap index * HACC_FORCE_VARIANTS + variant costs build + force.  Keeps the
+ * fastest setting's variant and item cap for this context's later calls (as
+ * hacc_set_variant and hacc_set_item_cap would).  times_ms (nullable, host,
+ * HACC_TUNE_SETTINGS doubles) receives each setting's mean time per force
+ * evaluation, *chosen (nullable) the setting kept.  Synchronises `stream`.
+ * Every setting sums the same pairs (the variants in the same order; the caps
+ * in different orders, so results differ by FP32 rounding). */
+#define HACC_TUNE_SETTINGS 30
 hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
                       const float *pos_m, int32_t reps, double *times_ms, int32_t *chosen,
                       hacc_stream_t stream);

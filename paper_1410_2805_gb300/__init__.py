@@ -54,7 +54,11 @@ class _BatchBox(ctypes.Structure):
 
 
 TICK_FIRST, TICK_LAST = 1, 2
-FORCE_VARIANTS = 4   # HACC_FORCE_VARIANTS
+FORCE_VARIANTS = 6   # HACC_FORCE_VARIANTS
+BATCH_TUNE_SETTINGS = 30   # HACC_BATCH_TUNE_SETTINGS
+TUNE_SETTINGS = 30   # HACC_TUNE_SETTINGS
+TUNE_CAPS = (0, 16, 24, 32, 48)   # item caps of the single-box tuner; setting = cap index * 6 + variant
+BATCH_TUNE_CAPS = (0, 32, 48, 64, 96)   # item caps of the batched tuner; setting = cap index * 6 + variant
 
 
 @dataclass
@@ -178,6 +182,10 @@ def lib():
             "hacc_server_tick": (st, [p, p, ctypes.POINTER(_TickInfo), ctypes.POINTER(i64), i32]),
             "hacc_stats_read": (st, [p, ctypes.POINTER(_Stats), ctypes.c_int]),
             "hacc_batch_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox)]),
+            "hacc_batch_tune": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, i32,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
+            "hacc_batch_diagnostics": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, p, p]),
+            "hacc_diagnostics_ci": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -267,15 +275,17 @@ class Context:
         self._check(lib().hacc_ctx_sync(self._h, self._stream(stream)), "hacc_ctx_sync")
 
     def tune(self, box: Box, split, pos, reps: int = 3, stream=None) -> dict:
-        """Time every pair-kernel variant on this machine and keep the fastest."""
+        """Time every (item cap, kernel variant) setting on this machine (chaining-mesh build + pair
+        force) and keep the fastest for this context."""
         _dev_rows(pos, "pos")
         sp = _split_of(split)
-        nv = FORCE_VARIANTS
-        times = (ctypes.c_double * nv)()
+        times = (ctypes.c_double * TUNE_SETTINGS)()
         chosen = ctypes.c_int32(-1)
         self._check(lib().hacc_tune(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0], _ptr(pos),
                                     int(reps), times, ctypes.byref(chosen), self._stream(stream)), "hacc_tune")
-        return dict(chosen=int(chosen.value), times_ms=[float(t) for t in times])
+        k = int(chosen.value)
+        return dict(chosen=k, variant=k % FORCE_VARIANTS, item_cap=TUNE_CAPS[k // FORCE_VARIANTS],
+                    times_ms=[float(t) for t in times])
 
     def batch_subcycle(self, split, boxes, pos_pool, vel_pool, n_sub: int, use_graph: bool = False, stream=None):
         """n_sub SKS sub-cycles of every box of `boxes` (list of BatchBox) in one
@@ -297,7 +307,44 @@ class Context:
         self._check(lib().hacc_batch_tick(self._h, ctypes.byref(sp._c()), len(boxes), arr, _ptr(pos_pool),
                                           _ptr(vel_pool), self._stream(stream)), "hacc_batch_tick")
 
+    def batch_tune(self, split, boxes, pos_pool, vel_pool, reps: int = 2, stream=None) -> dict:
+        """Time every (item cap, variant) setting of the batched pair launch on this batch and keep
+        the fastest for its geometry."""
+        _dev_rows(pos_pool, "pos_pool")
+        _dev_rows(vel_pool, "vel_pool")
+        sp = _split_of(split)
+        times = (ctypes.c_double * BATCH_TUNE_SETTINGS)()
+        chosen = ctypes.c_int32(-1)
+        self._check(lib().hacc_batch_tune(self._h, ctypes.byref(sp._c()), len(boxes), _boxes_c(boxes),
+                                          _ptr(pos_pool), _ptr(vel_pool), int(reps), times, ctypes.byref(chosen),
+                                          self._stream(stream)), "hacc_batch_tune")
+        k = int(chosen.value)
+        return dict(chosen=k, item_cap=BATCH_TUNE_CAPS[k // FORCE_VARIANTS] if k >= 0 else None,
+                    variant=k % FORCE_VARIANTS if k >= 0 else None, times_ms=[float(t) for t in times])
+
+    def batch_diagnostics(self, split, boxes, pos_pool, vel_pool, stream=None):
+        """FP64 (momentum[3], kinetic, potential) of every box: a (len(boxes), 5) float64 CUDA tensor."""
+        import torch
+        _dev_rows(pos_pool, "pos_pool")
+        _dev_rows(vel_pool, "vel_pool")
+        sp = _split_of(split)
+        out = torch.empty((max(1, len(boxes)), 5), dtype=torch.float64, device=pos_pool.device)
+        self._check(lib().hacc_batch_diagnostics(self._h, ctypes.byref(sp._c()), len(boxes), _boxes_c(boxes),
+                                                 _ptr(pos_pool), _ptr(vel_pool), _ptr(out), self._stream(stream)),
+                    "hacc_batch_diagnostics")
+        return out[:len(boxes)]
+
     # ---- precision variant: positions as (cell id, FP32 in-cell offset) -----
+    def diagnostics_ci(self, box: Box, split, cell, off, vel, stream=None):
+        """FP64 (momentum[3], kinetic, potential, sum m x[3]) of (cell, offset) positions: 8 float64."""
+        import torch
+        sp = _split_of(split)
+        out = torch.empty(8, dtype=torch.float64, device=off.device)
+        self._check(lib().hacc_diagnostics_ci(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), cell.shape[0],
+                                              _ptr(cell), _ptr(off), _ptr(vel), _ptr(out), self._stream(stream)),
+                    "hacc_diagnostics_ci")
+        return out
+
     def ci_from_f64(self, box: Box, r_cut: float, pos64, mass=None, stream=None):
         """(n, 3) float64 CUDA positions -> (cell int32 (n,), off_m float32 (n, 4))."""
         import torch

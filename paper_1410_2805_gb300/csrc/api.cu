@@ -108,6 +108,11 @@ hacc_status make_ci_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Ge
     return HACC_OK;
 }
 
+// Item caps the single-box tuner tries (0: cell-wide items of up to kItemMax).
+const int kTuneCaps[] = {0, 16, 24, 32, 48};
+constexpr int kTuneCapCount = 5;
+static_assert(kTuneCapCount * kForceVariants == HACC_TUNE_SETTINGS, "tuner table size");
+
 static double binom(int n, int k) {
     double r = 1.0;
     for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
@@ -443,42 +448,75 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Work w;
     HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
-    HACC_CUDA(bin_build(g, n, reinterpret_cast<const float4 *>(pos_m), nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s,
-                        item_cap_for(ctx, n), ctx->split_max),
-              "binning");
-    HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, e2;
     HACC_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
     HACC_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
-    const int saved = ctx->variant;
+    HACC_CUDA(cudaEventCreate(&e2), "cudaEventCreate");
+    const int saved_v = ctx->variant, saved_cap = ctx->item_cap;
     const bool saved_timing = ctx->timing, saved_counting = ctx->counting;
     ctx->timing = ctx->counting = false;
     double best = 1e300;
-    int best_v = 0;
+    int best_k = 0;
     hacc_status st = HACC_OK;
-    for (int v = 0; v < kForceVariants && st == HACC_OK; ++v) {
-        ctx->variant = v;
-        // forces go to w.P in sorted order (P is free after the gather)
-        st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr, s);
-        if (st != HACC_OK) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == HACC_OK; ++r)
+    const float4 *src = reinterpret_cast<const float4 *>(pos_m);
+    for (int ci = 0; ci < kTuneCapCount && st == HACC_OK; ++ci) {
+        const int cap = kTuneCaps[ci];
+        // the chaining-mesh build with this cap (binning + gather into cell order)
+        auto build = [&]() -> cudaError_t {
+            cudaError_t e = bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s, cap, ctx->split_max);
+            if (e == cudaSuccess) e = gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s);
+            return e;
+        };
+        cudaError_t e = build();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = build();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float bms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&bms, e0, e1);
+        if (e != cudaSuccess) {
+            st = check_cuda(ctx, e, "tuner binning");
+            break;
+        }
+        for (int v = 0; v < kForceVariants && st == HACC_OK; ++v) {
+            ctx->variant = v;
+            // forces go to w.P in sorted order (P is free after the gather)
             st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr, s);
-        cudaEventRecord(e1, s);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) { st = check_cuda(ctx, e, "cudaEventSynchronize"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        double per = (double)ms / reps;
-        if (times_ms) times_ms[v] = per;
-        if (per < best) { best = per; best_v = v; }
+            if (st != HACC_OK) break;
+            cudaEventRecord(e1, s);
+            for (int r = 0; r < reps && st == HACC_OK; ++r)
+                st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr,
+                                      s);
+            cudaEventRecord(e2, s);
+            e = cudaEventSynchronize(e2);
+            if (e != cudaSuccess) {
+                st = check_cuda(ctx, e, "cudaEventSynchronize");
+                break;
+            }
+            float fms = 0.f;
+            cudaEventElapsedTime(&fms, e1, e2);
+            const double per = ((double)bms + (double)fms) / reps;
+            const int k = ci * kForceVariants + v;
+            if (times_ms) times_ms[k] = per;
+            if (per < best) {
+                best = per;
+                best_k = k;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
     ctx->timing = saved_timing;
     ctx->counting = saved_counting;
-    ctx->variant = st == HACC_OK ? best_v : saved;
-    if (chosen) *chosen = ctx->variant;
+    if (st == HACC_OK) {
+        ctx->variant = best_k % kForceVariants;
+        ctx->item_cap = kTuneCaps[best_k / kForceVariants];
+    } else {
+        ctx->variant = saved_v;
+        ctx->item_cap = saved_cap;
+    }
+    if (chosen) *chosen = best_k;
     return st;
 }
 
@@ -704,6 +742,54 @@ hacc_status hacc_sr_force_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
               "binning");
     HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s), "gather");
     return ci_force(ctx, g, fc, &w, kModeForce, reinterpret_cast<float4 *>(acc), nullptr, 0.f, s);
+}
+
+hacc_status hacc_diagnostics_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
+                                const int32_t *cell, const float *off_m, const float *vel, double *out,
+                                hacc_stream_t stream) {
+    HACC_TRY(enter(ctx));
+    if (!split || !out) return set_error(ctx, HACC_EINVAL, "split or out is NULL");
+    Geometry g;
+    HACC_TRY(make_ci_geometry(ctx, box, split->r_cut, &g));
+    ForceConsts fc;
+    HACC_TRY(make_force_consts(ctx, split, g, &fc));
+    HACC_TRY(check_particles(ctx, n, off_m, vel));
+    if (n > 0 && (!cell || !vel)) return set_error(ctx, HACC_EINVAL, "cell or vel is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    HACC_CUDA(cudaMemsetAsync(out, 0, 8 * sizeof(double), s), "clearing diagnostics");
+    if (n == 0) return HACC_OK;
+    Work w;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
+    HACC_CUDA(bin_build_ci(g, n, const_cast<int32_t *>(cell), reinterpret_cast<float4 *>(const_cast<float *>(off_m)),
+                           nullptr, 0.0, w.P, w.b, ctx->d_flags, s),
+              "binning");
+    HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, reinterpret_cast<const float4 *>(vel), w.Vs, nullptr, nullptr, s),
+              "gather");
+    ForceLaunch fl;
+    fl.pos = w.Ps;
+    fl.items = w.b.items;
+    fl.n_items = w.b.n_items;
+    fl.cell_start = w.b.cell_start;
+    fl.work_counter = w.counter;
+    fl.mode = kModePotential;
+    fl.out = nullptr;
+    fl.perm = nullptr;
+    fl.vel = nullptr;
+    fl.pos_next = nullptr;
+    fl.h_kick = 0.f;
+    fl.h_drift = 0.f;
+    fl.phi_out = w.phi;
+    fl.within = nullptr;
+    fl.mass_flag = w.b.mass_flag;
+    fl.flags = ctx->d_flags;
+    fl.cell_offset = true;
+    fl.w = (float)ci_step(g);
+    fl.delta = (float)ci_rem(g);
+    HACC_CUDA(sr_force_launch(g, fc, fl, ctx->num_sms, s), "pair potential (cell/offset)");
+    HACC_CUDA(diag_reduce(n, w.Ps, w.Vs, w.phi, out, s), "diagnostics");
+    HACC_CUDA(diag_mass_moment_ci(n, cell, reinterpret_cast<const float4 *>(off_m), g.nc, ci_step(g), out + 5, s),
+              "mass moment");
+    return HACC_OK;
 }
 
 hacc_status hacc_subcycle_ci(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n, int32_t *cell,

@@ -75,6 +75,7 @@ hacc_status make_plan(hacc_ctx *ctx, const hacc_split *split, int32_t nbox, cons
         d.part_base = (int)n_total;
         d.n = (int)bb.n;
         d.row_off = bb.offset;
+        d.orig = b;
         n_total += bb.n;
         ncell_total += g.ncell;
         if (n_total >= ((int64_t)1 << 31) || ncell_total >= ((int64_t)1 << 31) || bb.offset + bb.n >= ((int64_t)1 << 31))
@@ -107,11 +108,42 @@ hacc_status ensure_staging(hacc_ctx *ctx, size_t bytes) {
     return HACC_OK;
 }
 
+uint64_t mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+// Geometry of a batch as the tuner keys it: every box's side, cells and size.
+uint64_t plan_key(const Plan &pl) {
+    uint64_t key = 0x7475ull;
+    key = mix(key, (uint64_t)pl.nbox);
+    for (const BoxDev &d : pl.base) {
+        uint32_t lb;
+        std::memcpy(&lb, &d.L, 4);
+        key = mix(key, lb);
+        key = mix(key, (uint64_t)d.nc);
+        key = mix(key, (uint64_t)d.n);
+    }
+    return key;
+}
+
+// Launch shape of a batched pass: the tuned one for this batch geometry, else
+// the context's variant and item cap.
+struct Shape {
+    int variant, cap;
+};
+
+Shape batch_shape(const hacc_ctx *ctx, const Plan &pl) {
+    if (ctx->btune_key && ctx->btune_key == plan_key(pl)) return Shape{ctx->btune_variant, ctx->btune_cap};
+    return Shape{ctx->variant, item_cap_for(ctx, pl.n_total)};
+}
+
 // One tick on the device tables `tab` (nbox entries).
 hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const BoxDev *tab, float4 *pos_pool,
                      float4 *vel_pool, const BatchWork &w, cudaStream_t s) {
+    const Shape sh = batch_shape(ctx, pl);
     HACC_CUDA_RETURN(bin_build_batch(pl.nbox, tab, pl.n_total, pl.ncell_total, pos_pool, vel_pool, w.P, w.ID, w.b,
-                                     ctx->d_flags, s, item_cap_for(ctx, pl.n_total), ctx->split_max),
+                                     ctx->d_flags, s, sh.cap, ctx->split_max),
                      "batched binning");
     HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.b.perm, w.P, w.Ps, nullptr, nullptr, w.ID, w.IDs, s), "gather");
     HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.IDs, vel_pool, w.Vs, nullptr, nullptr, nullptr, nullptr, s),
@@ -133,7 +165,7 @@ hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const
     fl.within = ctx->counting ? ctx->d_pairs + 1 : nullptr;
     fl.evaluated = ctx->counting ? ctx->d_pairs + 2 : nullptr;
     fl.mass_flag = w.b.mass_flag;
-    fl.variant = ctx->variant;
+    fl.variant = sh.variant;
     fl.boxes = tab;
     fl.ids = w.IDs;
     fl.pos_pool = pos_pool;
@@ -154,11 +186,6 @@ hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const
     HACC_CUDA_RETURN(sr_force_launch(g, fc, fl, ctx->num_sms, s), "batched pair force");
     ctx->force_launches++;
     return HACC_OK;
-}
-
-uint64_t mix(uint64_t h, uint64_t v) {
-    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
-    return h;
 }
 
 }  // namespace
@@ -231,6 +258,193 @@ extern "C" hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, i
                     w, s);
 }
 
+// Item caps the batched tuner tries (0: cell-wide items of up to kItemMax).
+static const int kTuneCaps[] = {0, 32, 48, 64, 96};
+static_assert(sizeof(kTuneCaps) / sizeof(kTuneCaps[0]) * kForceVariants == HACC_BATCH_TUNE_SETTINGS,
+              "tuner table size");
+
+extern "C" hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                                       const hacc_batch_box *boxes, const float *pos_pool, const float *vel_pool,
+                                       int32_t reps, double *times_ms, int32_t *chosen, hacc_stream_t stream) {
+    HACC_STATUS_RETURN(hacc_enter(ctx));
+    if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
+    if (reps < 1) return set_error(ctx, HACC_EINVAL, "reps must be >= 1");
+    Plan pl;
+    HACC_STATUS_RETURN(make_plan(ctx, split, nbox, boxes, &pl));
+    if (pl.nbox == 0) return HACC_OK;
+    if (!pos_pool || !vel_pool || ((uintptr_t)pos_pool & 15u) || ((uintptr_t)vel_pool & 15u))
+        return set_error(ctx, HACC_EINVAL, "pool arrays NULL or not 16-byte aligned");
+    Geometry g0;
+    g0.Lf = pl.base[0].L;
+    g0.Ld = pl.base[0].Ld;
+    g0.nc = pl.base[0].nc;
+    g0.ncell = (int64_t)g0.nc * g0.nc * g0.nc;
+    g0.inv_w = pl.base[0].inv_w;
+    ForceConsts fc;
+    HACC_STATUS_RETURN(make_force_consts(ctx, split, g0, &fc));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BatchWork w;
+    auto carve = [&](char *base, float4 **acc) {
+        Carver c(base);
+        c.off = carve_batch(base, pl.n_total, pl.ncell_total, pl.nbox, &w);
+        *acc = c.take<float4>(pl.n_total);
+        return c.off + 256;
+    };
+    float4 *acc = nullptr;
+    HACC_STATUS_RETURN(ensure_scratch(ctx, carve(nullptr, &acc), s));
+    carve(ctx->scratch.base, &acc);
+    HACC_STATUS_RETURN(ensure_staging(ctx, sizeof(BoxDev) * pl.nbox));
+    BoxDev *st = static_cast<BoxDev *>(ctx->stage);
+    for (int q = 0; q < pl.nbox; ++q) st[q] = pl.base[q];   // the positions as they are: no stream
+    HACC_CUDA_RETURN(cudaMemcpyAsync(w.tables, st, sizeof(BoxDev) * pl.nbox, cudaMemcpyHostToDevice, s),
+                     "box table upload");
+    HACC_CUDA_RETURN(cudaEventRecord(ctx->stage_event, s), "cudaEventRecord");
+    float4 *pp = const_cast<float4 *>(reinterpret_cast<const float4 *>(pos_pool));
+    float4 *vp = const_cast<float4 *>(reinterpret_cast<const float4 *>(vel_pool));
+    cudaEvent_t e0, e1;
+    HACC_CUDA_RETURN(cudaEventCreate(&e0), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(ctx, HACC_ECUDA, "cudaEventCreate failed");
+    }
+    hacc_status res = HACC_OK;
+    double best = 1e300;
+    int best_k = -1;
+    const int ncap = (int)(sizeof(kTuneCaps) / sizeof(kTuneCaps[0]));
+    for (int ci = 0; ci < ncap && res == HACC_OK; ++ci) {
+        // one binning per item cap; the pair kernel in force mode (results to scratch) per variant
+        cudaError_t e = bin_build_batch(pl.nbox, w.tables, pl.n_total, pl.ncell_total, pp, vp, w.P, w.ID, w.b,
+                                        ctx->d_flags, s, kTuneCaps[ci], ctx->split_max);
+        if (e == cudaSuccess) e = gather_sorted(pl.n_total, w.b.perm, w.P, w.Ps, nullptr, nullptr, w.ID, w.IDs, s);
+        if (e != cudaSuccess) {
+            res = check_cuda(ctx, e, "batched binning (tuner)");
+            break;
+        }
+        for (int v = 0; v < kForceVariants && res == HACC_OK; ++v) {
+            ForceLaunch fl;
+            fl.pos = w.Ps;
+            fl.items = w.b.items;
+            fl.n_items = w.b.n_items;
+            fl.cell_start = w.b.cell_start;
+            fl.work_counter = w.counter;
+            fl.mode = kModeForce;
+            fl.out = acc;
+            fl.perm = nullptr;
+            fl.vel = nullptr;
+            fl.pos_next = nullptr;
+            fl.h_kick = 0.f;
+            fl.h_drift = 0.f;
+            fl.phi_out = nullptr;
+            fl.within = nullptr;
+            fl.mass_flag = w.b.mass_flag;
+            fl.variant = v;
+            fl.boxes = w.tables;
+            fl.ids = w.IDs;
+            fl.flags = ctx->d_flags;
+            e = sr_force_launch(g0, fc, fl, ctx->num_sms, s);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = sr_force_launch(g0, fc, fl, ctx->num_sms, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                res = check_cuda(ctx, e, "pair kernel (tuner)");
+                break;
+            }
+            const int k = ci * kForceVariants + v;
+            const double per = (double)ms / reps;
+            if (times_ms) times_ms[k] = per;
+            if (per < best) {
+                best = per;
+                best_k = k;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (res != HACC_OK) return res;
+    ctx->btune_key = plan_key(pl);
+    ctx->btune_cap = kTuneCaps[best_k / kForceVariants];
+    ctx->btune_variant = best_k % kForceVariants;
+    if (chosen) *chosen = best_k;
+    return HACC_OK;
+}
+
+extern "C" hacc_status hacc_batch_diagnostics(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
+                                              const hacc_batch_box *boxes, const float *pos_pool,
+                                              const float *vel_pool, double *out, hacc_stream_t stream) {
+    HACC_STATUS_RETURN(hacc_enter(ctx));
+    if (!split || (nbox > 0 && !out)) return set_error(ctx, HACC_EINVAL, "split or out is NULL");
+    Plan pl;
+    HACC_STATUS_RETURN(make_plan(ctx, split, nbox, boxes, &pl));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (nbox > 0) HACC_CUDA_RETURN(cudaMemsetAsync(out, 0, sizeof(double) * 5 * nbox, s), "clearing diagnostics");
+    if (pl.nbox == 0) return HACC_OK;
+    if (!pos_pool || !vel_pool || ((uintptr_t)pos_pool & 15u) || ((uintptr_t)vel_pool & 15u))
+        return set_error(ctx, HACC_EINVAL, "pool arrays NULL or not 16-byte aligned");
+    Geometry g0;
+    g0.Lf = pl.base[0].L;
+    g0.Ld = pl.base[0].Ld;
+    g0.nc = pl.base[0].nc;
+    g0.ncell = (int64_t)g0.nc * g0.nc * g0.nc;
+    g0.inv_w = pl.base[0].inv_w;
+    ForceConsts fc;
+    HACC_STATUS_RETURN(make_force_consts(ctx, split, g0, &fc));
+    // scratch: the batched tick's buffers, then the potentials and the partial sums
+    BatchWork w;
+    auto carve = [&](char *base, float **phi, double **partial) {
+        Carver c(base);
+        c.off = carve_batch(base, pl.n_total, pl.ncell_total, pl.nbox, &w);
+        *phi = c.take<float>(pl.n_total);
+        *partial = c.take<double>((size_t)pl.nbox * kDiagParts * 5);
+        return c.off + 256;
+    };
+    float *phi = nullptr;
+    double *partial = nullptr;
+    HACC_STATUS_RETURN(ensure_scratch(ctx, carve(nullptr, &phi, &partial), s));
+    carve(ctx->scratch.base, &phi, &partial);
+    HACC_STATUS_RETURN(ensure_staging(ctx, sizeof(BoxDev) * pl.nbox));
+    BoxDev *st = static_cast<BoxDev *>(ctx->stage);
+    for (int q = 0; q < pl.nbox; ++q) st[q] = pl.base[q];   // no stream, no kick
+    HACC_CUDA_RETURN(cudaMemcpyAsync(w.tables, st, sizeof(BoxDev) * pl.nbox, cudaMemcpyHostToDevice, s),
+                     "box table upload");
+    HACC_CUDA_RETURN(cudaEventRecord(ctx->stage_event, s), "cudaEventRecord");
+    float4 *pp = const_cast<float4 *>(reinterpret_cast<const float4 *>(pos_pool));
+    float4 *vp = const_cast<float4 *>(reinterpret_cast<const float4 *>(vel_pool));
+    // the pools are only read: the binning writes wrapped copies to scratch
+    HACC_CUDA_RETURN(bin_build_batch(pl.nbox, w.tables, pl.n_total, pl.ncell_total, pp, vp, w.P, w.ID, w.b,
+                                     ctx->d_flags, s, item_cap_for(ctx, pl.n_total), ctx->split_max),
+                     "batched binning");
+    HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.b.perm, w.P, w.Ps, nullptr, nullptr, w.ID, w.IDs, s), "gather");
+    HACC_CUDA_RETURN(gather_sorted(pl.n_total, w.IDs, vp, w.Vs, nullptr, nullptr, nullptr, nullptr, s),
+                     "gather velocities");
+    ForceLaunch fl;
+    fl.pos = w.Ps;
+    fl.items = w.b.items;
+    fl.n_items = w.b.n_items;
+    fl.cell_start = w.b.cell_start;
+    fl.work_counter = w.counter;
+    fl.mode = kModePotential;
+    fl.out = nullptr;
+    fl.perm = nullptr;
+    fl.vel = nullptr;
+    fl.pos_next = nullptr;
+    fl.h_kick = 0.f;
+    fl.h_drift = 0.f;
+    fl.phi_out = phi;
+    fl.within = nullptr;
+    fl.mass_flag = w.b.mass_flag;
+    fl.variant = ctx->variant;
+    fl.boxes = w.tables;
+    fl.ids = w.IDs;
+    fl.flags = ctx->d_flags;
+    HACC_CUDA_RETURN(sr_force_launch(g0, fc, fl, ctx->num_sms, s), "batched pair potential");
+    HACC_CUDA_RETURN(diag_reduce_batch(pl.nbox, w.tables, w.b.cell_start, w.Ps, w.Vs, phi, partial, out, s),
+                     "batched diagnostics");
+    return HACC_OK;
+}
+
 extern "C" hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
                                            const hacc_batch_box *boxes, float *pos_pool, float *vel_pool,
                                            int32_t n_sub, int32_t use_graph, hacc_stream_t stream) {
@@ -300,9 +514,10 @@ extern "C" hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *spli
     key = mix(key, (uint64_t)(uintptr_t)pp);
     key = mix(key, (uint64_t)(uintptr_t)vp);
     key = mix(key, (uint64_t)(uintptr_t)ctx->scratch.base);
-    key = mix(key, (uint64_t)ctx->variant);
+    const Shape sh = batch_shape(ctx, pl);
+    key = mix(key, (uint64_t)sh.variant);
     key = mix(key, (uint64_t)ctx->counting);
-    key = mix(key, (uint64_t)ctx->item_cap);
+    key = mix(key, (uint64_t)sh.cap);
     key = mix(key, (uint64_t)ctx->split_max);
     key = mix(key, (uint64_t)(uintptr_t)s);
     if (!ctx->graph_exec || ctx->graph_key != key) {

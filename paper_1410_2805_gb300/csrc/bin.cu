@@ -51,36 +51,59 @@ __device__ __forceinline__ uint8_t sub_cell(float fx, float fy, float fz) {
                      (qx & 1));
 }
 
+// Arrival slot of each lane's particle in its cell (count[c] counts the
+// cell's particles).  Lanes whose cell equals the previous lane's form a run
+// (input rows next to each other often share a cell); the first lane of a
+// run claims the run's slots with one atomic and the others take the slots
+// that follow, in lane order.  Lanes without a particle pass c < 0.  All
+// lanes of the warp must call it.
+__device__ __forceinline__ uint32_t claim_slot(uint32_t *__restrict__ count, int32_t c) {
+    const int lane = threadIdx.x & 31;
+    const int32_t prev = __shfl_up_sync(0xffffffffu, c, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != c || c < 0);
+    const unsigned le = 0xffffffffu >> (31 - lane);              // lanes <= this lane
+    const int head = 31 - __clz(heads & le);                     // first lane of this lane's run
+    const unsigned after = heads & ~le;
+    const int next = after ? __ffs(after) - 1 : 32;              // first lane of the next run
+    uint32_t base = 0;
+    if (head == lane && c >= 0) base = atomicAdd(&count[c], (uint32_t)(next - lane));
+    base = __shfl_sync(0xffffffffu, base, head);
+    return base + (uint32_t)(lane - head);
+}
+
 __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restrict__ src,
                                                  const float4 *__restrict__ vel, float drift,
                                                  float4 *dst, float Lf, float inv_w, double Ld, int nc,
                                                  int32_t *__restrict__ key, int32_t *__restrict__ rank,
                                                  uint32_t *__restrict__ count, int *flags, int *mass_flag,
                                                  uint8_t *__restrict__ sub, const int32_t *__restrict__ sub_level) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float4 p = src[i];
-    if (p.w != src[0].w) atomicOr(mass_flag, 1);
-    if (vel) {
-        float4 v = vel[i];
-        p.x = __fmaf_rn(drift, v.x, p.x);
-        p.y = __fmaf_rn(drift, v.y, p.y);
-        p.z = __fmaf_rn(drift, v.z, p.z);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t c = -1;
+    if (i < n) {
+        float4 p = src[i];
+        if (p.w != src[0].w) atomicOr(mass_flag, 1);
+        if (vel) {
+            float4 v = vel[i];
+            p.x = __fmaf_rn(drift, v.x, p.x);
+            p.y = __fmaf_rn(drift, v.y, p.y);
+            p.z = __fmaf_rn(drift, v.z, p.z);
+        }
+        bool ok = wrap1(p.x, Lf);
+        ok &= wrap1(p.y, Lf);
+        ok &= wrap1(p.z, Lf);
+        if (!ok) atomicOr(flags, kFlagDomain);
+        int cx = cell1(p.x, inv_w, Ld, nc), cy = cell1(p.y, inv_w, Ld, nc), cz = cell1(p.z, inv_w, Ld, nc);
+        c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
+        dst[i] = p;
+        key[i] = c;
+        if (sub) {
+            const uint8_t m = sub_cell(p.x * inv_w - (float)cx, p.y * inv_w - (float)cy, p.z * inv_w - (float)cz);
+            // with kick counts: (kick count, octant), else the 4x4x4 Morton sub-cell
+            sub[i] = sub_level ? (uint8_t)((min(sub_level[i], 31) << 3) | (m >> 3)) : m;
+        }
     }
-    bool ok = wrap1(p.x, Lf);
-    ok &= wrap1(p.y, Lf);
-    ok &= wrap1(p.z, Lf);
-    if (!ok) atomicOr(flags, kFlagDomain);
-    int cx = cell1(p.x, inv_w, Ld, nc), cy = cell1(p.y, inv_w, Ld, nc), cz = cell1(p.z, inv_w, Ld, nc);
-    int32_t c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
-    dst[i] = p;
-    key[i] = c;
-    if (sub) {
-        const uint8_t m = sub_cell(p.x * inv_w - (float)cx, p.y * inv_w - (float)cy, p.z * inv_w - (float)cz);
-        // with kick counts: (kick count, octant), else the 4x4x4 Morton sub-cell
-        sub[i] = sub_level ? (uint8_t)((min(sub_level[i], 31) << 3) | (m >> 3)) : m;
-    }
-    rank[i] = (int32_t)atomicAdd(&count[c], 1u);
+    const uint32_t slot = claim_slot(count, c);
+    if (i < n) rank[i] = (int32_t)slot;
 }
 
 // Lane layout of a work item of n <= 128 particles: 2^lg groups of 32 >> lg
@@ -222,14 +245,14 @@ __global__ void __launch_bounds__(kBlock) k_place(int64_t n, const int32_t *__re
     else perm_tmp[at] = (int32_t)i;
 }
 
-// One warp per cell: the arrival order from the atomics is arbitrary, so each
-// element's final slot is the number of smaller keys in its cell.  The key is
-// the input row (distinct), which gives ascending input row within the cell,
-// or with SUB the pair (Morton sub-cell, input row), which groups the cell's
-// particles by sub-cell; when the cell's rows span less than 2^26 the pair is
-// ranked as one 32-bit key (sub-cell << 26 | row - smallest row).  Cells of
-// more than kBigCell particles go to a list sorted by input row by
-// k_order_big.
+// The arrival order from the atomics is arbitrary, so each element's final
+// slot is the number of smaller keys in its cell.  The key is the input row
+// (distinct), which gives ascending input row within the cell (k_order_rows),
+// or the pair (Morton sub-cell, input row), which groups the cell's particles
+// by sub-cell (k_order_sub, one warp per cell); when the cell's rows span less
+// than 2^24 the pair is ranked as one 32-bit key (sub-cell code << 24 | row -
+// smallest row; codes are below 2^8).  Cells of more than kBigCell particles go to a list sorted by
+// input row by k_order_big.
 constexpr uint32_t kBigCell = 512;
 
 struct RowOf32 {
@@ -240,7 +263,7 @@ struct RowOf64 {
 };
 struct RowOfPacked {
     uint32_t base;
-    __device__ int32_t operator()(uint32_t k) const { return (int32_t)((k & 0x3ffffffu) + base); }
+    __device__ int32_t operator()(uint32_t k) const { return (int32_t)((k & 0xffffffu) + base); }
 };
 
 // Rank of each lane's key among the cell's cnt <= 32 keys (lanes >= cnt hold
@@ -267,13 +290,12 @@ __device__ __forceinline__ void rank_shared(const Key *w, uint32_t cnt, int lane
     }
 }
 
-template <bool SUB>
-__global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t *__restrict__ count,
-                                                   const unsigned long long *__restrict__ packed,
-                                                   int32_t *__restrict__ perm_tmp,
-                                                   int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
-                                                   int *__restrict__ big_count,
-                                                   const unsigned long long *__restrict__ order_tmp) {
+__global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint32_t *__restrict__ count,
+                                                       const unsigned long long *__restrict__ packed,
+                                                       int32_t *__restrict__ perm_tmp,
+                                                       int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
+                                                       int *__restrict__ big_count,
+                                                       const unsigned long long *__restrict__ order_tmp) {
     int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (c >= ncell) return;
@@ -282,26 +304,11 @@ __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t 
     uint32_t s = (uint32_t)(packed[c] & 0xffffffffull);
     if (cnt > kBigCell) {
         // big cells are ordered by row alone, from perm_tmp
-        if (SUB)
-            for (uint32_t e = lane; e < cnt; e += 32) perm_tmp[s + e] = (int32_t)(uint32_t)order_tmp[s + e];
+        for (uint32_t e = lane; e < cnt; e += 32) perm_tmp[s + e] = (int32_t)(uint32_t)order_tmp[s + e];
         if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)c;
         return;
     }
     int32_t *out = perm + s;
-    if (!SUB) {
-        const int32_t *seg = perm_tmp + s;
-        if (cnt <= 32) {
-            rank_warp(lane < (int)cnt ? seg[lane] : 0x7fffffff, (int)cnt, lane, out, RowOf32{});
-            return;
-        }
-        // larger cells: the keys go to shared memory once, then every lane
-        // ranks its keys against them (broadcast reads)
-        __shared__ int32_t ids[kBlock / 32][kBigCell];
-        int32_t *w = ids[threadIdx.x >> 5];
-        for (uint32_t e = lane; e < cnt; e += 32) w[e] = seg[e];
-        rank_shared(w, cnt, lane, out, RowOf32{});
-        return;
-    }
     const unsigned long long *seg = order_tmp + s;
     uint32_t lo = 0xffffffffu, hi = 0u;
     for (uint32_t e = lane; e < cnt; e += 32) {
@@ -313,16 +320,16 @@ __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t 
     hi = __reduce_max_sync(0xffffffffu, hi);
     __shared__ unsigned long long keys[kBlock / 32][kBigCell];
     unsigned long long *w = keys[threadIdx.x >> 5];
-    if (hi - lo < (1u << 26)) {
+    if (hi - lo < (1u << 24)) {
         const RowOfPacked row{lo};
         if (cnt <= 32) {
             uint32_t v = 0xffffffffu;
-            if (lane < (int)cnt) v = ((uint32_t)(seg[lane] >> 32) << 26) | ((uint32_t)seg[lane] - lo);
+            if (lane < (int)cnt) v = ((uint32_t)(seg[lane] >> 32) << 24) | ((uint32_t)seg[lane] - lo);
             rank_warp(v, (int)cnt, lane, out, row);
             return;
         }
         uint32_t *w32 = reinterpret_cast<uint32_t *>(w);
-        for (uint32_t e = lane; e < cnt; e += 32) w32[e] = ((uint32_t)(seg[e] >> 32) << 26) | ((uint32_t)seg[e] - lo);
+        for (uint32_t e = lane; e < cnt; e += 32) w32[e] = ((uint32_t)(seg[e] >> 32) << 24) | ((uint32_t)seg[e] - lo);
         rank_shared(w32, cnt, lane, out, row);
         return;
     }
@@ -332,6 +339,122 @@ __global__ void __launch_bounds__(kBlock) k_order(int64_t ncell, const uint32_t 
     }
     for (uint32_t e = lane; e < cnt; e += 32) w[e] = seg[e];
     rank_shared(w, cnt, lane, out, RowOf64{});
+}
+
+// The in-cell order, a block per 128 consecutive cells: their slots form one
+// range of the placement array, which the block stages into shared memory
+// with coalesced loads (when it holds at most kOrdCap entries; else the warps
+// copy their cells from global memory into a shared buffer of their own).
+// Each warp then ranks one cell at a time: the slot of a key is the number of
+// smaller keys of its cell (keys are distinct), counted from shared memory --
+// for a cell of up to 32 keys in one unrolled pass of 32 independent
+// broadcast loads, for larger cells (up to kBigCell) with 2 or 4 keys per
+// lane on each pass over the cell.  The key is the input row (row order), or with SUB the
+// pair (sub-cell code, input row) as one 32-bit key, code << 24 | row (codes
+// below 2^8, rows below 2^24; larger calls take k_order_sub).  Cells above kBigCell are
+// ordered by input row alone, by k_order_big (with SUB their rows are copied
+// to perm_tmp first).
+constexpr int kOrdCells = 128;
+constexpr int kOrdCap = 6144;
+constexpr int64_t kOrdSubMaxRows = (int64_t)1 << 24;
+
+template <bool SUB>
+__device__ __forceinline__ uint32_t order_key(const int32_t *perm_tmp, const unsigned long long *order_tmp,
+                                              uint32_t e) {
+    if (SUB) {
+        const unsigned long long v = order_tmp[e];
+        return ((uint32_t)(v >> 32) << 24) | (uint32_t)v;
+    }
+    return (uint32_t)perm_tmp[e];
+}
+
+// Ranks of the keys seg[e0 + lane + 32 k], k < J, among the cnt keys of the
+// cell (one pass over the cell feeds J comparisons per load); writes each
+// row to its slot.
+template <int J>
+__device__ __forceinline__ void rank_lanes(const uint32_t *seg, uint32_t cnt, uint32_t e0, int lane, int32_t *out,
+                                           uint32_t row_mask) {
+    uint32_t v[J], r[J];
+#pragma unroll
+    for (int k = 0; k < J; ++k) {
+        const uint32_t e = e0 + lane + 32 * k;
+        v[k] = e < cnt ? seg[e] : 0xffffffffu;
+        r[k] = 0;
+    }
+    for (uint32_t u = 0; u < cnt; ++u) {
+        const uint32_t x = seg[u];
+#pragma unroll
+        for (int k = 0; k < J; ++k) r[k] += x < v[k] ? 1u : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < J; ++k)
+        if (e0 + lane + 32 * k < cnt) out[r[k]] = (int32_t)(v[k] & row_mask);
+}
+
+template <bool SUB>
+__global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint32_t *__restrict__ count,
+                                                        const unsigned long long *__restrict__ packed,
+                                                        int32_t *__restrict__ perm_tmp,
+                                                        int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
+                                                        int *__restrict__ big_count,
+                                                        const unsigned long long *__restrict__ order_tmp) {
+    __shared__ uint32_t keys[kOrdCap];
+    __shared__ uint32_t sortbuf[kBlock / 32][kBigCell];   // a warp's cell when the range is not staged
+    __shared__ uint32_t cstart[kOrdCells], ccount[kOrdCells];
+    const int64_t c0 = (int64_t)blockIdx.x * kOrdCells;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int ncb = ncell - c0 < kOrdCells ? (int)(ncell - c0) : kOrdCells;   // cells of this block (>= 1)
+    if (t < kOrdCells) {
+        uint32_t cnt = 0, st = 0;
+        if (t < ncb) {
+            cnt = count[c0 + t];
+            st = (uint32_t)(packed[c0 + t] & 0xffffffffull);
+            if (cnt > kBigCell) big_list[atomicAdd(big_count, 1)] = (int32_t)(c0 + t);
+        }
+        ccount[t] = cnt;
+        cstart[t] = st;
+    }
+    __syncthreads();
+    const uint32_t S0 = cstart[0], S1 = cstart[ncb - 1] + ccount[ncb - 1];
+    const bool staged = S1 - S0 <= (uint32_t)kOrdCap;
+    if (staged) {
+        for (uint32_t e = t; e < S1 - S0; e += kBlock) keys[e] = order_key<SUB>(perm_tmp, order_tmp, S0 + e);
+        __syncthreads();
+    }
+    const uint32_t row_mask = SUB ? (1u << 24) - 1u : 0xffffffffu;
+    uint32_t *buf = sortbuf[w];
+    for (int q = w; q < ncb; q += kBlock / 32) {
+        const uint32_t cnt = ccount[q];
+        if (cnt == 0) continue;
+        const uint32_t st = cstart[q];
+        if (cnt > kBigCell) {
+            // big cells are ordered by row alone, from perm_tmp
+            if (SUB)
+                for (uint32_t e = lane; e < cnt; e += 32) perm_tmp[st + e] = (int32_t)(uint32_t)order_tmp[st + e];
+            continue;
+        }
+        int32_t *out = perm + st;
+        const uint32_t *seg = keys + (st - S0);
+        if (!staged) {
+            __syncwarp();
+            for (uint32_t e = lane; e < cnt; e += 32) buf[e] = order_key<SUB>(perm_tmp, order_tmp, st + e);
+            __syncwarp();
+            seg = buf;
+        }
+        if (cnt <= 32) {
+            const uint32_t v = lane < (int)cnt ? seg[lane] : 0u;
+            uint32_t r = 0;
+#pragma unroll
+            for (int u = 0; u < 32; ++u) r += (u < (int)cnt && seg[u] < v) ? 1u : 0u;
+            if (lane < (int)cnt) out[r] = (int32_t)(v & row_mask);
+            continue;
+        }
+        if (cnt <= 64) {
+            rank_lanes<2>(seg, cnt, 0, lane, out, row_mask);
+            continue;
+        }
+        for (uint32_t e0 = 0; e0 < cnt; e0 += 4 * 32) rank_lanes<4>(seg, cnt, e0, lane, out, row_mask);
+    }
 }
 
 // Big cells, one block per cell (grid-stride over the list): sort chunks of
@@ -451,36 +574,41 @@ __global__ void __launch_bounds__(kBlock) k_bkey(int64_t n_total, int nbox, cons
                                                   int32_t *__restrict__ id, int32_t *__restrict__ key,
                                                   int32_t *__restrict__ rank, uint32_t *__restrict__ count, int *flags,
                                                   int *mass_flag, uint8_t *__restrict__ sub) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_total) return;
-    int lo = 0, hi = nbox - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (boxes[mid].part_base <= t) lo = mid;
-        else hi = mid - 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t c = -1;
+    if (t < n_total) {
+        int lo = 0, hi = nbox - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (boxes[mid].part_base <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BoxDev bx = boxes[lo];
+        const long long row = bx.row_off + (t - bx.part_base);
+        float4 p = pos_pool[row];
+        if (bx.pre != 0.0f) {
+            float4 v = vel_pool[row];
+            p.x = __fmaf_rn(bx.pre, v.x, p.x);
+            p.y = __fmaf_rn(bx.pre, v.y, p.y);
+            p.z = __fmaf_rn(bx.pre, v.z, p.z);
+        }
+        bool ok = wrap1(p.x, bx.L);
+        ok &= wrap1(p.y, bx.L);
+        ok &= wrap1(p.z, bx.L);
+        if (!ok) atomicOr(flags, kFlagDomain);
+        if (p.w != pos_pool[boxes[0].row_off].w) atomicOr(mass_flag, 1);
+        const int nc = bx.nc;
+        int cx = cell1(p.x, bx.inv_w, bx.Ld, nc), cy = cell1(p.y, bx.inv_w, bx.Ld, nc),
+            cz = cell1(p.z, bx.inv_w, bx.Ld, nc);
+        c = bx.cell_base + (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
+        dst[t] = p;
+        id[t] = (int32_t)row;
+        key[t] = c;
+        if (sub)
+            sub[t] = sub_cell(p.x * bx.inv_w - (float)cx, p.y * bx.inv_w - (float)cy, p.z * bx.inv_w - (float)cz);
     }
-    const BoxDev bx = boxes[lo];
-    const long long row = bx.row_off + (t - bx.part_base);
-    float4 p = pos_pool[row];
-    if (bx.pre != 0.0f) {
-        float4 v = vel_pool[row];
-        p.x = __fmaf_rn(bx.pre, v.x, p.x);
-        p.y = __fmaf_rn(bx.pre, v.y, p.y);
-        p.z = __fmaf_rn(bx.pre, v.z, p.z);
-    }
-    bool ok = wrap1(p.x, bx.L);
-    ok &= wrap1(p.y, bx.L);
-    ok &= wrap1(p.z, bx.L);
-    if (!ok) atomicOr(flags, kFlagDomain);
-    if (p.w != pos_pool[boxes[0].row_off].w) atomicOr(mass_flag, 1);
-    const int nc = bx.nc;
-    int cx = cell1(p.x, bx.inv_w, bx.Ld, nc), cy = cell1(p.y, bx.inv_w, bx.Ld, nc), cz = cell1(p.z, bx.inv_w, bx.Ld, nc);
-    int32_t c = bx.cell_base + (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
-    dst[t] = p;
-    id[t] = (int32_t)row;
-    key[t] = c;
-    if (sub) sub[t] = sub_cell(p.x * bx.inv_w - (float)cx, p.y * bx.inv_w - (float)cy, p.z * bx.inv_w - (float)cz);
-    rank[t] = (int32_t)atomicAdd(&count[c], 1u);
+    const uint32_t slot = claim_slot(count, c);
+    if (t < n_total) rank[t] = (int32_t)slot;
 }
 
 __global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__restrict__ perm,
@@ -886,12 +1014,15 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(b.big_count, 0, sizeof(int), s)) != cudaSuccess) return e;
-        if (sub)
-            k_order<true><<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm,
-                                                                    b.big_list, b.big_count, b.order_tmp);
+        if (sub && n > kOrdSubMaxRows)
+            k_order_sub<<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm,
+                                                                  b.big_list, b.big_count, b.order_tmp);
+        else if (sub)
+            k_order_rows<true><<<blocks_for(ncell, kOrdCells), kBlock, 0, s>>>(
+                ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, b.order_tmp);
         else
-            k_order<false><<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm,
-                                                                     b.big_list, b.big_count, nullptr);
+            k_order_rows<false><<<blocks_for(ncell, kOrdCells), kBlock, 0, s>>>(
+                ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, nullptr);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (n > (int64_t)kBigCell) {

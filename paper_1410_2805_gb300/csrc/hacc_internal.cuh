@@ -69,6 +69,9 @@ struct hacc_ctx {
     cudaEvent_t stage_event = nullptr;
     void *graph_exec = nullptr;
     uint64_t graph_key = 0;
+    // batched launch shape chosen by hacc_batch_tune for one batch geometry
+    uint64_t btune_key = 0;
+    int btune_variant = 0, btune_cap = 0;
     int64_t graph_launches = 0, graph_forces = 0;
     // multi-level steps (api.cu): cached CUDA graph of the event loop, with a
     // conditional rebinning node per event; captured on a stream of its own
@@ -207,7 +210,7 @@ struct BoxDev {
     float h;             // kick factor of this tick
     float pre;           // stream applied before binning (h/2 on a run's first sub-cycle, else 0)
     float post;          // stream after the kick (h, or h/2 on a run's last sub-cycle)
-    float pad;
+    int orig;            // index of the box in the caller's list
 };
 
 // ---- binning (bin.cu) ----------------------------------------------------
@@ -364,7 +367,7 @@ struct ForceLaunch {
     int variant = 0;            // pair-kernel variant (autotuned), 0..kForceVariants-1
 };
 
-constexpr int kForceVariants = 4;
+constexpr int kForceVariants = 6;
 
 cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
                             cudaStream_t s);
@@ -374,6 +377,16 @@ hacc_status timed_force_launch(hacc_ctx *ctx, const Geometry &g, const ForceCons
 // FP64 sums: out[0..2] = sum m v, out[3] = sum m v^2 / 2, out[4] = sum phi.
 cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const float *phi, double *out,
                         cudaStream_t s);
+// The same sums per box of a batch, over each box's range of the cell-sorted
+// arrays (cells cell_base .. cell_base + nc^3 of cell_start), with a fixed
+// partition of every range: out[5 orig + k] for each box (other entries are
+// left as they are); partial: kDiagParts x 5 doubles per box of scratch.
+constexpr int kDiagParts = 32;
+cudaError_t diag_reduce_batch(int nbox, const BoxDev *boxes, const int32_t *cell_start, const float4 *pos,
+                              const float4 *vel, const float *phi, double *partial, double *out, cudaStream_t s);
+// FP64 sum of m x over (cell, offset) positions, x = (c + 1/2) w + off per axis: out[0..2] (added to).
+cudaError_t diag_mass_moment_ci(int64_t n, const int32_t *cell, const float4 *off, int nc, double w, double *out,
+                                cudaStream_t s);
 
 // ---- PM (pm.cu) ------------------------------------------------------------
 // Long-range acceleration G * a_PM at pos; stored to acc (if non-null) and/or

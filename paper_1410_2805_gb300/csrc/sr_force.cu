@@ -86,6 +86,54 @@ struct PairConsts {
     float eps, T, q0, q1, q2, q3, q4, q5;
 };
 
+// Packed FP32 pairs (two lanes' worth of FP32 values in one 64-bit register
+// pair, one f32x2 instruction): each element is rounded exactly as the scalar
+// instruction would round it.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpk2(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// A staged entry: one float4 (x, y, z, m), or with packed pairs (PK) the two
+// float4 (x, x, y, y), (z, z, m, m), so that each j meets two i per
+// instruction without register moves.
+template <bool PK>
+__device__ __forceinline__ void put_entry(float4 *buf, int at, float4 v) {
+    if (PK) {
+        buf[2 * at] = make_float4(v.x, v.x, v.y, v.y);
+        buf[2 * at + 1] = make_float4(v.z, v.z, v.w, v.w);
+    } else {
+        buf[at] = v;
+    }
+}
+template <bool PK>
+__device__ __forceinline__ float4 get_entry(const float4 *buf, int at) {
+    if (PK) {
+        const float4 a = buf[2 * at], b = buf[2 * at + 1];
+        return make_float4(a.x, a.z, b.x, b.z);
+    }
+    return buf[at];
+}
+
 // Accumulate the interaction of one staged j (already image-shifted) with
 // the K i-particles of this lane.  UM: all masses equal (the mass is applied
 // once in the epilogue).
@@ -156,7 +204,79 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
     const int lpg = 32 >> lg;
     const int tg = (nj + G - 1) >> lg;   // entries per group (interleaved)
     constexpr int kUnroll = U == 1 ? (K >= 3 ? 1 : 2) : (K >= 5 ? 1 : (K >= 3 ? 2 : 4));
-    if (U == 2) {
+    if constexpr (U == 3) {
+        // packed pairs: particles 2p and 2p+1 of the lane in one f32x2 register
+        // pair, i coordinates negated (dx = xj + (-xi)), P5 with negated
+        // coefficients (f = r^2 r + (-P5)); the cutoff selects f before
+        // the accumulating FMAs; an odd K leaves particle K-1 scalar.
+        constexpr int KP = K / 2;
+        static_assert(!COUNT && !POT, "the packed loop serves the force and kick forms");
+        uint64_t nx[KP > 0 ? KP : 1], ny[KP > 0 ? KP : 1], nz[KP > 0 ? KP : 1];
+        uint64_t gx[KP > 0 ? KP : 1], gy[KP > 0 ? KP : 1], gz[KP > 0 ? KP : 1];
+#pragma unroll
+        for (int p = 0; p < KP; ++p) {
+            nx[p] = pk2(-xs[2 * p], -xs[2 * p + 1]);
+            ny[p] = pk2(-ys[2 * p], -ys[2 * p + 1]);
+            nz[p] = pk2(-zs[2 * p], -zs[2 * p + 1]);
+            gx[p] = pk2(ax[2 * p], ax[2 * p + 1]);
+            gy[p] = pk2(ay[2 * p], ay[2 * p + 1]);
+            gz[p] = pk2(az[2 * p], az[2 * p + 1]);
+        }
+        const uint64_t e2 = pk2(C.eps, C.eps);
+        const uint64_t m5 = pk2(-C.q5, -C.q5), m4 = pk2(-C.q4, -C.q4), m3 = pk2(-C.q3, -C.q3);
+        const uint64_t m2 = pk2(-C.q2, -C.q2), m1 = pk2(-C.q1, -C.q1), m0 = pk2(-C.q0, -C.q0);
+        const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(buf) + 2 * grp;
+        constexpr int kUnrollP = K >= 4 ? 1 : 2;
+#pragma unroll kUnrollP
+        for (int t = 0; t < tg; ++t) {
+            const ulonglong2 a = bp[2 * (t << lg)], b = bp[2 * (t << lg) + 1];   // (xx, yy), (zz, mm)
+#pragma unroll
+            for (int p = 0; p < KP; ++p) {
+                const uint64_t dx = add2(a.x, nx[p]);
+                const uint64_t dy = add2(a.y, ny[p]);
+                const uint64_t dz = add2(b.x, nz[p]);
+                const uint64_t tt = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+                float t0, t1;
+                unpk2(tt, t0, t1);
+                const uint64_t r = pk2(rsqrt_approx(t0), rsqrt_approx(t1));
+                uint64_t q = fma2(m5, tt, m4);
+                q = fma2(q, tt, m3);
+                q = fma2(q, tt, m2);
+                q = fma2(q, tt, m1);
+                q = fma2(q, tt, m0);
+                uint64_t f = fma2(mul2(r, r), r, q);   // t^(-3/2) - P5
+                if (!UM) f = mul2(f, b.y);
+                float f0, f1;
+                unpk2(f, f0, f1);
+                const bool u0 = EPS0 ? (t0 < C.T && t0 > 0.0f) : (t0 < C.T);
+                const bool u1 = EPS0 ? (t1 < C.T && t1 > 0.0f) : (t1 < C.T);
+                f = pk2(u0 ? f0 : 0.0f, u1 ? f1 : 0.0f);
+                gx[p] = fma2(f, dx, gx[p]);
+                gy[p] = fma2(f, dy, gy[p]);
+                gz[p] = fma2(f, dz, gz[p]);
+            }
+            if (K & 1) {
+                float xj, yj, zj, mj, dummy_hi;
+                unpk2(a.x, xj, dummy_hi);
+                unpk2(a.y, yj, dummy_hi);
+                unpk2(b.x, zj, dummy_hi);
+                unpk2(b.y, mj, dummy_hi);
+                const float4 pj = make_float4(xj, yj, zj, mj);
+                float xl[1] = {xs[K - 1]}, yl[1] = {ys[K - 1]}, zl[1] = {zs[K - 1]};
+                float al[1] = {ax[K - 1]}, bl[1] = {ay[K - 1]}, cl[1] = {az[K - 1]};
+                interact<1, false, false, EPS0, UM>(P, C, pj, -1, iself, lpg, xl, yl, zl, al, bl, cl, cnt);
+                ax[K - 1] = al[0];
+                ay[K - 1] = bl[0];
+                az[K - 1] = cl[0];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < KP; ++p) {
+            unpk2(gx[p], ax[2 * p], ax[2 * p + 1]);
+            unpk2(gy[p], ay[2 * p], ay[2 * p + 1]);
+            unpk2(gz[p], az[2 * p], az[2 * p + 1]);
+        }
+    } else if (U == 2) {
         // pointer-stepped loop over the group's entries g, g+G, ...
         const float4 *q = buf + grp;
         int e = grp;
@@ -281,7 +401,7 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const int at = fill + __popc(m & below);
-                buf[at] = v;
+                put_entry<U == 3>(buf, at, v);
                 if (COUNT || POT) ids[at] = j;
             }
             fill += __popc(m);
@@ -293,7 +413,7 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
         if (nj == 0) break;
         // a short last tile is padded to whole lane groups with far, massless entries
         const int padded = (nj + G - 1) & ~(G - 1);
-        if (nj < tile && lane < padded - nj) buf[nj + lane] = dummy;
+        if (nj < tile && lane < padded - nj) put_entry<U == 3>(buf, nj + lane, dummy);
         __syncwarp();
         run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
         __syncwarp();
@@ -303,12 +423,12 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
         float4 cv = dummy;
         int ci = 0;
         if (lane < rest) {
-            cv = buf[nj + lane];
+            cv = get_entry<U == 3>(buf, nj + lane);
             if (COUNT || POT) ci = ids[nj + lane];
         }
         __syncwarp();
         if (lane < rest) {
-            buf[lane] = cv;
+            put_entry<U == 3>(buf, lane, cv);
             if (COUNT || POT) ids[lane] = ci;
         }
         fill = rest;
@@ -589,7 +709,7 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *id
 // 5 -> 96 registers per thread); U: unroll policy.  The autotuner picks.
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
 __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
-    __shared__ float4 tiles[kWarps][kTileCap];
+    __shared__ float4 tiles[kWarps][kTileCap * (U == 3 ? 2 : 1)];
     __shared__ int tile_ids[COUNT || POT ? kWarps : 1][kTileCap];
     __shared__ int4 runs[kWarps][kMaxRuns];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -618,6 +738,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_sr_force_ci(KParams P) {
         work_loop<false, false, EPS0, false, 0, true>(P, buf, nullptr, rt, lane, 0.0f);
 }
 
+// Pair potential (diagnostics) of the precision variant.
+template <bool EPS0>
+__global__ void __launch_bounds__(kThreads, 5) k_sr_pot_ci(KParams P) {
+    __shared__ float4 tiles[kWarps][kTileCap];
+    __shared__ int tile_ids[kWarps][kTileCap];
+    __shared__ int4 runs[kWarps][kMaxRuns];
+    __shared__ int4 steps[kWarps][kMaxRuns];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const RunTable rt{runs[w], steps[w]};
+    work_loop<false, true, EPS0, false, 0, true>(P, tiles[w], tile_ids[w], rt, lane, 0.0f);
+}
+
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
 cudaError_t launch_one(const KParams &P, int num_sms, cudaStream_t s) {
     int per_sm = 0;
@@ -630,15 +762,24 @@ cudaError_t launch_one(const KParams &P, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Variants 0..kForceVariants-1: (MINB, U) = (5, 0), (4, 0), (5, 2), (4, 2).
+// Variants 0..kForceVariants-1: (MINB, U) = (5, 0), (4, 0), (5, 2), (4, 2),
+// (5, 3), (4, 3); U = 3 is the packed-pair loop, which the counting form
+// replaces by its scalar twin (all variants give bitwise the same forces).
 // (A blocked tile layout, each group's entries contiguous at a padded stride,
 // measured 5% slower than these and changes the summation order.)
 template <bool COUNT, bool POT, bool EPS0>
 cudaError_t launch_variant(const KParams &P, int variant, int num_sms, cudaStream_t s) {
+    if (COUNT && variant >= 4) variant -= 4;
     switch (variant) {
         case 1: return launch_one<COUNT, POT, EPS0, 4, 0>(P, num_sms, s);
         case 2: return launch_one<COUNT, POT, EPS0, 5, 2>(P, num_sms, s);
         case 3: return launch_one<COUNT, POT, EPS0, 4, 2>(P, num_sms, s);
+        case 4:
+            if constexpr (!COUNT && !POT) return launch_one<COUNT, POT, EPS0, 5, 3>(P, num_sms, s);
+            return cudaErrorInvalidValue;
+        case 5:
+            if constexpr (!COUNT && !POT) return launch_one<COUNT, POT, EPS0, 4, 3>(P, num_sms, s);
+            return cudaErrorInvalidValue;
         default: return launch_one<COUNT, POT, EPS0, 5, 0>(P, num_sms, s);
     }
 }
@@ -647,6 +788,7 @@ cudaError_t launch_variant(const KParams &P, int variant, int num_sms, cudaStrea
 
 cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
                             cudaStream_t s) {
+    const bool pot = fl.mode == kModePotential;
     cudaError_t e = cudaMemsetAsync(fl.work_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     KParams P;
@@ -686,9 +828,19 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     P.kick = fl.kick;
     P.delta = fl.delta;
     const bool eps0 = !(fc.eps > 0.0f);
-    const bool pot = fl.mode == kModePotential;
     const bool count = fl.within != nullptr;
     const int v = fl.variant;
+    if (fl.cell_offset && pot) {
+        int per_sm = 0;
+        cudaError_t e = eps0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_pot_ci<true>, kThreads, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_pot_ci<false>, kThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        if (eps0) k_sr_pot_ci<true><<<num_sms * per_sm, kThreads, 0, s>>>(P);
+        else k_sr_pot_ci<false><<<num_sms * per_sm, kThreads, 0, s>>>(P);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (fl.cell_offset) {
         int per_sm = 0;
         cudaError_t e = eps0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sr_force_ci<true>, kThreads, 0)
@@ -735,7 +887,104 @@ __global__ void __launch_bounds__(256) k_diag(int64_t n, const float4 *__restric
         atomicAdd(out + threadIdx.x, x);
     }
 }
+// Per box of a batch: block (box q, part k) sums part k of the box's sorted
+// range (a fixed split into kDiagParts) in a fixed order; k_diag_combine adds
+// the parts of each box in order.  Nothing depends on the other boxes.
+__global__ void __launch_bounds__(256) k_diag_batch(const BoxDev *__restrict__ boxes,
+                                                     const int32_t *__restrict__ cell_start,
+                                                     const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                                                     const float *__restrict__ phi, double *__restrict__ partial) {
+    const int q = blockIdx.x / kDiagParts, part = blockIdx.x % kDiagParts;
+    const BoxDev bx = boxes[q];
+    const int64_t a = cell_start[bx.cell_base];
+    const int64_t len = (int64_t)cell_start[bx.cell_base + bx.nc * bx.nc * bx.nc] - a;
+    const int64_t lo = a + len * part / kDiagParts, hi = a + len * (part + 1) / kDiagParts;
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const float4 v = vel[i];
+        const double m = pos[i].w;
+        s[0] += m * v.x;
+        s[1] += m * v.y;
+        s[2] += m * v.z;
+        s[3] += 0.5 * m * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        s[4] += (double)phi[i];
+    }
+    __shared__ double red[5][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double x = s[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double x = 0;
+        for (int r = 0; r < (int)(blockDim.x / 32); ++r) x += red[threadIdx.x][r];
+        partial[((int64_t)q * kDiagParts + part) * 5 + threadIdx.x] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_diag_combine(int nbox, const BoxDev *__restrict__ boxes,
+                                                       const double *__restrict__ partial, double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nbox * 5) return;
+    const int q = (int)(t / 5), k = (int)(t % 5);
+    double x = 0;
+    for (int part = 0; part < kDiagParts; ++part) x += partial[((int64_t)q * kDiagParts + part) * 5 + k];
+    out[(int64_t)boxes[q].orig * 5 + k] = x;
+}
+
+__global__ void __launch_bounds__(256) k_mass_moment_ci(int64_t n, const int32_t *__restrict__ cell,
+                                                         const float4 *__restrict__ off, int nc, double w,
+                                                         double *out) {
+    double s[3] = {0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cell[i];
+        const float4 o = off[i];
+        const double m = o.w;
+        s[0] += m * fma((double)(c % nc) + 0.5, w, (double)o.x);
+        s[1] += m * fma((double)((c / nc) % nc) + 0.5, w, (double)o.y);
+        s[2] += m * fma((double)(c / (nc * nc)) + 0.5, w, (double)o.z);
+    }
+    __shared__ double red[3][8];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double x = s[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][wp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double x = 0;
+        for (int r = 0; r < (int)(blockDim.x / 32); ++r) x += red[threadIdx.x][r];
+        atomicAdd(out + threadIdx.x, x);
+    }
+}
 }  // namespace
+
+cudaError_t diag_reduce_batch(int nbox, const BoxDev *boxes, const int32_t *cell_start, const float4 *pos,
+                              const float4 *vel, const float *phi, double *partial, double *out, cudaStream_t s) {
+    if (nbox <= 0) return cudaSuccess;
+    k_diag_batch<<<(unsigned)nbox * kDiagParts, 256, 0, s>>>(boxes, cell_start, pos, vel, phi, partial);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_diag_combine<<<(unsigned)((nbox * 5 + 255) / 256), 256, 0, s>>>(nbox, boxes, partial, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t diag_mass_moment_ci(int64_t n, const int32_t *cell, const float4 *off, int nc, double w, double *out,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    k_mass_moment_ci<<<blocks, 256, 0, s>>>(n, cell, off, nc, w, out);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t diag_reduce(int64_t n, const float4 *pos, const float4 *vel, const float *phi, double *out,
                         cudaStream_t s) {

@@ -136,3 +136,74 @@ def test_batch_candidate_count_exact(env, split_params):
         want += oracle.candidates(count_o, nc)
     assert st["candidate_pairs"] == want
     assert st["within_pairs"] <= st["evaluated_pairs"] <= st["candidate_pairs"]
+
+
+def test_every_tuner_setting_sums_the_oracle_pairs(split_params):
+    # Every (item cap, variant) setting the batched tuner can pick: with zero
+    # velocities one tick is a pure kick, so v / h is each particle's force;
+    # it matches the oracle per box, and the pairs inside the cutoff are the
+    # oracle's.
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1410_2805_gb300 as hacc
+    ctx = hacc.Context()
+    sp = dict(split_params)
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    pos, _, boxes = _pool(SPECS[:4], seed0=300)
+    h = 0.01
+    refs = []
+    for (o, n, L) in boxes:
+        a, w = oracle.force_mesh(pos[o:o + n], L, sp)
+        refs.append((a, w))
+    within_oracle = sum(w for _, w in refs)
+    bb = [hacc.BatchBox(L=L, offset=o, n=n, dt=h, flags=hacc.TICK_FIRST | hacc.TICK_LAST) for (o, n, L) in boxes]
+    seen = set()
+    for k in range(hacc.BATCH_TUNE_SETTINGS):
+        cap, variant = hacc.BATCH_TUNE_CAPS[k // hacc.FORCE_VARIANTS], k % hacc.FORCE_VARIANTS
+        ctx.set_item_cap(cap)
+        ctx.set_variant(variant)
+        P = torch.from_numpy(pos).cuda()
+        V = torch.zeros_like(P)
+        ctx.stats_read(reset=True)
+        ctx.stats_enable(counting=True)
+        ctx.batch_tick(sp, bb, P, V)
+        st = ctx.stats_read(reset=True)
+        ctx.stats_enable()
+        ctx.sync()
+        assert abs(st["within_pairs"] - within_oracle) <= 2
+        seen.add(st["candidate_pairs"])
+        v = V.cpu().numpy()[:, :3].astype(np.float64) / np.float64(np.float32(h))
+        for (o, n, L), (a, _) in zip(boxes, refs):
+            rms = np.sqrt((a ** 2).sum(1).mean())
+            assert np.abs(v[o:o + n] - a).max() / rms <= 1e-4, (k, L)
+    assert len(seen) == 1
+    ctx.close()
+
+
+def test_batch_tune_keeps_the_fastest_setting_for_the_geometry(split_params):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1410_2805_gb300 as hacc
+    pos, vel, boxes = _pool(SPECS[:4], seed0=400)
+    bb = [hacc.BatchBox(L=L, offset=o, n=n, dt=0.05) for (o, n, L) in boxes]
+    ctx = hacc.Context()
+    P, V = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
+    res = ctx.batch_tune(split_params, bb, P, V, reps=1)
+    assert 0 <= res["chosen"] < hacc.BATCH_TUNE_SETTINGS and all(t > 0 for t in res["times_ms"])
+    assert res["times_ms"][res["chosen"]] == min(res["times_ms"])
+    assert torch.equal(P, torch.from_numpy(pos).cuda()) and torch.equal(V, torch.from_numpy(vel).cuda())
+    ctx.batch_subcycle(split_params, bb, P, V, n_sub=3, use_graph=True)
+    ctx.sync()
+    # the same steps on a fresh context set to the chosen setting by hand
+    ref = hacc.Context()
+    ref.set_item_cap(res["item_cap"])
+    ref.set_variant(res["variant"])
+    P2, V2 = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
+    ref.batch_subcycle(split_params, bb, P2, V2, n_sub=3, use_graph=True)
+    ref.sync()
+    assert torch.equal(P, P2) and torch.equal(V, V2)
+    ctx.close()
+    ref.close()

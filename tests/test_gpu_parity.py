@@ -239,16 +239,32 @@ def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_para
     p = _dev(torch, pos)
     box = hacc.Box(L=28.0)
     res = ctx.tune(box, split_params, p, reps=1)
-    assert 0 <= res["chosen"] < hacc.FORCE_VARIANTS and all(t > 0 for t in res["times_ms"])
-    assert len(res["times_ms"]) == hacc.FORCE_VARIANTS
-    ref = None
-    for v in range(hacc.FORCE_VARIANTS):
-        ctx.set_variant(v)
-        a = ctx.sr_force(box, split_params, p).clone()
-        if ref is None:
-            ref = a
-        assert torch.equal(a, ref)
-    ctx.set_variant(res["chosen"])
+    assert 0 <= res["chosen"] < hacc.TUNE_SETTINGS and all(t > 0 for t in res["times_ms"])
+    assert len(res["times_ms"]) == hacc.TUNE_SETTINGS and res["times_ms"][res["chosen"]] == min(res["times_ms"])
+    assert res["item_cap"] in hacc.TUNE_CAPS and 0 <= res["variant"] < hacc.FORCE_VARIANTS
+    # the tuned setting is the context's now: the same forces as setting it by hand
+    a_tuned = ctx.sr_force(box, split_params, p).clone()
+    ctx.set_item_cap(res["item_cap"])
+    ctx.set_variant(res["variant"])
+    assert torch.equal(ctx.sr_force(box, split_params, p), a_tuned)
+    # every variant, at every cap the tuner tries, gives bitwise the same forces as variant 0
+    sp = dict(split_params)
+    sp["r_cut"] = float(np.float32(sp["r_cut"]))
+    sp["eps"] = float(np.float32(sp["eps"]))
+    ref_o, _ = oracle.force_mesh(pos, 28.0, sp)
+    rms = np.sqrt((ref_o ** 2).sum(1).mean())
+    for cap in hacc.TUNE_CAPS:
+        ctx.set_item_cap(cap)
+        ref = None
+        for v in range(hacc.FORCE_VARIANTS):
+            ctx.set_variant(v)
+            a = ctx.sr_force(box, split_params, p).clone()
+            if ref is None:
+                ref = a
+                assert np.abs(a.cpu().numpy()[:, :3] - ref_o).max() / rms <= 1e-4
+            assert torch.equal(a, ref)
+    ctx.set_item_cap(-1)
+    ctx.set_variant(0)
 
 
 def test_bin_crowded_cells_bit_exact(torch, hacc, ctx, split_params):
