@@ -295,18 +295,22 @@ hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t 
                                 int32_t n_sub, int32_t use_graph, hacc_stream_t stream);
 
 /* Autotuner of the batched launch (a tuning aid of the library; the paper has
- * no counterpart).  Bins the batch as it is (no stream) once per work-item cap
- * in {0 (cell-wide items), 32, 48, 64, 96} (see hacc_set_item_cap) and times
- * every pair-kernel variant on it in force mode (reps launches after one
- * warm-up, CUDA events on `stream`); setting k = cap index * HACC_FORCE_VARIANTS
- * + variant.  The fastest setting is kept for this batch geometry (the boxes'
- * sides, cells and sizes) and used by later hacc_batch_subcycle and
- * hacc_batch_tick calls whose non-empty boxes have that geometry (other
- * batches use the context's variant and item cap); a later tune replaces it.
- * times_ms (nullable, host, HACC_BATCH_TUNE_SETTINGS doubles) receives each
- * setting's mean launch time, *chosen (nullable) the setting kept.  The pools
- * are only read.  Synchronises `stream`.  Every setting sums the same pairs. */
-#define HACC_BATCH_TUNE_SETTINGS 30
+ * no counterpart).  For every setting of work-item cap in {0 (cell-wide
+ * items), 32, 48, 64, 96} (see hacc_set_item_cap) x queue order (cell order,
+ * largest first; see hacc_set_queue_order) x pair-kernel variant, times whole
+ * batched ticks as hacc_batch_tick runs them (binning, gathers, the kick and
+ * stream pass; each box one sub-cycle of step boxes[b].dt) on scratch copies
+ * of the pools (reps ticks after one warm-up, CUDA events on `stream`);
+ * setting k = (cap index * 2 + order) * HACC_FORCE_VARIANTS + variant.  The
+ * fastest setting is kept for this batch geometry (the boxes' sides, cells and
+ * sizes) and used by later hacc_batch_subcycle and hacc_batch_tick calls whose
+ * non-empty boxes have that geometry (other batches use the context's
+ * settings); a later tune replaces it.  times_ms (nullable, host,
+ * HACC_BATCH_TUNE_SETTINGS doubles) receives each setting's mean tick time,
+ * *chosen (nullable) the setting kept.  The pools are only read (the scratch
+ * grows by 32 bytes per pool row).  Synchronises `stream`.  Every setting sums
+ * the same pairs. */
+#define HACC_BATCH_TUNE_SETTINGS 60
 hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes,
                             const float *pos_pool, const float *vel_pool, int32_t reps, double *times_ms,
                             int32_t *chosen, hacc_stream_t stream);
@@ -395,7 +399,7 @@ size_t hacc_batch_scratch_bytes(const hacc_split *split, int32_t nbox, const hac
  * HACC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  The caller owns pos_m
  * (n rows, not modified) and acc (n rows, receives (ax, ay, az, 0)).
- *   - Limit: about 49 bytes per particle plus 32 bytes per chaining-mesh cell
+ *   - Limit: about 49.3 bytes per particle plus 36 bytes per chaining-mesh cell
  *     must fit in the array (e.g. 262144 particles with up to 100000 cells);
  *     larger problems return HACC_ENOMEM before anything is enqueued.
  *   - Works on the current CUDA device; `stream` must belong to it
@@ -416,18 +420,22 @@ hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_split *split, 
 #define HACC_FORCE_VARIANTS 6
 
 /* Autotuner (a tuning aid of the library; the paper has no counterpart):
- * for every work-item cap in {0 (cell-wide items), 16, 24, 32, 48} (see
- * hacc_set_item_cap) times the chaining-mesh build of pos_m with that cap
- * (binning and the gather into cell order) and every pair-kernel variant on
- * it (reps launches each after a warm-up, CUDA events on `stream`); setting
- * k = cap index * HACC_FORCE_VARIANTS + variant costs build + force.  Keeps the
- * fastest setting's variant and item cap for this context's later calls (as
- * hacc_set_variant and hacc_set_item_cap would).  times_ms (nullable, host,
- * HACC_TUNE_SETTINGS doubles) receives each setting's mean time per force
- * evaluation, *chosen (nullable) the setting kept.  Synchronises `stream`.
- * Every setting sums the same pairs (the variants in the same order; the caps
- * in different orders, so results differ by FP32 rounding). */
-#define HACC_TUNE_SETTINGS 30
+ * for every setting of work-item cap in {0 (cell-wide items), 16, 24, 32, 48}
+ * (see hacc_set_item_cap) x queue order (cell order, largest first; see
+ * hacc_set_queue_order) x pair-kernel variant, times one sub-cycle's work on
+ * pos_m as hacc_subcycle runs it: the chaining-mesh build (binning, gather
+ * into cell order) and the pair-kernel launch that kicks and streams (with
+ * zero velocities of its own; pos_m is not modified), reps times after a
+ * warm-up sub-cycle from pos_m, each timed one binning what the previous one
+ * left in cell order (as the sub-cycle loop does), CUDA events on `stream`; setting k = (cap index * 2 + order) *
+ * HACC_FORCE_VARIANTS + variant.  Keeps the fastest setting for this
+ * context's later calls (as hacc_set_item_cap, hacc_set_queue_order and
+ * hacc_set_variant would).  times_ms (nullable, host, HACC_TUNE_SETTINGS
+ * doubles) receives each setting's mean time, *chosen (nullable) the setting
+ * kept.  Synchronises `stream`.  Every setting sums the same pairs (the
+ * variants and orders in the same order; the caps in different orders, so
+ * results differ by FP32 rounding). */
+#define HACC_TUNE_SETTINGS 60
 hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
                       const float *pos_m, int32_t reps, double *times_ms, int32_t *chosen,
                       hacc_stream_t stream);
@@ -466,6 +474,15 @@ hacc_status hacc_set_stencil(hacc_ctx *ctx, int32_t cells_per_rcut);
  * order differs, so results differ by FP32 rounding).  HACC_EINVAL for a cap
  * outside {-1, 0} and [16, 160] or split_max < 0. */
 hacc_status hacc_set_item_cap(hacc_ctx *ctx, int32_t cap, int32_t split_max);
+
+/* Order in which the pair kernel's warps take the work items of a call of
+ * 2^20 particles or more (single box or batch; smaller calls keep cell order):
+ * heavy_first = 1 takes the largest items first, so that the items of dense
+ * cells do not set the launch's tail; 0 (default) takes them in cell order
+ * (neighbouring items on neighbouring warps, which share their neighbour
+ * particles in the caches).  Results do not depend on it.  HACC_EINVAL for
+ * other values. */
+hacc_status hacc_set_queue_order(hacc_ctx *ctx, int32_t heavy_first);
 
 /* Select the pair-kernel variant by hand (0 <= variant < HACC_FORCE_VARIANTS). */
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant);

@@ -55,10 +55,17 @@ class _BatchBox(ctypes.Structure):
 
 TICK_FIRST, TICK_LAST = 1, 2
 FORCE_VARIANTS = 6   # HACC_FORCE_VARIANTS
-BATCH_TUNE_SETTINGS = 30   # HACC_BATCH_TUNE_SETTINGS
-TUNE_SETTINGS = 30   # HACC_TUNE_SETTINGS
-TUNE_CAPS = (0, 16, 24, 32, 48)   # item caps of the single-box tuner; setting = cap index * 6 + variant
-BATCH_TUNE_CAPS = (0, 32, 48, 64, 96)   # item caps of the batched tuner; setting = cap index * 6 + variant
+BATCH_TUNE_SETTINGS = 60   # HACC_BATCH_TUNE_SETTINGS
+TUNE_SETTINGS = 60   # HACC_TUNE_SETTINGS
+# tuner settings: k = (cap index * 2 + queue order) * FORCE_VARIANTS + variant
+TUNE_CAPS = (0, 16, 24, 32, 48)   # item caps of the single-box tuner
+BATCH_TUNE_CAPS = (0, 32, 48, 64, 96)   # item caps of the batched tuner
+
+
+def tune_setting(k: int, caps) -> dict:
+    """(item cap, heavy_first, variant) of tuner setting k."""
+    return dict(item_cap=caps[k // (2 * FORCE_VARIANTS)], heavy_first=bool((k // FORCE_VARIANTS) % 2),
+                variant=k % FORCE_VARIANTS)
 
 
 @dataclass
@@ -171,6 +178,7 @@ def lib():
             "hacc_tune": (st, [p, ctypes.POINTER(_Box), ctypes.POINTER(_Split), i64, p, i32,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), p]),
             "hacc_set_variant": (st, [p, i32]),
+            "hacc_set_queue_order": (st, [p, i32]),
             "hacc_set_item_cap": (st, [p, i32, i32]),
             "hacc_set_stencil": (st, [p, i32]),
             "hacc_batch_subcycle": (st, [p, ctypes.POINTER(_Split), i32, ctypes.POINTER(_BatchBox), p, p, i32, i32,
@@ -284,8 +292,7 @@ class Context:
         self._check(lib().hacc_tune(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), pos.shape[0], _ptr(pos),
                                     int(reps), times, ctypes.byref(chosen), self._stream(stream)), "hacc_tune")
         k = int(chosen.value)
-        return dict(chosen=k, variant=k % FORCE_VARIANTS, item_cap=TUNE_CAPS[k // FORCE_VARIANTS],
-                    times_ms=[float(t) for t in times])
+        return dict(chosen=k, **tune_setting(k, TUNE_CAPS), times_ms=[float(t) for t in times])
 
     def batch_subcycle(self, split, boxes, pos_pool, vel_pool, n_sub: int, use_graph: bool = False, stream=None):
         """n_sub SKS sub-cycles of every box of `boxes` (list of BatchBox) in one
@@ -319,8 +326,8 @@ class Context:
                                           _ptr(pos_pool), _ptr(vel_pool), int(reps), times, ctypes.byref(chosen),
                                           self._stream(stream)), "hacc_batch_tune")
         k = int(chosen.value)
-        return dict(chosen=k, item_cap=BATCH_TUNE_CAPS[k // FORCE_VARIANTS] if k >= 0 else None,
-                    variant=k % FORCE_VARIANTS if k >= 0 else None, times_ms=[float(t) for t in times])
+        return dict(chosen=k, **(tune_setting(k, BATCH_TUNE_CAPS) if k >= 0 else {}),
+                    times_ms=[float(t) for t in times])
 
     def batch_diagnostics(self, split, boxes, pos_pool, vel_pool, stream=None):
         """FP64 (momentum[3], kinetic, potential) of every box: a (len(boxes), 5) float64 CUDA tensor."""
@@ -378,6 +385,10 @@ class Context:
         self._check(lib().hacc_subcycle_ci(self._h, ctypes.byref(box._c()), ctypes.byref(sp._c()), cell.shape[0],
                                            _ptr(cell), _ptr(off), _ptr(vel), float(dt), int(n_sub),
                                            self._stream(stream)), "hacc_subcycle_ci")
+
+    def set_queue_order(self, heavy_first: bool):
+        """Work-item order of large force launches: largest first (True, default) or cell order."""
+        self._check(lib().hacc_set_queue_order(self._h, int(bool(heavy_first))), "hacc_set_queue_order")
 
     def set_variant(self, variant: int):
         self._check(lib().hacc_set_variant(self._h, int(variant)), "hacc_set_variant")

@@ -111,7 +111,8 @@ hacc_status make_ci_geometry(hacc_ctx *ctx, const hacc_box *box, float r_cut, Ge
 // Item caps the single-box tuner tries (0: cell-wide items of up to kItemMax).
 const int kTuneCaps[] = {0, 16, 24, 32, 48};
 constexpr int kTuneCapCount = 5;
-static_assert(kTuneCapCount * kForceVariants == HACC_TUNE_SETTINGS, "tuner table size");
+constexpr int kTuneSettings = kTuneCapCount * 2 * kForceVariants;   // cap x queue order x variant
+static_assert(kTuneSettings == HACC_TUNE_SETTINGS, "tuner table size");
 
 static double binom(int n, int k) {
     double r = 1.0;
@@ -258,8 +259,12 @@ hacc_status launch_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc
 // The short-range force on sorted positions (w->Ps, cell starts and items in w->b).
 hacc_status run_sorted_force(hacc_ctx *ctx, const Geometry &g, const ForceConsts &fc, Work *w, int mode,
                              float4 *out, const int32_t *perm, float4 *vel, float4 *pos_next, float hk, float hd,
-                             unsigned long long *within, cudaStream_t s) {
+                             unsigned long long *within, cudaStream_t s, int64_t n = 0) {
     ForceLaunch fl;
+    if (ctx->queue_order && n >= kHeavyFirstMinN) {
+        HACC_CUDA(items_heavy_first(w->b, max_items(n, g.ncell), s), "item order");
+        fl.order = w->b.order;
+    }
     fl.pos = w->Ps;
     fl.items = w->b.items;
     fl.n_items = w->b.n_items;
@@ -427,6 +432,13 @@ hacc_status hacc_set_item_cap(hacc_ctx *ctx, int32_t cap, int32_t split_max) {
     return HACC_OK;
 }
 
+hacc_status hacc_set_queue_order(hacc_ctx *ctx, int32_t heavy_first) {
+    HACC_TRY(enter(ctx));
+    if (heavy_first != 0 && heavy_first != 1) return set_error(ctx, HACC_EINVAL, "heavy_first must be 0 or 1");
+    ctx->queue_order = heavy_first;
+    return HACC_OK;
+}
+
 hacc_status hacc_set_variant(hacc_ctx *ctx, int32_t variant) {
     HACC_TRY(enter(ctx));
     if (variant < 0 || variant >= kForceVariants) return set_error(ctx, HACC_EINVAL, "variant out of range");
@@ -446,74 +458,67 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     HACC_TRY(check_particles(ctx, n, pos_m, nullptr));
     if (n == 0) return HACC_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the working set of a sub-cycle, plus zero velocities for it (the kick and
+    // stream then cost what they cost in a sub-cycle).  As in the sub-cycle
+    // loop, each timed sub-cycle bins the positions the previous one left in
+    // cell order (a warm-up sub-cycle from pos_m starts each setting); with
+    // zero velocities and a step of 1e-3 they move by ~1e-6.
     Work w;
-    HACC_TRY(prepare_work(ctx, n, g, false, s, &w));
-    cudaEvent_t e0, e1, e2;
+    HACC_TRY(prepare_work(ctx, n, g, true, s, &w));
+    HACC_CUDA(cudaMemsetAsync(w.V, 0, sizeof(float4) * (size_t)n, s), "clearing tuner velocities");
+    cudaEvent_t e0, e1;
     HACC_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
     HACC_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
-    HACC_CUDA(cudaEventCreate(&e2), "cudaEventCreate");
-    const int saved_v = ctx->variant, saved_cap = ctx->item_cap;
+    const int saved_v = ctx->variant, saved_cap = ctx->item_cap, saved_order = ctx->queue_order;
     const bool saved_timing = ctx->timing, saved_counting = ctx->counting;
     ctx->timing = ctx->counting = false;
     double best = 1e300;
     int best_k = 0;
     hacc_status st = HACC_OK;
     const float4 *src = reinterpret_cast<const float4 *>(pos_m);
-    for (int ci = 0; ci < kTuneCapCount && st == HACC_OK; ++ci) {
-        const int cap = kTuneCaps[ci];
-        // the chaining-mesh build with this cap (binning + gather into cell order)
-        auto build = [&]() -> cudaError_t {
-            cudaError_t e = bin_build(g, n, src, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s, cap, ctx->split_max);
-            if (e == cudaSuccess) e = gather_sorted(n, w.b.perm, w.P, w.Ps, nullptr, nullptr, nullptr, nullptr, s);
-            return e;
-        };
-        cudaError_t e = build();
-        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = build();
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float bms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&bms, e0, e1);
+    const float h = 1e-3f;
+    // one sub-cycle's chaining-mesh build and pair-kernel launch (kick + stream)
+    auto subcycle_work = [&](int cap, bool first) -> hacc_status {
+        HACC_CUDA(bin_build(g, n, first ? src : w.P, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s, cap,
+                            ctx->split_max),
+                  "tuner binning");
+        HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, w.V, w.Vs, nullptr, w.IDs, s), "tuner gather");
+        return run_sorted_force(ctx, g, fc, &w, kModeKickDrift, nullptr, nullptr, w.Vs, w.P, h, h, nullptr, s, n);
+    };
+    for (int k = 0; k < kTuneSettings && st == HACC_OK; ++k) {
+        const int cap = kTuneCaps[k / (2 * kForceVariants)];
+        ctx->queue_order = (k / kForceVariants) % 2;
+        ctx->variant = k % kForceVariants;
+        st = subcycle_work(cap, true);   // warm-up, from pos_m
+        if (st != HACC_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == HACC_OK; ++r) st = subcycle_work(cap, false);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
-            st = check_cuda(ctx, e, "tuner binning");
+            st = check_cuda(ctx, e, "cudaEventSynchronize");
             break;
         }
-        for (int v = 0; v < kForceVariants && st == HACC_OK; ++v) {
-            ctx->variant = v;
-            // forces go to w.P in sorted order (P is free after the gather)
-            st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr, s);
-            if (st != HACC_OK) break;
-            cudaEventRecord(e1, s);
-            for (int r = 0; r < reps && st == HACC_OK; ++r)
-                st = run_sorted_force(ctx, g, fc, &w, kModeForce, w.P, nullptr, nullptr, nullptr, 0.f, 0.f, nullptr,
-                                      s);
-            cudaEventRecord(e2, s);
-            e = cudaEventSynchronize(e2);
-            if (e != cudaSuccess) {
-                st = check_cuda(ctx, e, "cudaEventSynchronize");
-                break;
-            }
-            float fms = 0.f;
-            cudaEventElapsedTime(&fms, e1, e2);
-            const double per = ((double)bms + (double)fms) / reps;
-            const int k = ci * kForceVariants + v;
-            if (times_ms) times_ms[k] = per;
-            if (per < best) {
-                best = per;
-                best_k = k;
-            }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = (double)ms / reps;
+        if (times_ms) times_ms[k] = per;
+        if (per < best) {
+            best = per;
+            best_k = k;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
     ctx->timing = saved_timing;
     ctx->counting = saved_counting;
     if (st == HACC_OK) {
         ctx->variant = best_k % kForceVariants;
-        ctx->item_cap = kTuneCaps[best_k / kForceVariants];
+        ctx->queue_order = (best_k / kForceVariants) % 2;
+        ctx->item_cap = kTuneCaps[best_k / (2 * kForceVariants)];
     } else {
         ctx->variant = saved_v;
+        ctx->queue_order = saved_order;
         ctx->item_cap = saved_cap;
     }
     if (chosen) *chosen = best_k;
@@ -616,7 +621,7 @@ hacc_status hacc_sr_force(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
     }
     if (n > 0)
         HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModeForce, reinterpret_cast<float4 *>(acc), w.b.perm, nullptr,
-                                  nullptr, 0.f, 0.f, within, s));
+                                  nullptr, 0.f, 0.f, within, s, n));
     return HACC_OK;
 }
 
@@ -656,7 +661,7 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
         // kick h, then stream h (fused halves) or h/2 (closing the last sub-cycle);
         // positions of this sub-cycle's sorted order go to w.P
         HACC_TRY(run_sorted_force(ctx, g, fc, &w, kModeKickDrift, nullptr, nullptr, w.Vs, w.P, h, last ? h2 : h,
-                                  nullptr, s));
+                                  nullptr, s, n));
         std::swap(w.V, w.Vs);
         std::swap(w.ID, w.IDs);
     }

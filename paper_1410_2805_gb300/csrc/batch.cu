@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -130,12 +131,13 @@ uint64_t plan_key(const Plan &pl) {
 // Launch shape of a batched pass: the tuned one for this batch geometry, else
 // the context's variant and item cap.
 struct Shape {
-    int variant, cap;
+    int variant, cap, order;
 };
 
 Shape batch_shape(const hacc_ctx *ctx, const Plan &pl) {
-    if (ctx->btune_key && ctx->btune_key == plan_key(pl)) return Shape{ctx->btune_variant, ctx->btune_cap};
-    return Shape{ctx->variant, item_cap_for(ctx, pl.n_total)};
+    if (ctx->btune_key && ctx->btune_key == plan_key(pl))
+        return Shape{ctx->btune_variant, ctx->btune_cap, ctx->btune_order};
+    return Shape{ctx->variant, item_cap_for(ctx, pl.n_total), ctx->queue_order};
 }
 
 // One tick on the device tables `tab` (nbox entries).
@@ -166,6 +168,10 @@ hacc_status run_tick(hacc_ctx *ctx, const ForceConsts &fc, const Plan &pl, const
     fl.evaluated = ctx->counting ? ctx->d_pairs + 2 : nullptr;
     fl.mass_flag = w.b.mass_flag;
     fl.variant = sh.variant;
+    if (sh.order && pl.n_total >= kHeavyFirstMinN) {
+        HACC_CUDA_RETURN(items_heavy_first(w.b, max_items(pl.n_total, pl.ncell_total), s), "item order");
+        fl.order = w.b.order;
+    }
     fl.boxes = tab;
     fl.ids = w.IDs;
     fl.pos_pool = pos_pool;
@@ -258,10 +264,11 @@ extern "C" hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, i
                     w, s);
 }
 
-// Item caps the batched tuner tries (0: cell-wide items of up to kItemMax).
+// Item caps the batched tuner tries (0: cell-wide items of up to kItemMax);
+// setting k = (cap index * 2 + queue order) * kForceVariants + variant.
 static const int kTuneCaps[] = {0, 32, 48, 64, 96};
-static_assert(sizeof(kTuneCaps) / sizeof(kTuneCaps[0]) * kForceVariants == HACC_BATCH_TUNE_SETTINGS,
-              "tuner table size");
+static constexpr int kTuneSettings = (int)(sizeof(kTuneCaps) / sizeof(kTuneCaps[0])) * 2 * kForceVariants;
+static_assert(kTuneSettings == HACC_BATCH_TUNE_SETTINGS, "tuner table size");
 
 extern "C" hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, int32_t nbox,
                                        const hacc_batch_box *boxes, const float *pos_pool, const float *vel_pool,
@@ -274,6 +281,8 @@ extern "C" hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, i
     if (pl.nbox == 0) return HACC_OK;
     if (!pos_pool || !vel_pool || ((uintptr_t)pos_pool & 15u) || ((uintptr_t)vel_pool & 15u))
         return set_error(ctx, HACC_EINVAL, "pool arrays NULL or not 16-byte aligned");
+    for (int b = 0; b < nbox; ++b)
+        if (!std::isfinite(boxes[b].dt)) return set_error(ctx, HACC_EINVAL, "dt must be finite");
     Geometry g0;
     g0.Lf = pl.base[0].L;
     g0.Ld = pl.base[0].Ld;
@@ -283,89 +292,98 @@ extern "C" hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, i
     ForceConsts fc;
     HACC_STATUS_RETURN(make_force_consts(ctx, split, g0, &fc));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the batched tick as it runs, on scratch copies of the pools (the tick
+    // writes its results back to the pool rows)
+    int64_t rows = 0;
+    for (const BoxDev &d : pl.base) rows = std::max<int64_t>(rows, d.row_off + d.n);
     BatchWork w;
-    auto carve = [&](char *base, float4 **acc) {
+    auto carve = [&](char *base, float4 **pc, float4 **vc) {
         Carver c(base);
         c.off = carve_batch(base, pl.n_total, pl.ncell_total, pl.nbox, &w);
-        *acc = c.take<float4>(pl.n_total);
+        *pc = c.take<float4>(rows);
+        *vc = c.take<float4>(rows);
         return c.off + 256;
     };
-    float4 *acc = nullptr;
-    HACC_STATUS_RETURN(ensure_scratch(ctx, carve(nullptr, &acc), s));
-    carve(ctx->scratch.base, &acc);
+    float4 *pc = nullptr, *vc = nullptr;
+    HACC_STATUS_RETURN(ensure_scratch(ctx, carve(nullptr, &pc, &vc), s));
+    carve(ctx->scratch.base, &pc, &vc);
     HACC_STATUS_RETURN(ensure_staging(ctx, sizeof(BoxDev) * pl.nbox));
     BoxDev *st = static_cast<BoxDev *>(ctx->stage);
-    for (int q = 0; q < pl.nbox; ++q) st[q] = pl.base[q];   // the positions as they are: no stream
+    for (int b = 0, q = 0; b < nbox; ++b) {
+        if (boxes[b].n == 0) continue;
+        BoxDev d = pl.base[q];
+        const float h = (float)boxes[b].dt;   // one whole sub-cycle of step dt
+        d.h = h;
+        d.pre = 0.5f * h;
+        d.post = 0.5f * h;
+        st[q++] = d;
+    }
     HACC_CUDA_RETURN(cudaMemcpyAsync(w.tables, st, sizeof(BoxDev) * pl.nbox, cudaMemcpyHostToDevice, s),
                      "box table upload");
     HACC_CUDA_RETURN(cudaEventRecord(ctx->stage_event, s), "cudaEventRecord");
-    float4 *pp = const_cast<float4 *>(reinterpret_cast<const float4 *>(pos_pool));
-    float4 *vp = const_cast<float4 *>(reinterpret_cast<const float4 *>(vel_pool));
     cudaEvent_t e0, e1;
     HACC_CUDA_RETURN(cudaEventCreate(&e0), "cudaEventCreate");
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return set_error(ctx, HACC_ECUDA, "cudaEventCreate failed");
     }
+    const uint64_t key = plan_key(pl);
+    const uint64_t saved_key = ctx->btune_key;
+    const int saved_v = ctx->btune_variant, saved_cap = ctx->btune_cap, saved_order = ctx->btune_order;
+    const bool saved_timing = ctx->timing, saved_counting = ctx->counting;
+    ctx->timing = ctx->counting = false;
     hacc_status res = HACC_OK;
     double best = 1e300;
     int best_k = -1;
-    const int ncap = (int)(sizeof(kTuneCaps) / sizeof(kTuneCaps[0]));
-    for (int ci = 0; ci < ncap && res == HACC_OK; ++ci) {
-        // one binning per item cap; the pair kernel in force mode (results to scratch) per variant
-        cudaError_t e = bin_build_batch(pl.nbox, w.tables, pl.n_total, pl.ncell_total, pp, vp, w.P, w.ID, w.b,
-                                        ctx->d_flags, s, kTuneCaps[ci], ctx->split_max);
-        if (e == cudaSuccess) e = gather_sorted(pl.n_total, w.b.perm, w.P, w.Ps, nullptr, nullptr, w.ID, w.IDs, s);
-        if (e != cudaSuccess) {
-            res = check_cuda(ctx, e, "batched binning (tuner)");
-            break;
-        }
-        for (int v = 0; v < kForceVariants && res == HACC_OK; ++v) {
-            ForceLaunch fl;
-            fl.pos = w.Ps;
-            fl.items = w.b.items;
-            fl.n_items = w.b.n_items;
-            fl.cell_start = w.b.cell_start;
-            fl.work_counter = w.counter;
-            fl.mode = kModeForce;
-            fl.out = acc;
-            fl.perm = nullptr;
-            fl.vel = nullptr;
-            fl.pos_next = nullptr;
-            fl.h_kick = 0.f;
-            fl.h_drift = 0.f;
-            fl.phi_out = nullptr;
-            fl.within = nullptr;
-            fl.mass_flag = w.b.mass_flag;
-            fl.variant = v;
-            fl.boxes = w.tables;
-            fl.ids = w.IDs;
-            fl.flags = ctx->d_flags;
-            e = sr_force_launch(g0, fc, fl, ctx->num_sms, s);   // warm-up
+    const size_t bytes = sizeof(float4) * (size_t)rows;
+    for (int k = 0; k < kTuneSettings && res == HACC_OK; ++k) {
+        ctx->btune_key = key;   // run_tick takes the shape under test
+        ctx->btune_cap = kTuneCaps[k / (2 * kForceVariants)];
+        ctx->btune_order = (k / kForceVariants) % 2;
+        ctx->btune_variant = k % kForceVariants;
+        double total = 0.0;
+        for (int r = 0; r <= reps && res == HACC_OK; ++r) {   // r = 0: warm-up
+            cudaError_t e = cudaMemcpyAsync(pc, pos_pool, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(vc, vel_pool, bytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = sr_force_launch(g0, fc, fl, ctx->num_sms, s);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e != cudaSuccess) {
+                res = check_cuda(ctx, e, "tuner pool copy");
+                break;
+            }
+            res = run_tick(ctx, fc, pl, w.tables, pc, vc, w, s);
+            if (res != HACC_OK) break;
+            e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) {
-                res = check_cuda(ctx, e, "pair kernel (tuner)");
+                res = check_cuda(ctx, e, "tuner timing");
                 break;
             }
-            const int k = ci * kForceVariants + v;
-            const double per = (double)ms / reps;
-            if (times_ms) times_ms[k] = per;
-            if (per < best) {
-                best = per;
-                best_k = k;
-            }
+            if (r > 0) total += ms;
+        }
+        if (res != HACC_OK) break;
+        const double per = total / reps;
+        if (times_ms) times_ms[k] = per;
+        if (per < best) {
+            best = per;
+            best_k = k;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (res != HACC_OK) return res;
-    ctx->btune_key = plan_key(pl);
-    ctx->btune_cap = kTuneCaps[best_k / kForceVariants];
+    ctx->timing = saved_timing;
+    ctx->counting = saved_counting;
+    if (res != HACC_OK) {
+        ctx->btune_key = saved_key;
+        ctx->btune_variant = saved_v;
+        ctx->btune_cap = saved_cap;
+        ctx->btune_order = saved_order;
+        return res;
+    }
+    ctx->btune_key = key;
+    ctx->btune_cap = kTuneCaps[best_k / (2 * kForceVariants)];
+    ctx->btune_order = (best_k / kForceVariants) % 2;
     ctx->btune_variant = best_k % kForceVariants;
     if (chosen) *chosen = best_k;
     return HACC_OK;
@@ -519,6 +537,7 @@ extern "C" hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *spli
     key = mix(key, (uint64_t)ctx->counting);
     key = mix(key, (uint64_t)sh.cap);
     key = mix(key, (uint64_t)ctx->split_max);
+    key = mix(key, (uint64_t)sh.order);
     key = mix(key, (uint64_t)(uintptr_t)s);
     if (!ctx->graph_exec || ctx->graph_key != key) {
         if (ctx->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->graph_exec));

@@ -371,24 +371,84 @@ __device__ __forceinline__ uint32_t order_key(const int32_t *perm_tmp, const uns
 // Ranks of the keys seg[e0 + lane + 32 k], k < J, among the cnt keys of the
 // cell (one pass over the cell feeds J comparisons per load); writes each
 // row to its slot.
-template <int J>
-__device__ __forceinline__ void rank_lanes(const uint32_t *seg, uint32_t cnt, uint32_t e0, int lane, int32_t *out,
+template <int J, class Seg>
+__device__ __forceinline__ void rank_lanes(const Seg &seg, uint32_t cnt, uint32_t e0, int lane, int32_t *out,
                                            uint32_t row_mask) {
     uint32_t v[J], r[J];
 #pragma unroll
     for (int k = 0; k < J; ++k) {
         const uint32_t e = e0 + lane + 32 * k;
-        v[k] = e < cnt ? seg[e] : 0xffffffffu;
+        v[k] = e < cnt ? seg(e) : 0xffffffffu;
         r[k] = 0;
     }
     for (uint32_t u = 0; u < cnt; ++u) {
-        const uint32_t x = seg[u];
+        const uint32_t x = seg(u);
 #pragma unroll
         for (int k = 0; k < J; ++k) r[k] += x < v[k] ? 1u : 0u;
     }
 #pragma unroll
     for (int k = 0; k < J; ++k)
         if (e0 + lane + 32 * k < cnt) out[r[k]] = (int32_t)(v[k] & row_mask);
+}
+
+// Ranking by stretches.  The key pass gives each run of adjacent lanes with
+// the same cell consecutive slots in input-row order, so a cell's slots hold
+// stretches of consecutive keys (key + 1 follows key), and stretches are
+// disjoint intervals of keys: sorting the stretch heads sorts the cell.  A
+// key's slot is the rank of its stretch's head (the lengths of the stretches
+// with smaller heads) plus its offset within the stretch.  Work O(cnt log R +
+// R^2) for R stretches instead of O(cnt^2): R is small when the input rows
+// follow the previous binning's cell order (the sub-cycle loop).  Returns
+// false, doing nothing, when R is above cnt / 4 or kHeads (a lattice-ordered
+// or shuffled input), where counting is cheaper.
+constexpr int kHeads = 128;
+
+template <class Seg>
+__device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int lane, int32_t *out,
+                                               uint32_t row_mask, uint32_t *hkey, uint32_t *hslot, uint32_t *hrank) {
+    const unsigned lt = (1u << lane) - 1u;
+    int R = 0;
+    for (uint32_t e0 = 0; e0 < cnt; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        bool head = false;
+        uint32_t v = 0;
+        if (e < cnt) {
+            v = seg(e);
+            head = e == 0 || v != seg(e - 1) + 1u;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, head);
+        const int at = R + __popc(m & lt);
+        if (head && at < kHeads) {
+            hkey[at] = v;
+            hslot[at] = e;
+        }
+        R += __popc(m);
+    }
+    if (R > kHeads || 4 * (uint32_t)R > cnt) return false;
+    __syncwarp();
+    // rank of each stretch head: the summed lengths of the stretches below it
+    for (int t = lane; t < R; t += 32) {
+        const uint32_t kt = hkey[t];
+        uint32_t r = 0;
+        for (int u = 0; u < R; ++u) {
+            const uint32_t len = (u + 1 < R ? hslot[u + 1] : cnt) - hslot[u];
+            r += hkey[u] < kt ? len : 0u;
+        }
+        hrank[t] = r;
+    }
+    __syncwarp();
+    for (uint32_t e = lane; e < cnt; e += 32) {
+        // the last stretch starting at or before slot e
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (hslot[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        out[hrank[lo] + (e - hslot[lo])] = (int32_t)(seg(e) & row_mask);
+    }
+    __syncwarp();
+    return true;
 }
 
 template <bool SUB>
@@ -399,7 +459,7 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
                                                         int *__restrict__ big_count,
                                                         const unsigned long long *__restrict__ order_tmp) {
     __shared__ uint32_t keys[kOrdCap];
-    __shared__ uint32_t sortbuf[kBlock / 32][kBigCell];   // a warp's cell when the range is not staged
+    __shared__ uint32_t heads[kBlock / 32][3][kHeads];    // a warp's stretch heads: keys, slots, ranks
     __shared__ uint32_t cstart[kOrdCells], ccount[kOrdCells];
     const int64_t c0 = (int64_t)blockIdx.x * kOrdCells;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -422,7 +482,6 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
         __syncthreads();
     }
     const uint32_t row_mask = SUB ? (1u << 24) - 1u : 0xffffffffu;
-    uint32_t *buf = sortbuf[w];
     for (int q = w; q < ncb; q += kBlock / 32) {
         const uint32_t cnt = ccount[q];
         if (cnt == 0) continue;
@@ -434,21 +493,22 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
             continue;
         }
         int32_t *out = perm + st;
-        const uint32_t *seg = keys + (st - S0);
-        if (!staged) {
-            __syncwarp();
-            for (uint32_t e = lane; e < cnt; e += 32) buf[e] = order_key<SUB>(perm_tmp, order_tmp, st + e);
-            __syncwarp();
-            seg = buf;
-        }
+        // the cell's keys in slot order, from the staged range or from global memory
+        const uint32_t *sk = keys + (st - S0);
+        auto seg = [&](uint32_t e) -> uint32_t {
+            return staged ? sk[e] : order_key<SUB>(perm_tmp, order_tmp, st + e);
+        };
         if (cnt <= 32) {
-            const uint32_t v = lane < (int)cnt ? seg[lane] : 0u;
+            const uint32_t v = lane < (int)cnt ? seg(lane) : 0u;
             uint32_t r = 0;
 #pragma unroll
-            for (int u = 0; u < 32; ++u) r += (u < (int)cnt && seg[u] < v) ? 1u : 0u;
+            for (int u = 0; u < 32; ++u) r += (u < (int)cnt && seg(u) < v) ? 1u : 0u;
             if (lane < (int)cnt) out[r] = (int32_t)(v & row_mask);
             continue;
         }
+        // (sub-cell keys rarely run on: a cell's particles spread over 64 sub-cells)
+        if (!SUB && rank_stretches(seg, cnt, lane, out, row_mask, heads[w][0], heads[w][1], heads[w][2]))
+            continue;
         if (cnt <= 64) {
             rank_lanes<2>(seg, cnt, 0, lane, out, row_mask);
             continue;
@@ -962,6 +1022,53 @@ __global__ void __launch_bounds__(kBlock) k_items_kicked(int64_t ncell, const in
 
 inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
 
+// Size class of an item, 0 for the largest: ni >= 150 -> 0, ni < 10 -> 15.
+__device__ __forceinline__ int item_class(int ni) { return kItemClasses - 1 - min(ni / 10, kItemClasses - 1); }
+
+__global__ void __launch_bounds__(kBlock) k_item_hist(const int4 *__restrict__ items, const int32_t *__restrict__ n_items,
+                                                       uint32_t *__restrict__ cls) {
+    __shared__ uint32_t h[kItemClasses];
+    if (threadIdx.x < kItemClasses) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it < *n_items) atomicAdd(&h[item_class(items[it].z)], 1u);
+    __syncthreads();
+    if (threadIdx.x < kItemClasses && h[threadIdx.x]) atomicAdd(&cls[threadIdx.x], h[threadIdx.x]);
+}
+
+// Exclusive scan of the class counts into the class cursors (one warp).
+__global__ void k_item_bases(uint32_t *cls) {
+    const int lane = threadIdx.x;
+    uint32_t v = lane < kItemClasses ? cls[lane] : 0u, x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane < kItemClasses) cls[kItemClasses + lane] = x - v;
+}
+
+// Each block ranks its items per class in shared memory, reserves one range
+// per class from the cursors and writes the item indices there.
+__global__ void __launch_bounds__(kBlock) k_item_place(const int4 *__restrict__ items,
+                                                        const int32_t *__restrict__ n_items, uint32_t *__restrict__ cls,
+                                                        int32_t *__restrict__ order) {
+    __shared__ uint32_t h[kItemClasses], base[kItemClasses];
+    if (threadIdx.x < kItemClasses) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = -1;
+    uint32_t local = 0;
+    if (it < *n_items) {
+        c = item_class(items[it].z);
+        local = atomicAdd(&h[c], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kItemClasses && h[threadIdx.x])
+        base[threadIdx.x] = atomicAdd(&cls[kItemClasses + threadIdx.x], h[threadIdx.x]);
+    __syncthreads();
+    if (c >= 0) order[base[c] + local] = (int32_t)it;
+}
+
 }  // namespace
 
 size_t scan_tmp_elems(int64_t len) {
@@ -976,6 +1083,20 @@ size_t scan_tmp_elems(int64_t len) {
 
 int64_t max_items(int64_t n, int64_t ncell) { return ncell + n / kItemCapMin + 1; }
 
+cudaError_t items_heavy_first(const BinBuffers &b, int64_t max_items, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.item_cls, 0, sizeof(uint32_t) * 2 * kItemClasses, s);
+    if (e != cudaSuccess) return e;
+    k_item_hist<<<blocks_for(max_items), kBlock, 0, s>>>(b.items, b.n_items, b.item_cls);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_item_bases<<<1, 32, 0, s>>>(b.item_cls);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_item_place<<<blocks_for(max_items), kBlock, 0, s>>>(b.items, b.n_items, b.item_cls, b.order);
+    note_launch();
+    return cudaGetLastError();
+}
+
 void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_order) {
     b->key = c.take<int32_t>(n);
     b->rank = c.take<int32_t>(n);
@@ -987,6 +1108,8 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_orde
     b->perm_tmp = c.take<int32_t>(n);
     b->perm = c.take<int32_t>(n);
     b->items = c.take<int4>(max_items(n, ncell));
+    b->order = c.take<int32_t>(max_items(n, ncell));
+    b->item_cls = c.take<uint32_t>(2 * kItemClasses);
     b->n_items = c.take<int32_t>(1);
     b->mass_flag = c.take<int>(1);
     b->big_list = c.take<int32_t>(n / (kBigCell + 1) + 1);

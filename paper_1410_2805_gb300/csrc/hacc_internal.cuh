@@ -57,6 +57,7 @@ struct hacc_ctx {
     int stencil = 1;                          // single-box force paths: 1 (27 cells) or 2 (125 cells of half width)
     int item_cap = -1;                        // work-item cap of the force paths (0: cell-wide items, -1: auto)
     int split_max = hacc::kDefaultSplitMax;   // cells above this many particles keep items of up to kItemMax
+    int queue_order = 0;                      // 1: largest work items first (calls of 2^20 particles and more), 0: cell order
     double force_ms = 0.0;
     double build_ms = 0.0;                    // event-timed chaining-mesh builds (binning + sorted gather)
     int64_t builds = 0;
@@ -71,7 +72,7 @@ struct hacc_ctx {
     uint64_t graph_key = 0;
     // batched launch shape chosen by hacc_batch_tune for one batch geometry
     uint64_t btune_key = 0;
-    int btune_variant = 0, btune_cap = 0;
+    int btune_variant = 0, btune_cap = 0, btune_order = 0;
     int64_t graph_launches = 0, graph_forces = 0;
     // multi-level steps (api.cu): cached CUDA graph of the event loop, with a
     // conditional rebinning node per event; captured on a stream of its own
@@ -225,6 +226,8 @@ struct BinBuffers {
     int32_t *perm_tmp;     // [n]
     int32_t *perm;         // [n]
     int4 *items;           // [max_items]
+    int32_t *order;        // [max_items] work-queue order of the items (heavy_first), or unused
+    uint32_t *item_cls;    // [2 kItemClasses] per-class counts and cursors of heavy_first
     int32_t *n_items;      // [1] device
     int *mass_flag;        // [1] device: nonzero if some mass differs from the first
     int32_t *big_list;     // cells too large for the warp-level ordering
@@ -234,6 +237,13 @@ struct BinBuffers {
 };
 
 size_t scan_tmp_elems(int64_t len);
+// Work-queue order of the force items: largest items first (classes of item
+// size, a counting sort of item indices into b.order), so that the heaviest
+// items do not set the tail of a persistent launch.  Changes which warp takes
+// which item, never a sum.  max_items bounds the device item count.
+constexpr int kItemClasses = 16;
+constexpr int64_t kHeavyFirstMinN = (int64_t)1 << 20;   // smaller calls keep the plain order
+cudaError_t items_heavy_first(const BinBuffers &b, int64_t max_items, cudaStream_t s);
 int64_t max_items(int64_t n, int64_t ncell);
 // sub_order = false leaves out the sub-cell arrays (item_cap must then be 0).
 void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_order = true);
@@ -365,6 +375,7 @@ struct ForceLaunch {
     float w = 0.0f;
     float delta = 0.0f;
     int variant = 0;            // pair-kernel variant (autotuned), 0..kForceVariants-1
+    const int32_t *order = nullptr;   // non-null: the queue takes items[order[k]] (items_heavy_first)
 };
 
 constexpr int kForceVariants = 6;

@@ -46,6 +46,7 @@ constexpr int kThreads = kWarps * 32;
 struct KParams {
     const float4 *__restrict__ pos;
     const int4 *__restrict__ items;
+    const int32_t *__restrict__ order;
     const int32_t *__restrict__ n_items;
     const int32_t *__restrict__ cell_start;
     int *work_counter;
@@ -694,7 +695,7 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *id
         if (lane == 0) it = atomicAdd(P.work_counter, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
-        int4 item = P.items[it];
+        int4 item = P.items[P.order ? P.order[it] : it];
         switch (item.w & 15) {
             case 1: process_item<1, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
             case 2: process_item<2, COUNT, POT, EPS0, UM, U, CI>(P, item, buf, ids, rt, lane, m_uniform); break;
@@ -794,6 +795,7 @@ cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const Forc
     KParams P;
     P.pos = fl.pos;
     P.items = fl.items;
+    P.order = fl.order;
     P.n_items = fl.n_items;
     P.cell_start = fl.cell_start;
     P.work_counter = fl.work_counter;

@@ -161,9 +161,10 @@ def test_every_tuner_setting_sums_the_oracle_pairs(split_params):
     bb = [hacc.BatchBox(L=L, offset=o, n=n, dt=h, flags=hacc.TICK_FIRST | hacc.TICK_LAST) for (o, n, L) in boxes]
     seen = set()
     for k in range(hacc.BATCH_TUNE_SETTINGS):
-        cap, variant = hacc.BATCH_TUNE_CAPS[k // hacc.FORCE_VARIANTS], k % hacc.FORCE_VARIANTS
-        ctx.set_item_cap(cap)
-        ctx.set_variant(variant)
+        setting = hacc.tune_setting(k, hacc.BATCH_TUNE_CAPS)
+        ctx.set_item_cap(setting["item_cap"])
+        ctx.set_variant(setting["variant"])
+        ctx.set_queue_order(setting["heavy_first"])
         P = torch.from_numpy(pos).cuda()
         V = torch.zeros_like(P)
         ctx.stats_read(reset=True)
@@ -201,6 +202,7 @@ def test_batch_tune_keeps_the_fastest_setting_for_the_geometry(split_params):
     ref = hacc.Context()
     ref.set_item_cap(res["item_cap"])
     ref.set_variant(res["variant"])
+    ref.set_queue_order(res["heavy_first"])
     P2, V2 = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
     ref.batch_subcycle(split_params, bb, P2, V2, n_sub=3, use_graph=True)
     ref.sync()

@@ -265,6 +265,7 @@ def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_para
             assert torch.equal(a, ref)
     ctx.set_item_cap(-1)
     ctx.set_variant(0)
+    ctx.set_queue_order(False)
 
 
 def test_bin_crowded_cells_bit_exact(torch, hacc, ctx, split_params):
