@@ -1043,8 +1043,8 @@ def run_ours(args):
                          "heavy_first": tuning["heavy_first"], "ms_by_setting": tuning["times_ms"],
                          "settings": "item cap in %s x queue order (cell, largest first) x variants (blocks/SM, "
                                      "inner loop) = (5,indexed), (4,indexed), (5,pointer-stepped), "
-                                     "(4,pointer-stepped), (5,packed pairs), (4,packed pairs); time = one "
-                                     "sub-cycle's chaining-mesh build + kick-and-stream launch" % (list(hacc.TUNE_CAPS),)}}
+                                     "(4,pointer-stepped); time = one sub-cycle's chaining-mesh build + "
+                                     "kick-and-stream launch" % (list(hacc.TUNE_CAPS),)}}
     if not args.no_batch:
         line["batched"] = run_batched(torch, hacc, ctx, split)
         # Zel'dovich box at a step where most particles drift a small part of

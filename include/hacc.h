@@ -310,7 +310,7 @@ hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t 
  * *chosen (nullable) the setting kept.  The pools are only read (the scratch
  * grows by 32 bytes per pool row).  Synchronises `stream`.  Every setting sums
  * the same pairs. */
-#define HACC_BATCH_TUNE_SETTINGS 60
+#define HACC_BATCH_TUNE_SETTINGS 40
 hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes,
                             const float *pos_pool, const float *vel_pool, int32_t reps, double *times_ms,
                             int32_t *chosen, hacc_stream_t stream);
@@ -416,8 +416,8 @@ hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_split *split, 
                                   const float *pos_m, float *acc, hacc_stream_t stream);
 
 /* Number of pair-kernel variants: register budget (96 or 128 per thread) x
- * inner loop (indexed, pointer-stepped, packed FP32 pairs). */
-#define HACC_FORCE_VARIANTS 6
+ * inner loop (indexed or pointer-stepped); all give bitwise the same forces. */
+#define HACC_FORCE_VARIANTS 4
 
 /* Autotuner (a tuning aid of the library; the paper has no counterpart):
  * for every setting of work-item cap in {0 (cell-wide items), 16, 24, 32, 48}
@@ -435,7 +435,7 @@ hacc_status hacc_sr_force_noalloc(const hacc_box *box, const hacc_split *split, 
  * kept.  Synchronises `stream`.  Every setting sums the same pairs (the
  * variants and orders in the same order; the caps in different orders, so
  * results differ by FP32 rounding). */
-#define HACC_TUNE_SETTINGS 60
+#define HACC_TUNE_SETTINGS 40
 hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
                       const float *pos_m, int32_t reps, double *times_ms, int32_t *chosen,
                       hacc_stream_t stream);

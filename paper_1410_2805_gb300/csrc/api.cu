@@ -480,7 +480,7 @@ hacc_status hacc_tune(hacc_ctx *ctx, const hacc_box *box, const hacc_split *spli
     // one sub-cycle's chaining-mesh build and pair-kernel launch (kick + stream)
     auto subcycle_work = [&](int cap, bool first) -> hacc_status {
         HACC_CUDA(bin_build(g, n, first ? src : w.P, nullptr, 0.0f, w.P, w.b, ctx->d_flags, true, s, cap,
-                            ctx->split_max),
+                            ctx->split_max, nullptr, !first),
                   "tuner binning");
         HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, w.V, w.Vs, nullptr, w.IDs, s), "tuner gather");
         return run_sorted_force(ctx, g, fc, &w, kModeKickDrift, nullptr, nullptr, w.Vs, w.P, h, h, nullptr, s, n);
@@ -652,7 +652,7 @@ hacc_status hacc_subcycle(hacc_ctx *ctx, const hacc_box *box, const hacc_split *
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         HACC_TRY(timing_begin(ctx, s, &ev));
         HACC_CUDA(bin_build(g, n, first ? pos_in : w.P, first ? vel_in : nullptr, h2, w.P, w.b, ctx->d_flags, true,
-                            s, item_cap_for(ctx, n), ctx->split_max),
+                            s, item_cap_for(ctx, n), ctx->split_max, nullptr, !first),
                   "binning");
         HACC_CUDA(gather_sorted(n, w.b.perm, w.P, w.Ps, first ? vel_in : w.V, w.Vs, first ? nullptr : w.ID, w.IDs,
                                 s),

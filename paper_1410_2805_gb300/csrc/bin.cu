@@ -451,13 +451,18 @@ __device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int
     return true;
 }
 
+// row_below: with SUB, cells of at most row_below particles are ordered by
+// row alone (the row is the key's low 24 bits); stretches: try the ranking
+// by stretches for row-ordered cells (the input follows a previous cell
+// order).
 template <bool SUB>
 __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint32_t *__restrict__ count,
                                                         const unsigned long long *__restrict__ packed,
                                                         int32_t *__restrict__ perm_tmp,
                                                         int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
                                                         int *__restrict__ big_count,
-                                                        const unsigned long long *__restrict__ order_tmp) {
+                                                        const unsigned long long *__restrict__ order_tmp,
+                                                        uint32_t row_below, int stretches) {
     __shared__ uint32_t keys[kOrdCap];
     __shared__ uint32_t heads[kBlock / 32][3][kHeads];    // a warp's stretch heads: keys, slots, ranks
     __shared__ uint32_t cstart[kOrdCells], ccount[kOrdCells];
@@ -469,7 +474,6 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
         if (t < ncb) {
             cnt = count[c0 + t];
             st = (uint32_t)(packed[c0 + t] & 0xffffffffull);
-            if (cnt > kBigCell) big_list[atomicAdd(big_count, 1)] = (int32_t)(c0 + t);
         }
         ccount[t] = cnt;
         cstart[t] = st;
@@ -486,17 +490,15 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
         const uint32_t cnt = ccount[q];
         if (cnt == 0) continue;
         const uint32_t st = cstart[q];
-        if (cnt > kBigCell) {
-            // big cells are ordered by row alone, from perm_tmp
-            if (SUB)
-                for (uint32_t e = lane; e < cnt; e += 32) perm_tmp[st + e] = (int32_t)(uint32_t)order_tmp[st + e];
-            continue;
-        }
         int32_t *out = perm + st;
-        // the cell's keys in slot order, from the staged range or from global memory
+        // the cell's keys in slot order, from the staged range or from global
+        // memory; a cell ordered by row alone takes the row bits of the key
+        // (big cells are ordered by row alone too)
         const uint32_t *sk = keys + (st - S0);
+        const bool by_row = !SUB || cnt <= row_below || cnt > kBigCell;
+        const uint32_t kmask = by_row ? row_mask : 0xffffffffu;
         auto seg = [&](uint32_t e) -> uint32_t {
-            return staged ? sk[e] : order_key<SUB>(perm_tmp, order_tmp, st + e);
+            return (staged ? sk[e] : order_key<SUB>(perm_tmp, order_tmp, st + e)) & kmask;
         };
         if (cnt <= 32) {
             const uint32_t v = lane < (int)cnt ? seg(lane) : 0u;
@@ -507,8 +509,16 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
             continue;
         }
         // (sub-cell keys rarely run on: a cell's particles spread over 64 sub-cells)
-        if (!SUB && rank_stretches(seg, cnt, lane, out, row_mask, heads[w][0], heads[w][1], heads[w][2]))
+        if (by_row && stretches &&
+            rank_stretches(seg, cnt, lane, out, row_mask, heads[w][0], heads[w][1], heads[w][2]))
             continue;
+        if (cnt > kBigCell) {
+            // to the big-cell sort by row, from perm_tmp
+            if (SUB)
+                for (uint32_t e = lane; e < cnt; e += 32) perm_tmp[st + e] = (int32_t)(uint32_t)order_tmp[st + e];
+            if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)(c0 + q);
+            continue;
+        }
         if (cnt <= 64) {
             rank_lanes<2>(seg, cnt, 0, lane, out, row_mask);
             continue;
@@ -1126,7 +1136,8 @@ ItemRule item_rule(int item_cap, int split_max) {
 
 // Counting sort by key and work items, shared by the single-box and batched passes.
 cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_items, const BoxDev *boxes, int nbox,
-                     cudaStream_t s, ItemRule cap = {kItemMax, 0xffffffffu}, const uint8_t *sub = nullptr) {
+                     cudaStream_t s, ItemRule cap = {kItemMax, 0xffffffffu}, const uint8_t *sub = nullptr,
+                     uint32_t row_below = 0, bool stretches = false) {
     cudaError_t e;
     k_pack<<<blocks_for(ncell), kBlock, 0, s>>>(ncell, b.count, b.packed, cap);
     note_launch();
@@ -1142,10 +1153,12 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
                                                                   b.big_list, b.big_count, b.order_tmp);
         else if (sub)
             k_order_rows<true><<<blocks_for(ncell, kOrdCells), kBlock, 0, s>>>(
-                ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, b.order_tmp);
+                ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, b.order_tmp, row_below,
+                stretches ? 1 : 0);
         else
             k_order_rows<false><<<blocks_for(ncell, kOrdCells), kBlock, 0, s>>>(
-                ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, nullptr);
+                ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, nullptr, 0u,
+                stretches ? 1 : 0);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (n > (int64_t)kBigCell) {
@@ -1163,7 +1176,7 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
 
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s,
-                      int item_cap, int split_max, const int32_t *sub_level) {
+                      int item_cap, int split_max, const int32_t *sub_level, bool sorted_input) {
     if (item_cap != 0 && (item_cap < kItemCapMin || item_cap > kItemMax)) return cudaErrorInvalidValue;
     if (split_max < 1 || ((item_cap || sub_level) && !b.sub)) return cudaErrorInvalidValue;
     uint8_t *sub = (item_cap || sub_level) ? b.sub : nullptr;
@@ -1176,7 +1189,11 @@ cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const flo
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s, item_rule(item_cap, split_max), sub);
+    // a cell that becomes one work item keeps row order (not with kick counts,
+    // whose order an event's items rely on)
+    const uint32_t row_below = (item_cap && !sub_level) ? (uint32_t)item_cap : 0u;
+    return bin_sort(n, g.ncell, b, make_items, nullptr, 1, s, item_rule(item_cap, split_max), sub, row_below,
+                    sorted_input);
 }
 
 cudaError_t ml_levels(const Geometry &g, int64_t n, const BinBuffers &b, int d, int lmin, int lmax, int32_t *level,
@@ -1239,7 +1256,9 @@ cudaError_t bin_build_batch(int nbox, const BoxDev *boxes, int64_t n_total, int6
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s, item_rule(item_cap, split_max), sub);
+    // as bin_build: a cell that becomes one work item keeps row order
+    return bin_sort(n_total, ncell_total, b, true, boxes, nbox, s, item_rule(item_cap, split_max), sub,
+                    item_cap ? (uint32_t)item_cap : 0u, false);
 }
 
 cudaError_t bin_build_ci(const Geometry &g, int64_t n, int32_t *cell, float4 *off, const float4 *vel, double drift,

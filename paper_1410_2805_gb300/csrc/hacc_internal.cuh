@@ -260,9 +260,15 @@ void carve_bin(Carver &c, int64_t n, int64_t ncell, BinBuffers *b, bool sub_orde
 // kItemMax.  sub_level (nullable, n kick counts aligned with src): order each
 // cell by (kick count, octant, input row) instead, so that the particles of a
 // kick count are consecutive.
+// sorted_input: src is in the cell order of a previous binning of the same
+// particles (the sub-cycle loop), which makes the in-cell ordering cheap.
+// With an item cap (and no kick counts), a cell that becomes one work item
+// keeps input-row order: the sub-cell order only shapes the items of cells
+// that are cut into several.
 cudaError_t bin_build(const Geometry &g, int64_t n, const float4 *src, const float4 *vel, float drift,
                       float4 *dst, const BinBuffers &b, int *d_flags, bool make_items, cudaStream_t s,
-                      int item_cap = 0, int split_max = kDefaultSplitMax, const int32_t *sub_level = nullptr);
+                      int item_cap = 0, int split_max = kDefaultSplitMax, const int32_t *sub_level = nullptr,
+                      bool sorted_input = false);
 
 // Batched binning of nbox boxes (table `boxes` on the device, ascending
 // part_base and cell_base): for every tick-scratch index t the particle at
@@ -378,7 +384,7 @@ struct ForceLaunch {
     const int32_t *order = nullptr;   // non-null: the queue takes items[order[k]] (items_heavy_first)
 };
 
-constexpr int kForceVariants = 6;
+constexpr int kForceVariants = 4;
 
 cudaError_t sr_force_launch(const Geometry &g, const ForceConsts &fc, const ForceLaunch &fl, int num_sms,
                             cudaStream_t s);

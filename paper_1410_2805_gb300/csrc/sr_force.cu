@@ -87,54 +87,6 @@ struct PairConsts {
     float eps, T, q0, q1, q2, q3, q4, q5;
 };
 
-// Packed FP32 pairs (two lanes' worth of FP32 values in one 64-bit register
-// pair, one f32x2 instruction): each element is rounded exactly as the scalar
-// instruction would round it.
-__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void unpk2(uint64_t v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// A staged entry: one float4 (x, y, z, m), or with packed pairs (PK) the two
-// float4 (x, x, y, y), (z, z, m, m), so that each j meets two i per
-// instruction without register moves.
-template <bool PK>
-__device__ __forceinline__ void put_entry(float4 *buf, int at, float4 v) {
-    if (PK) {
-        buf[2 * at] = make_float4(v.x, v.x, v.y, v.y);
-        buf[2 * at + 1] = make_float4(v.z, v.z, v.w, v.w);
-    } else {
-        buf[at] = v;
-    }
-}
-template <bool PK>
-__device__ __forceinline__ float4 get_entry(const float4 *buf, int at) {
-    if (PK) {
-        const float4 a = buf[2 * at], b = buf[2 * at + 1];
-        return make_float4(a.x, a.z, b.x, b.z);
-    }
-    return buf[at];
-}
-
 // Accumulate the interaction of one staged j (already image-shifted) with
 // the K i-particles of this lane.  UM: all masses equal (the mass is applied
 // once in the epilogue).
@@ -205,79 +157,7 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
     const int lpg = 32 >> lg;
     const int tg = (nj + G - 1) >> lg;   // entries per group (interleaved)
     constexpr int kUnroll = U == 1 ? (K >= 3 ? 1 : 2) : (K >= 5 ? 1 : (K >= 3 ? 2 : 4));
-    if constexpr (U == 3) {
-        // packed pairs: particles 2p and 2p+1 of the lane in one f32x2 register
-        // pair, i coordinates negated (dx = xj + (-xi)), P5 with negated
-        // coefficients (f = r^2 r + (-P5)); the cutoff selects f before
-        // the accumulating FMAs; an odd K leaves particle K-1 scalar.
-        constexpr int KP = K / 2;
-        static_assert(!COUNT && !POT, "the packed loop serves the force and kick forms");
-        uint64_t nx[KP > 0 ? KP : 1], ny[KP > 0 ? KP : 1], nz[KP > 0 ? KP : 1];
-        uint64_t gx[KP > 0 ? KP : 1], gy[KP > 0 ? KP : 1], gz[KP > 0 ? KP : 1];
-#pragma unroll
-        for (int p = 0; p < KP; ++p) {
-            nx[p] = pk2(-xs[2 * p], -xs[2 * p + 1]);
-            ny[p] = pk2(-ys[2 * p], -ys[2 * p + 1]);
-            nz[p] = pk2(-zs[2 * p], -zs[2 * p + 1]);
-            gx[p] = pk2(ax[2 * p], ax[2 * p + 1]);
-            gy[p] = pk2(ay[2 * p], ay[2 * p + 1]);
-            gz[p] = pk2(az[2 * p], az[2 * p + 1]);
-        }
-        const uint64_t e2 = pk2(C.eps, C.eps);
-        const uint64_t m5 = pk2(-C.q5, -C.q5), m4 = pk2(-C.q4, -C.q4), m3 = pk2(-C.q3, -C.q3);
-        const uint64_t m2 = pk2(-C.q2, -C.q2), m1 = pk2(-C.q1, -C.q1), m0 = pk2(-C.q0, -C.q0);
-        const ulonglong2 *bp = reinterpret_cast<const ulonglong2 *>(buf) + 2 * grp;
-        constexpr int kUnrollP = K >= 4 ? 1 : 2;
-#pragma unroll kUnrollP
-        for (int t = 0; t < tg; ++t) {
-            const ulonglong2 a = bp[2 * (t << lg)], b = bp[2 * (t << lg) + 1];   // (xx, yy), (zz, mm)
-#pragma unroll
-            for (int p = 0; p < KP; ++p) {
-                const uint64_t dx = add2(a.x, nx[p]);
-                const uint64_t dy = add2(a.y, ny[p]);
-                const uint64_t dz = add2(b.x, nz[p]);
-                const uint64_t tt = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
-                float t0, t1;
-                unpk2(tt, t0, t1);
-                const uint64_t r = pk2(rsqrt_approx(t0), rsqrt_approx(t1));
-                uint64_t q = fma2(m5, tt, m4);
-                q = fma2(q, tt, m3);
-                q = fma2(q, tt, m2);
-                q = fma2(q, tt, m1);
-                q = fma2(q, tt, m0);
-                uint64_t f = fma2(mul2(r, r), r, q);   // t^(-3/2) - P5
-                if (!UM) f = mul2(f, b.y);
-                float f0, f1;
-                unpk2(f, f0, f1);
-                const bool u0 = EPS0 ? (t0 < C.T && t0 > 0.0f) : (t0 < C.T);
-                const bool u1 = EPS0 ? (t1 < C.T && t1 > 0.0f) : (t1 < C.T);
-                f = pk2(u0 ? f0 : 0.0f, u1 ? f1 : 0.0f);
-                gx[p] = fma2(f, dx, gx[p]);
-                gy[p] = fma2(f, dy, gy[p]);
-                gz[p] = fma2(f, dz, gz[p]);
-            }
-            if (K & 1) {
-                float xj, yj, zj, mj, dummy_hi;
-                unpk2(a.x, xj, dummy_hi);
-                unpk2(a.y, yj, dummy_hi);
-                unpk2(b.x, zj, dummy_hi);
-                unpk2(b.y, mj, dummy_hi);
-                const float4 pj = make_float4(xj, yj, zj, mj);
-                float xl[1] = {xs[K - 1]}, yl[1] = {ys[K - 1]}, zl[1] = {zs[K - 1]};
-                float al[1] = {ax[K - 1]}, bl[1] = {ay[K - 1]}, cl[1] = {az[K - 1]};
-                interact<1, false, false, EPS0, UM>(P, C, pj, -1, iself, lpg, xl, yl, zl, al, bl, cl, cnt);
-                ax[K - 1] = al[0];
-                ay[K - 1] = bl[0];
-                az[K - 1] = cl[0];
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < KP; ++p) {
-            unpk2(gx[p], ax[2 * p], ax[2 * p + 1]);
-            unpk2(gy[p], ay[2 * p], ay[2 * p + 1]);
-            unpk2(gz[p], az[2 * p], az[2 * p + 1]);
-        }
-    } else if (U == 2) {
+    if (U == 2) {
         // pointer-stepped loop over the group's entries g, g+G, ...
         const float4 *q = buf + grp;
         int e = grp;
@@ -402,7 +282,7 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const int at = fill + __popc(m & below);
-                put_entry<U == 3>(buf, at, v);
+                buf[at] = v;
                 if (COUNT || POT) ids[at] = j;
             }
             fill += __popc(m);
@@ -414,7 +294,7 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
         if (nj == 0) break;
         // a short last tile is padded to whole lane groups with far, massless entries
         const int padded = (nj + G - 1) & ~(G - 1);
-        if (nj < tile && lane < padded - nj) put_entry<U == 3>(buf, nj + lane, dummy);
+        if (nj < tile && lane < padded - nj) buf[nj + lane] = dummy;
         __syncwarp();
         run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
         __syncwarp();
@@ -424,12 +304,12 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
         float4 cv = dummy;
         int ci = 0;
         if (lane < rest) {
-            cv = get_entry<U == 3>(buf, nj + lane);
+            cv = buf[nj + lane];
             if (COUNT || POT) ci = ids[nj + lane];
         }
         __syncwarp();
         if (lane < rest) {
-            put_entry<U == 3>(buf, lane, cv);
+            buf[lane] = cv;
             if (COUNT || POT) ids[lane] = ci;
         }
         fill = rest;
@@ -710,7 +590,7 @@ __device__ __forceinline__ void work_loop(const KParams &P, float4 *buf, int *id
 // 5 -> 96 registers per thread); U: unroll policy.  The autotuner picks.
 template <bool COUNT, bool POT, bool EPS0, int MINB, int U>
 __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
-    __shared__ float4 tiles[kWarps][kTileCap * (U == 3 ? 2 : 1)];
+    __shared__ float4 tiles[kWarps][kTileCap];
     __shared__ int tile_ids[COUNT || POT ? kWarps : 1][kTileCap];
     __shared__ int4 runs[kWarps][kMaxRuns];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -763,24 +643,16 @@ cudaError_t launch_one(const KParams &P, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Variants 0..kForceVariants-1: (MINB, U) = (5, 0), (4, 0), (5, 2), (4, 2),
-// (5, 3), (4, 3); U = 3 is the packed-pair loop, which the counting form
-// replaces by its scalar twin (all variants give bitwise the same forces).
+// Variants 0..kForceVariants-1: (MINB, U) = (5, 0), (4, 0), (5, 2), (4, 2);
+// all give bitwise the same forces.
 // (A blocked tile layout, each group's entries contiguous at a padded stride,
 // measured 5% slower than these and changes the summation order.)
 template <bool COUNT, bool POT, bool EPS0>
 cudaError_t launch_variant(const KParams &P, int variant, int num_sms, cudaStream_t s) {
-    if (COUNT && variant >= 4) variant -= 4;
     switch (variant) {
         case 1: return launch_one<COUNT, POT, EPS0, 4, 0>(P, num_sms, s);
         case 2: return launch_one<COUNT, POT, EPS0, 5, 2>(P, num_sms, s);
         case 3: return launch_one<COUNT, POT, EPS0, 4, 2>(P, num_sms, s);
-        case 4:
-            if constexpr (!COUNT && !POT) return launch_one<COUNT, POT, EPS0, 5, 3>(P, num_sms, s);
-            return cudaErrorInvalidValue;
-        case 5:
-            if constexpr (!COUNT && !POT) return launch_one<COUNT, POT, EPS0, 4, 3>(P, num_sms, s);
-            return cudaErrorInvalidValue;
         default: return launch_one<COUNT, POT, EPS0, 5, 0>(P, num_sms, s);
     }
 }

@@ -238,6 +238,7 @@ def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_para
     pos = synth.blob_mixture(20000, 28.0, seed=61)
     p = _dev(torch, pos)
     box = hacc.Box(L=28.0)
+    counts0 = ctx.pair_counts(box, split_params, p)
     res = ctx.tune(box, split_params, p, reps=1)
     assert 0 <= res["chosen"] < hacc.TUNE_SETTINGS and all(t > 0 for t in res["times_ms"])
     assert len(res["times_ms"]) == hacc.TUNE_SETTINGS and res["times_ms"][res["chosen"]] == min(res["times_ms"])
@@ -260,9 +261,10 @@ def test_every_kernel_variant_gives_the_same_forces(torch, hacc, ctx, split_para
             ctx.set_variant(v)
             a = ctx.sr_force(box, split_params, p).clone()
             if ref is None:
+                assert np.abs(a.cpu().numpy()[:, :3] - ref_o).max() / rms <= 1e-4, (cap, v)
                 ref = a
-                assert np.abs(a.cpu().numpy()[:, :3] - ref_o).max() / rms <= 1e-4
-            assert torch.equal(a, ref)
+            assert torch.equal(a, ref), (cap, v)
+            assert ctx.pair_counts(box, split_params, p) == counts0
     ctx.set_item_cap(-1)
     ctx.set_variant(0)
     ctx.set_queue_order(False)
