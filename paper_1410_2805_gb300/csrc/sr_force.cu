@@ -135,14 +135,16 @@ __device__ __forceinline__ void interact(const KParams &P, const PairConsts &C, 
     }
 }
 
-// Axis-aligned bounds of an item's i-particles (after the run's i shift).
-struct Bounds {
-    float lx, ly, lz, hx, hy, hz;
-};
-
 // Entries of a staged tile: up to 32 G entries, plus room for the up to 31
 // that a compaction round carries past a full tile.
 constexpr int kTileCap = 32 * 8 + 32;
+
+// Tile steps per pass of the pair loop (the last tile is padded with far,
+// massless entries to whole passes, so the loop has no remainder).
+template <int K>
+struct Unroll {
+    static constexpr int F = K >= 5 ? 1 : (K >= 3 ? 2 : 4);
+};
 
 // Run the warp's i-particles against the staged entries [0, nj) of buf:
 // group g takes entries g, g+G, g+2G, ... (consecutive float4 addresses
@@ -155,18 +157,24 @@ __device__ __forceinline__ void run_tile(const KParams &P, const PairConsts &C, 
                                          float (&az)[K], unsigned &cnt) {
     const int G = 1 << lg;
     const int lpg = 32 >> lg;
-    const int tg = (nj + G - 1) >> lg;   // entries per group (interleaved)
+    // entries per group (interleaved); the pointer-stepped loop runs whole passes
+    const int tg = U == 2 ? (nj + G * Unroll<K>::F - 1) / (G * Unroll<K>::F) * Unroll<K>::F : (nj + G - 1) >> lg;
     constexpr int kUnroll = U == 1 ? (K >= 3 ? 1 : 2) : (K >= 5 ? 1 : (K >= 3 ? 2 : 4));
     if (U == 2) {
-        // pointer-stepped loop over the group's entries g, g+G, ...
+        // pointer-stepped loop over the group's entries g, g+G, ..., F entries a
+        // pass (the tile holds whole passes: no remainder)
+        constexpr int F = Unroll<K>::F;
         const float4 *q = buf + grp;
         int e = grp;
-#pragma unroll kUnroll
-        for (int t = 0; t < tg; ++t) {
-            const int jidx = (COUNT || POT) && e < nj ? ids[e] : -1;
-            interact<K, COUNT, POT, EPS0, UM>(P, C, *q, jidx, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
-            q += G;
-            e += G;
+#pragma unroll 1
+        for (int t = 0; t < tg; t += F) {
+#pragma unroll
+            for (int u = 0; u < F; ++u) {
+                const int jidx = (COUNT || POT) && e + u * G < nj ? ids[e + u * G] : -1;
+                interact<K, COUNT, POT, EPS0, UM>(P, C, q[u * G], jidx, iself, lpg, xs, ys, zs, ax, ay, az, cnt);
+            }
+            q += F * G;
+            e += F * G;
         }
     } else {
         const float4 *bp = buf + grp;
@@ -196,7 +204,9 @@ constexpr int kMaxRuns = 64;   // 2 (2R+1)^2 <= 50 for R <= 2
 struct RunTable {
     int4 *A;
     int4 *B;
+    float4 *bnd;   // [0], [1]: the item's bounds (lx, ly, lz, -), (hx, hy, hz, -); [2], [3]: shifted, keep_r2 in [2].w
 };
+
 
 // Stream the runs [r0, r1) of the table (all with the same i shift tx, ty,
 // tz) through the warp's shared tile.  The warp is split into G = 2^lg lane
@@ -216,7 +226,7 @@ struct RunTable {
 template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &rt, int r0, int r1, float L, float tx,
                                              float ty, float tz, int iself, int i_end, int lg, int grp,
-                                             const Bounds &bb, float (&xs)[K], float (&ys)[K], float (&zs)[K],
+                                             float (&xs)[K], float (&ys)[K], float (&zs)[K],
                                              float (&ax)[K], float (&ay)[K], float (&az)[K], unsigned &cnt,
                                              unsigned &jsum, float4 *buf, int *ids, int lane, int &fill, bool last) {
     const bool ishift = (tx != 0.0f) || (ty != 0.0f) || (tz != 0.0f);
@@ -234,11 +244,14 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
     const PairConsts C{P.eps, P.T, P.q0, P.q1, P.q2, P.q3, P.q4, P.q5};
     const float4 dummy = make_float4(1e18f, 1e18f, 1e18f, 0.0f);   // far away, zero mass
     const int tile = 32 << lg;
-    // the item's bounds in this frame (monotone rounding keeps them bounds)
-    const float lx = ishift ? __fadd_rn(bb.lx, tx) : bb.lx, hx = ishift ? __fadd_rn(bb.hx, tx) : bb.hx;
-    const float ly = ishift ? __fadd_rn(bb.ly, ty) : bb.ly, hy = ishift ? __fadd_rn(bb.hy, ty) : bb.hy;
-    const float lz = ishift ? __fadd_rn(bb.lz, tz) : bb.lz, hz = ishift ? __fadd_rn(bb.hz, tz) : bb.hz;
-    const float keep_r2 = P.T * 1.001f + 1e-3f;
+    // the item's bounds in this frame (monotone rounding keeps them bounds),
+    // held in the warp's shared slots rather than in registers across the tiles
+    if (lane == 0) {
+        const float4 l = rt.bnd[0], h = rt.bnd[1];
+        rt.bnd[2] = make_float4(__fadd_rn(l.x, tx), __fadd_rn(l.y, ty), __fadd_rn(l.z, tz), P.T * 1.001f + 1e-3f);
+        rt.bnd[3] = make_float4(__fadd_rn(h.x, tx), __fadd_rn(h.y, ty), __fadd_rn(h.z, tz), 0.0f);
+    }
+    __syncwarp();
     const unsigned below = (1u << lane) - 1u;
     const int t_end = rt.A[r1 - 1].x;
     int t0 = r0 > 0 ? rt.A[r0 - 1].x : 0;
@@ -274,10 +287,11 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
                     if (a.z & 2) v.y = __fadd_rn(v.y, -L);
                     if (a.z & 4) v.z = __fadd_rn(v.z, -L);
                 }
-                const float ex = fmaxf(fmaxf(lx - v.x, v.x - hx), 0.0f);
-                const float ey = fmaxf(fmaxf(ly - v.y, v.y - hy), 0.0f);
-                const float ez = fmaxf(fmaxf(lz - v.z, v.z - hz), 0.0f);
-                keep = __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, ez * ez)) < keep_r2;
+                const float4 lo = rt.bnd[2], hi = rt.bnd[3];
+                const float ex = fmaxf(fmaxf(lo.x - v.x, v.x - hi.x), 0.0f);
+                const float ey = fmaxf(fmaxf(lo.y - v.y, v.y - hi.y), 0.0f);
+                const float ez = fmaxf(fmaxf(lo.z - v.z, v.z - hi.z), 0.0f);
+                keep = __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, ez * ez)) < lo.w;
             }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep) {
@@ -292,8 +306,10 @@ __device__ __forceinline__ void process_runs(const KParams &P, const RunTable &r
         if (fill < tile && !last) break;
         const int nj = min(fill, tile);
         if (nj == 0) break;
-        // a short last tile is padded to whole lane groups with far, massless entries
-        const int padded = (nj + G - 1) & ~(G - 1);
+        // a short last tile is padded to whole passes of the pair loop (Unroll<K>::F
+        // entries per lane group) with far, massless entries
+        const int step = G * Unroll<K>::F;
+        const int padded = (nj + step - 1) / step * step;
         if (nj < tile && lane < padded - nj) buf[nj + lane] = dummy;
         __syncwarp();
         run_tile<K, COUNT, POT, EPS0, UM, U>(P, C, buf, ids, nj, iself, lg, grp, xs, ys, zs, ax, ay, az, cnt);
@@ -444,17 +460,15 @@ template <int K, bool COUNT, bool POT, bool EPS0, bool UM, int U, bool CI>
 __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids, const RunTable &rt, int lane,
                              float m_uniform) {
     // geometry: the single box of the call, or this item's box of a batch
+    // (the kick and drift factors are read again in the epilogue)
     int nc = P.nc;
     float L = P.L;
     int cbase = 0;
-    float h_kick = P.h_kick, h_drift = P.h_drift;
     if (P.boxes) {
         const BoxDev &bx = P.boxes[item.w >> 8];
         nc = bx.nc;
         L = bx.L;
         cbase = bx.cell_base;
-        h_kick = bx.h;
-        h_drift = bx.post;
     }
     const int c = item.x - cbase, i0 = item.y, ni = item.z;
     const int lg = (item.w >> 4) & 15;    // 2^lg lane groups
@@ -463,38 +477,47 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
     const int slot = lane & (lpg - 1);
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
 
-    // every group holds the same K x lpg particles of the cell
-    float xi[K], yi[K], zi[K], mi[K];
+    // every group holds the same K x lpg particles of the cell (their masses
+    // are read again in the epilogue)
+    float xi[K], yi[K], zi[K];
     float ax[K], ay[K], az[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         int q = slot + lpg * k;
         float4 p = q < ni ? P.pos[i0 + q] : make_float4(-1e30f, -1e30f, -1e30f, 0.0f);
-        xi[k] = p.x; yi[k] = p.y; zi[k] = p.z; mi[k] = p.w;
+        xi[k] = p.x; yi[k] = p.y; zi[k] = p.z;
         ax[k] = 0.0f; ay[k] = 0.0f; az[k] = 0.0f;
     }
     unsigned cnt = 0, jsum = 0;           // pairs inside the cutoff; j evaluated (counting form)
     const int iself = i0 + slot;          // sorted index of this lane's k = 0 particle
-    // bounding box of the item's particles (for the j culling of the runs)
-    Bounds bb{1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+    // bounding box of the item's particles (for the j culling of the runs),
+    // kept in the warp's shared slots
+    {
+        float lx = 1e30f, ly = 1e30f, lz = 1e30f, hx = -1e30f, hy = -1e30f, hz = -1e30f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (slot + lpg * k < ni) {
-            bb.lx = fminf(bb.lx, xi[k]);
-            bb.hx = fmaxf(bb.hx, xi[k]);
-            bb.ly = fminf(bb.ly, yi[k]);
-            bb.hy = fmaxf(bb.hy, yi[k]);
-            bb.lz = fminf(bb.lz, zi[k]);
-            bb.hz = fmaxf(bb.hz, zi[k]);
+        for (int k = 0; k < K; ++k) {
+            if (slot + lpg * k < ni) {
+                lx = fminf(lx, xi[k]);
+                hx = fmaxf(hx, xi[k]);
+                ly = fminf(ly, yi[k]);
+                hy = fmaxf(hy, yi[k]);
+                lz = fminf(lz, zi[k]);
+                hz = fmaxf(hz, zi[k]);
+            }
         }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        bb.lx = fminf(bb.lx, __shfl_xor_sync(0xffffffffu, bb.lx, o));
-        bb.hx = fmaxf(bb.hx, __shfl_xor_sync(0xffffffffu, bb.hx, o));
-        bb.ly = fminf(bb.ly, __shfl_xor_sync(0xffffffffu, bb.ly, o));
-        bb.hy = fmaxf(bb.hy, __shfl_xor_sync(0xffffffffu, bb.hy, o));
-        bb.lz = fminf(bb.lz, __shfl_xor_sync(0xffffffffu, bb.lz, o));
-        bb.hz = fmaxf(bb.hz, __shfl_xor_sync(0xffffffffu, bb.hz, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+        if (lane == 0) {
+            rt.bnd[0] = make_float4(lx, ly, lz, 0.0f);
+            rt.bnd[1] = make_float4(hx, hy, hz, 0.0f);
+        }
+        __syncwarp();
     }
 
     // neighbour cells cx-R..cx+R (R = 1: 27 cells; R = 2: 125 cells of a mesh twice as fine)
@@ -527,7 +550,7 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
             tz = (bits & 32) ? -L : 0.0f;
         }
         if (rt.A[q1 - 1].x > (q > 0 ? rt.A[q - 1].x : 0))   // not empty
-            process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, q, q1, L, tx, ty, tz, iself, i0 + ni, lg, grp, bb,
+            process_runs<K, COUNT, POT, EPS0, UM, U, CI>(P, rt, q, q1, L, tx, ty, tz, iself, i0 + ni, lg, grp,
                                                          xi, yi, zi, ax, ay, az, cnt, jsum, buf, ids, lane, fill, true);
         q = q1;
     }
@@ -544,17 +567,24 @@ __device__ void process_item(const KParams &P, int4 item, float4 *buf, int *ids,
 
     // epilogue (group 0 writes)
     if (grp == 0) {
+        float h_kick = P.h_kick, h_drift = P.h_drift;
+        if (P.boxes) {
+            const BoxDev &bx = P.boxes[item.w >> 8];
+            h_kick = bx.h;
+            h_drift = bx.post;
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int q = slot + lpg * k;
             if (q >= ni) continue;
             int i = i0 + q;
+            const float mi = P.pos[i].w;
             if (POT) {
-                P.phi_out[i] = 0.5f * P.G * mi[k] * ax[k];
+                P.phi_out[i] = 0.5f * P.G * mi * ax[k];
                 continue;
             }
             const float gm = UM ? P.G * m_uniform : P.G;
-            write_result(P, i, gm * ax[k], gm * ay[k], gm * az[k], xi[k], yi[k], zi[k], mi[k], h_kick, h_drift, L);
+            write_result(P, i, gm * ax[k], gm * ay[k], gm * az[k], xi[k], yi[k], zi[k], mi, h_kick, h_drift, L);
         }
     }
     if (COUNT) {
@@ -593,10 +623,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sr_force(KParams P) {
     __shared__ float4 tiles[kWarps][kTileCap];
     __shared__ int tile_ids[COUNT || POT ? kWarps : 1][kTileCap];
     __shared__ int4 runs[kWarps][kMaxRuns];
+    __shared__ float4 bnd[kWarps][4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
     int *ids = tile_ids[COUNT || POT ? w : 0];
-    const RunTable rt{runs[w], nullptr};
+    const RunTable rt{runs[w], nullptr, bnd[w]};
     // equal masses (flag left 0 by the binning pass): apply the mass once per i
     if (!POT && P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
         work_loop<COUNT, POT, EPS0, true, U>(P, buf, ids, rt, lane, P.pos[0].w);
@@ -610,9 +641,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_sr_force_ci(KParams P) {
     __shared__ float4 tiles[kWarps][kTileCap];
     __shared__ int4 runs[kWarps][kMaxRuns];
     __shared__ int4 steps[kWarps][kMaxRuns];
+    __shared__ float4 bnd[kWarps][4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf = tiles[w];
-    const RunTable rt{runs[w], steps[w]};
+    const RunTable rt{runs[w], steps[w], bnd[w]};
     if (P.mass_flag && *P.mass_flag == 0 && *P.n_items > 0)
         work_loop<false, false, EPS0, true, 0, true>(P, buf, nullptr, rt, lane, P.pos[0].w);
     else
@@ -626,8 +658,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_sr_pot_ci(KParams P) {
     __shared__ int tile_ids[kWarps][kTileCap];
     __shared__ int4 runs[kWarps][kMaxRuns];
     __shared__ int4 steps[kWarps][kMaxRuns];
+    __shared__ float4 bnd[kWarps][4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const RunTable rt{runs[w], steps[w]};
+    const RunTable rt{runs[w], steps[w], bnd[w]};
     work_loop<false, true, EPS0, false, 0, true>(P, tiles[w], tile_ids[w], rt, lane, 0.0f);
 }
 
