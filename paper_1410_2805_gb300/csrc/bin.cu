@@ -4,7 +4,8 @@
 //
 // Pipeline (all HBM-bound, one pass each):
 //   k_key     wrap (after an optional drift), exact cell id, per-cell count
-//             and arrival slot (atomic), [sub-cell]        read 16-32 B, write 24-25 B
+//             and arrival slot (atomic), [sub-cell]        read 16-32 B, write 8-25 B
+//             (in place without a drift only moved particles are written back)
 //   scan      exclusive scan of (count, work-item count) packed in 64 bits
 //   k_place   perm_tmp[start[c] + slot] = i, [its sub-cell] read 12-13 B, write 4-5 B
 //   k_order   within each cell, sort perm by input row (stable order) or by
@@ -56,7 +57,8 @@ __device__ __forceinline__ uint8_t sub_cell(float fx, float fy, float fz) {
 // (input rows next to each other often share a cell); the first lane of a
 // run claims the run's slots with one atomic and the others take the slots
 // that follow, in lane order.  Lanes without a particle pass c < 0.  All
-// lanes of the warp must call it.
+// lanes of the warp must call it.  (One atomic per distinct cell of the warp,
+// found with a match, measured slower.)
 __device__ __forceinline__ uint32_t claim_slot(uint32_t *__restrict__ count, int32_t c) {
     const int lane = threadIdx.x & 31;
     const int32_t prev = __shfl_up_sync(0xffffffffu, c, 1);
@@ -88,13 +90,16 @@ __global__ void __launch_bounds__(kBlock) k_key(int64_t n, const float4 *__restr
             p.y = __fmaf_rn(drift, v.y, p.y);
             p.z = __fmaf_rn(drift, v.z, p.z);
         }
+        // wrap1 leaves a coordinate in [0, L) bit for bit as it is, so an
+        // in-place call (no drift) writes back only the particles it moved
+        const bool inside = p.x >= 0.0f && p.x < Lf && p.y >= 0.0f && p.y < Lf && p.z >= 0.0f && p.z < Lf;
         bool ok = wrap1(p.x, Lf);
         ok &= wrap1(p.y, Lf);
         ok &= wrap1(p.z, Lf);
         if (!ok) atomicOr(flags, kFlagDomain);
         int cx = cell1(p.x, inv_w, Ld, nc), cy = cell1(p.y, inv_w, Ld, nc), cz = cell1(p.z, inv_w, Ld, nc);
         c = (int32_t)(((int64_t)cz * nc + cy) * nc + cx);
-        dst[i] = p;
+        if (!(inside && !vel && dst == src)) dst[i] = p;
         key[i] = c;
         if (sub) {
             const uint8_t m = sub_cell(p.x * inv_w - (float)cx, p.y * inv_w - (float)cy, p.z * inv_w - (float)cz);
@@ -341,20 +346,22 @@ __global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint3
     rank_shared(w, cnt, lane, out, RowOf64{});
 }
 
-// The in-cell order, a block per 128 consecutive cells: their slots form one
-// range of the placement array, which the block stages into shared memory
-// with coalesced loads (when it holds at most kOrdCap entries; else the warps
-// copy their cells from global memory into a shared buffer of their own).
-// Each warp then ranks one cell at a time: the slot of a key is the number of
-// smaller keys of its cell (keys are distinct), counted from shared memory --
-// for a cell of up to 32 keys in one unrolled pass of 32 independent
-// broadcast loads, for larger cells (up to kBigCell) with 2 or 4 keys per
-// lane on each pass over the cell.  The key is the input row (row order), or with SUB the
-// pair (sub-cell code, input row) as one 32-bit key, code << 24 | row (codes
-// below 2^8, rows below 2^24; larger calls take k_order_sub).  Cells above kBigCell are
-// ordered by input row alone, by k_order_big (with SUB their rows are copied
-// to perm_tmp first).
-constexpr int kOrdCells = 128;
+// The in-cell order, a block per kOrdCells consecutive cells: their slots
+// form one range of the placement array, which the block stages into shared
+// memory with coalesced loads (when it holds at most kOrdCap entries; else
+// the warps read their cells' keys from global memory).  Each warp then ranks
+// one cell at a time; keys are distinct, and the slot of a key is the number
+// of smaller keys of its cell.  A cell of up to 32 keys is ranked in registers
+// by its stretches of consecutive keys when it has few (the key pass's runs),
+// else by counting in one unrolled pass of 32 broadcast loads; a larger
+// row-ordered cell tries the stretch ranking in shared memory, and otherwise
+// counts with 2 or 4 keys per lane on each pass over the cell (up to
+// kBigCell).  The key is the input row (row order), or with SUB the pair
+// (sub-cell code, input row) as one 32-bit key, code << 24 | row (codes below
+// 2^8, rows below 2^24; larger calls take k_order_sub).  Cells above kBigCell
+// are ordered by input row alone, by k_order_big (with SUB their rows are
+// copied to perm_tmp first).
+constexpr int kOrdCells = 64;
 constexpr int kOrdCap = 6144;
 constexpr int64_t kOrdSubMaxRows = (int64_t)1 << 24;
 
@@ -398,10 +405,15 @@ __device__ __forceinline__ void rank_lanes(const Seg &seg, uint32_t cnt, uint32_
 // key's slot is the rank of its stretch's head (the lengths of the stretches
 // with smaller heads) plus its offset within the stretch.  Work O(cnt log R +
 // R^2) for R stretches instead of O(cnt^2): R is small when the input rows
-// follow the previous binning's cell order (the sub-cycle loop).  Returns
-// false, doing nothing, when R is above cnt / 4 or kHeads (a lattice-ordered
-// or shuffled input), where counting is cheaper.
+// follow the previous binning's cell order (the sub-cycle loop), and about a
+// third of cnt for lattice-ordered input.  Returns false, doing nothing, when
+// R is above cnt / 2 or kHeads (a shuffled input), where counting is cheaper.
 constexpr int kHeads = 128;
+// Cells of at most 32 keys rank by stretches in registers when they have at
+// most kRegHeads stretches (else by counting); row-ordered cells up to
+// kStretchTryMax keys try the shared-memory stretch ranking on any input.
+constexpr int kRegHeads = 16;
+constexpr uint32_t kStretchTryMax = 64;
 
 template <class Seg>
 __device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int lane, int32_t *out,
@@ -424,7 +436,7 @@ __device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int
         }
         R += __popc(m);
     }
-    if (R > kHeads || 4 * (uint32_t)R > cnt) return false;
+    if (R > kHeads || 2 * (uint32_t)R > cnt) return false;
     __syncwarp();
     // rank of each stretch head: the summed lengths of the stretches below it
     for (int t = lane; t < R; t += 32) {
@@ -502,14 +514,41 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
         };
         if (cnt <= 32) {
             const uint32_t v = lane < (int)cnt ? seg(lane) : 0u;
-            uint32_t r = 0;
+            // the stretches of consecutive keys in slot order (disjoint key
+            // intervals): a key's slot is the summed length of the stretches
+            // with smaller heads plus its offset in its own stretch
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
+            const unsigned hm = __ballot_sync(0xffffffffu, lane < (int)cnt && (lane == 0 || v != prev + 1u));
+            if (__popc(hm) <= kRegHeads) {
+                const int h = 31 - __clz(hm & (0xffffffffu >> (31 - lane)));   // this lane's stretch head
+                const uint32_t hv = __shfl_sync(0xffffffffu, v, h < 0 ? 0 : h);
+                uint32_t r = (uint32_t)(lane - h);
+                for (unsigned m = hm; m;) {
+                    const int a = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const int b = m ? __ffs(m) - 1 : (int)cnt;
+                    const uint32_t ka = __shfl_sync(0xffffffffu, v, a);
+                    r += ka < hv ? (uint32_t)(b - a) : 0u;
+                }
+                if (lane < (int)cnt) out[r] = (int32_t)(v & row_mask);
+            } else {
+                // bitonic sort of the warp's keys (lanes past the cell hold the
+                // largest key); lane q then holds the key of slot q
+                uint32_t x = lane < (int)cnt ? v : 0xffffffffu;
 #pragma unroll
-            for (int u = 0; u < 32; ++u) r += (u < (int)cnt && seg(u) < v) ? 1u : 0u;
-            if (lane < (int)cnt) out[r] = (int32_t)(v & row_mask);
+                for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                        x = keep_min ? min(x, y) : max(x, y);
+                    }
+                if (lane < (int)cnt) out[lane] = (int32_t)(x & row_mask);
+            }
             continue;
         }
         // (sub-cell keys rarely run on: a cell's particles spread over 64 sub-cells)
-        if (by_row && stretches &&
+        if (by_row && (stretches || cnt <= kStretchTryMax) &&
             rank_stretches(seg, cnt, lane, out, row_mask, heads[w][0], heads[w][1], heads[w][2]))
             continue;
         if (cnt > kBigCell) {
