@@ -353,9 +353,10 @@ __global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint3
 // one cell at a time; keys are distinct, and the slot of a key is the number
 // of smaller keys of its cell.  A cell of up to 32 keys is ranked in registers
 // by its stretches of consecutive keys when it has few (the key pass's runs),
-// else by counting in one unrolled pass of 32 broadcast loads; a larger
-// row-ordered cell tries the stretch ranking in shared memory, and otherwise
-// counts with 2 or 4 keys per lane on each pass over the cell (up to
+// else by a bitonic sort across the warp; a larger row-ordered cell tries
+// the stretch ranking in shared memory, and otherwise a cell of up to 64 keys
+// is sorted by a bitonic network over two keys per lane, a larger one ranked
+// by counting with 4 keys per lane on each pass over the cell (up to
 // kBigCell).  The key is the input row (row order), or with SUB the pair
 // (sub-cell code, input row) as one 32-bit key, code << 24 | row (codes below
 // 2^8, rows below 2^24; larger calls take k_order_sub).  Cells above kBigCell
@@ -559,7 +560,30 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
             continue;
         }
         if (cnt <= 64) {
-            rank_lanes<2>(seg, cnt, 0, lane, out, row_mask);
+            // bitonic sort of the cell's keys, slots lane and lane + 32 in each
+            // lane (slots past the cell hold the largest key)
+            uint32_t a = seg(lane);   // cnt > 32
+            uint32_t b = lane + 32 < (int)cnt ? seg(lane + 32) : 0xffffffffu;
+#pragma unroll
+            for (int k = 2; k <= 64; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    if (j == 32) {
+                        const uint32_t lo = min(a, b);
+                        b = max(a, b);
+                        a = lo;
+                    } else {
+                        const uint32_t ya = __shfl_xor_sync(0xffffffffu, a, j);
+                        const uint32_t yb = __shfl_xor_sync(0xffffffffu, b, j);
+                        const bool low = (lane & j) == 0;
+                        const bool up_a = k == 64 || (lane & k) == 0;
+                        const bool up_b = k == 64 || ((lane + 32) & k) == 0;
+                        a = low == up_a ? min(a, ya) : max(a, ya);
+                        b = low == up_b ? min(b, yb) : max(b, yb);
+                    }
+                }
+            out[lane] = (int32_t)(a & row_mask);
+            if (lane + 32 < (int)cnt) out[lane + 32] = (int32_t)(b & row_mask);
             continue;
         }
         for (uint32_t e0 = 0; e0 < cnt; e0 += 4 * 32) rank_lanes<4>(seg, cnt, e0, lane, out, row_mask);
