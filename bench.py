@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--served-rates", type=str, default="2,4,6,10,50", help="arrival rates (per s) of the served sweep")
     ap.add_argument("--no-c1", action="store_true", help="skip the plain 32^3 segment")
     ap.add_argument("--no-c3", action="store_true", help="skip the 512^3 precision segment")
+    ap.add_argument("--kernel-table", type=str, default="",
+                    help="write the device time of every kernel of one untimed step (CUDA activity records) "
+                         "as JSON to this path")
     ap.add_argument("--precision", action="store_true",
                     help="precision study instead: 512^3 Zel'dovich, FP32 absolute vs cell + offset positions")
     ap.add_argument("--precision-side", type=int, default=512)
@@ -892,6 +895,37 @@ def summary(line):
     return out
 
 
+def write_kernel_table(torch, path, fn, args, reps=2):
+    """Device time of every kernel launched by `fn` (one step of the bench
+    workload), from the CUDA activity records the PyTorch profiler collects:
+    launches, microseconds per step and share, largest first.  These are the
+    kernels' own durations at the clocks of a normal run (no replay)."""
+    import collections
+    import re
+
+    from torch.profiler import ProfilerActivity, profile
+    fn()
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for ev in prof.events():
+        if ev.device_type != torch.autograd.DeviceType.CUDA:
+            continue
+        name = re.sub(r"\(anonymous namespace\)::|hacc::|void ", "", ev.name).split("(")[0][:64]
+        t = getattr(ev, "device_time_total", None)
+        agg[name][0] += 1
+        agg[name][1] += t if t is not None else ev.cuda_time_total
+    total = sum(t for _, t in agg.values())
+    rows = [{"kernel": k, "launches_per_step": c / reps, "us_per_step": t / reps, "share": t / total if total else 0.0}
+            for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1])]
+    with open(path, "w") as f:
+        json.dump({"workload": args.config, "steps_profiled": reps, "pm": not args.no_pm,
+                   "device_us_per_step": total / reps, "kernels": rows}, f, indent=1)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -975,6 +1009,9 @@ def run_ours(args):
     within = cnt["within_pairs"]
     cand = cnt["candidate_pairs"]
     evaluated = cnt["evaluated_pairs"]
+
+    if args.kernel_table:
+        write_kernel_table(torch, args.kernel_table, lambda: step(snap_p.clone(), snap_v.clone()), args)
 
     # ---- end to end through the host-buffer C ABI (pinned memory) ----
     e2e = None
