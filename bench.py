@@ -67,8 +67,8 @@ def parse():
     ap.add_argument("--no-c1", action="store_true", help="skip the plain 32^3 segment")
     ap.add_argument("--no-c3", action="store_true", help="skip the 512^3 precision segment")
     ap.add_argument("--kernel-table", type=str, default="",
-                    help="write the device time of every kernel of one untimed step (CUDA activity records) "
-                         "as JSON to this path")
+                    help="write the device time of every kernel of one untimed step and of one hacc_bin call "
+                         "(CUDA activity records) as JSON to this path")
     ap.add_argument("--precision", action="store_true",
                     help="precision study instead: 512^3 Zel'dovich, FP32 absolute vs cell + offset positions")
     ap.add_argument("--precision-side", type=int, default=512)
@@ -901,11 +901,11 @@ def summary(line):
     return out
 
 
-def write_kernel_table(torch, path, fn, args, reps=2):
-    """Device time of every kernel launched by `fn` (one step of the bench
-    workload), from the CUDA activity records the PyTorch profiler collects:
-    launches, microseconds per step and share, largest first.  These are the
-    kernels' own durations at the clocks of a normal run (no replay)."""
+def kernel_table(torch, fn, reps=2):
+    """Device time of every kernel launched by `fn`, from the CUDA activity
+    records the PyTorch profiler collects: launches, microseconds per call and
+    share, largest first.  These are the kernels' own durations at the clocks
+    of a normal run (no replay)."""
     import collections
     import re
 
@@ -928,11 +928,9 @@ def write_kernel_table(torch, path, fn, args, reps=2):
         agg[name][0] += 1
         agg[name][1] += t if t is not None else ev.cuda_time_total
     total = sum(t for _, t in agg.values())
-    rows = [{"kernel": k, "launches_per_step": c / reps, "us_per_step": t / reps, "share": t / total if total else 0.0}
+    rows = [{"kernel": k, "launches_per_call": c / reps, "us_per_call": t / reps, "share": t / total if total else 0.0}
             for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1])]
-    with open(path, "w") as f:
-        json.dump({"workload": args.config, "steps_profiled": reps, "pm": not args.no_pm,
-                   "device_us_per_step": total / reps, "kernels": rows}, f, indent=1)
+    return {"calls_profiled": reps, "device_us_per_call": total / reps, "kernels": rows}
 
 
 def run_ours(args):
@@ -1020,7 +1018,15 @@ def run_ours(args):
     evaluated = cnt["evaluated_pairs"]
 
     if args.kernel_table:
-        write_kernel_table(torch, args.kernel_table, lambda: step(snap_p.clone(), snap_v.clone()), args)
+        # one step from the state the timed steps start from, and one hacc_bin
+        # call on those positions
+        wrapped = snap_p.clone()
+        ctx.bin(box, split.r_cut, wrapped)
+        tables = {"workload": args.config, "pm": not args.no_pm,
+                  "step": kernel_table(torch, lambda: step(snap_p.clone(), snap_v.clone())),
+                  "hacc_bin": kernel_table(torch, lambda: ctx.bin(box, split.r_cut, wrapped), reps=5)}
+        with open(args.kernel_table, "w") as f:
+            json.dump(tables, f, indent=1)
 
     # ---- end to end through the host-buffer C ABI (pinned memory) ----
     e2e = None
