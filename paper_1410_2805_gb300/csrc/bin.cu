@@ -354,10 +354,10 @@ __global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint3
 // of smaller keys of its cell.  A cell of up to 32 keys is ranked in registers
 // by its stretches of consecutive keys when it has few (the key pass's runs),
 // else by a bitonic sort across the warp; a larger row-ordered cell tries
-// the stretch ranking in shared memory, and otherwise a cell of up to 64 keys
-// is sorted by a bitonic network over two keys per lane, a larger one ranked
-// by counting with 4 keys per lane on each pass over the cell (up to
-// kBigCell).  The key is the input row (row order), or with SUB the pair
+// the stretch ranking in shared memory, and otherwise a cell of up to 256
+// keys is sorted by a bitonic network over 2, 4 or 8 keys per lane, a larger
+// one ranked by counting with 4 keys per lane on each pass over the cell (up
+// to kBigCell).  The key is the input row (row order), or with SUB the pair
 // (sub-cell code, input row) as one 32-bit key, code << 24 | row (codes below
 // 2^8, rows below 2^24; larger calls take k_order_sub).  Cells above kBigCell
 // are ordered by input row alone, by k_order_big (with SUB their rows are
@@ -464,6 +464,52 @@ __device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int
     return true;
 }
 
+// Bitonic sort of N = 32 KPL keys held KPL per lane (key of slot lane + 32 q in
+// x[q]): stages that pair keys of different lanes (j < 32) exchange them with
+// shuffles, the others (j >= 32) compare two registers of the same lane.
+// Afterwards x[q] holds the key of sorted slot lane + 32 q.
+template <int KPL>
+__device__ __forceinline__ void bitonic_lanes(uint32_t (&x)[KPL], int lane) {
+    constexpr int N = 32 * KPL;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int qj = j >> 5;
+#pragma unroll
+                for (int q = 0; q < KPL; ++q) {
+                    if (q & qj) continue;   // q is the lower slot of the pair (q, q | qj)
+                    const bool up = ((lane + 32 * q) & k) == 0;
+                    const uint32_t a = x[q], b = x[q | qj];
+                    x[q] = up ? min(a, b) : max(a, b);
+                    x[q | qj] = up ? max(a, b) : min(a, b);
+                }
+            } else {
+                const bool low = (lane & j) == 0;
+#pragma unroll
+                for (int q = 0; q < KPL; ++q) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], j);
+                    const bool up = ((lane + 32 * q) & k) == 0;
+                    x[q] = low == up ? min(x[q], y) : max(x[q], y);
+                }
+            }
+        }
+}
+
+// The cell's cnt <= 32 KPL keys sorted by bitonic_lanes (slots past the cell
+// hold the largest key); out[slot] = the row of the slot's key.
+template <int KPL, class Seg>
+__device__ __forceinline__ void sort_cell(const Seg &seg, uint32_t cnt, int lane, int32_t *out, uint32_t row_mask) {
+    uint32_t x[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) x[q] = (uint32_t)(lane + 32 * q) < cnt ? seg(lane + 32 * q) : 0xffffffffu;
+    bitonic_lanes<KPL>(x, lane);
+#pragma unroll
+    for (int q = 0; q < KPL; ++q)
+        if ((uint32_t)(lane + 32 * q) < cnt) out[lane + 32 * q] = (int32_t)(x[q] & row_mask);
+}
+
 // row_below: with SUB, cells of at most row_below particles are ordered by
 // row alone (the row is the key's low 24 bits); stretches: try the ranking
 // by stretches for row-ordered cells (the input follows a previous cell
@@ -533,18 +579,7 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
                 }
                 if (lane < (int)cnt) out[r] = (int32_t)(v & row_mask);
             } else {
-                // bitonic sort of the warp's keys (lanes past the cell hold the
-                // largest key); lane q then holds the key of slot q
-                uint32_t x = lane < (int)cnt ? v : 0xffffffffu;
-#pragma unroll
-                for (int k = 2; k <= 32; k <<= 1)
-#pragma unroll
-                    for (int j = k >> 1; j > 0; j >>= 1) {
-                        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-                        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-                        x = keep_min ? min(x, y) : max(x, y);
-                    }
-                if (lane < (int)cnt) out[lane] = (int32_t)(x & row_mask);
+                sort_cell<1>(seg, cnt, lane, out, row_mask);
             }
             continue;
         }
@@ -560,30 +595,15 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
             continue;
         }
         if (cnt <= 64) {
-            // bitonic sort of the cell's keys, slots lane and lane + 32 in each
-            // lane (slots past the cell hold the largest key)
-            uint32_t a = seg(lane);   // cnt > 32
-            uint32_t b = lane + 32 < (int)cnt ? seg(lane + 32) : 0xffffffffu;
-#pragma unroll
-            for (int k = 2; k <= 64; k <<= 1)
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    if (j == 32) {
-                        const uint32_t lo = min(a, b);
-                        b = max(a, b);
-                        a = lo;
-                    } else {
-                        const uint32_t ya = __shfl_xor_sync(0xffffffffu, a, j);
-                        const uint32_t yb = __shfl_xor_sync(0xffffffffu, b, j);
-                        const bool low = (lane & j) == 0;
-                        const bool up_a = k == 64 || (lane & k) == 0;
-                        const bool up_b = k == 64 || ((lane + 32) & k) == 0;
-                        a = low == up_a ? min(a, ya) : max(a, ya);
-                        b = low == up_b ? min(b, yb) : max(b, yb);
-                    }
-                }
-            out[lane] = (int32_t)(a & row_mask);
-            if (lane + 32 < (int)cnt) out[lane + 32] = (int32_t)(b & row_mask);
+            sort_cell<2>(seg, cnt, lane, out, row_mask);
+            continue;
+        }
+        if (cnt <= 128) {
+            sort_cell<4>(seg, cnt, lane, out, row_mask);
+            continue;
+        }
+        if (cnt <= 256) {
+            sort_cell<8>(seg, cnt, lane, out, row_mask);
             continue;
         }
         for (uint32_t e0 = 0; e0 < cnt; e0 += 4 * 32) rank_lanes<4>(seg, cnt, e0, lane, out, row_mask);
