@@ -296,7 +296,7 @@ hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t 
 
 /* Autotuner of the batched launch (a tuning aid of the library; the paper has
  * no counterpart).  For every setting of work-item cap in {0 (cell-wide
- * items), 32, 48, 64, 96} (see hacc_set_item_cap) x queue order (cell order,
+ * items), 32, 64, 96, 128, 160} (see hacc_set_item_cap) x queue order (cell order,
  * largest first; see hacc_set_queue_order) x pair-kernel variant, times whole
  * batched ticks as hacc_batch_tick runs them (binning, gathers, the kick and
  * stream pass; each box one sub-cycle of step boxes[b].dt) on scratch copies
@@ -310,7 +310,7 @@ hacc_status hacc_batch_subcycle(hacc_ctx *ctx, const hacc_split *split, int32_t 
  * *chosen (nullable) the setting kept.  The pools are only read (the scratch
  * grows by 32 bytes per pool row).  Synchronises `stream`.  Every setting sums
  * the same pairs. */
-#define HACC_BATCH_TUNE_SETTINGS 40
+#define HACC_BATCH_TUNE_SETTINGS 48
 hacc_status hacc_batch_tune(hacc_ctx *ctx, const hacc_split *split, int32_t nbox, const hacc_batch_box *boxes,
                             const float *pos_pool, const float *vel_pool, int32_t reps, double *times_ms,
                             int32_t *chosen, hacc_stream_t stream);

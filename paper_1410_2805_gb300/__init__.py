@@ -55,11 +55,11 @@ class _BatchBox(ctypes.Structure):
 
 TICK_FIRST, TICK_LAST = 1, 2
 FORCE_VARIANTS = 4   # HACC_FORCE_VARIANTS
-BATCH_TUNE_SETTINGS = 40   # HACC_BATCH_TUNE_SETTINGS
+BATCH_TUNE_SETTINGS = 48   # HACC_BATCH_TUNE_SETTINGS
 TUNE_SETTINGS = 40   # HACC_TUNE_SETTINGS
 # tuner settings: k = (cap index * 2 + queue order) * FORCE_VARIANTS + variant
 TUNE_CAPS = (0, 16, 24, 32, 48)   # item caps of the single-box tuner
-BATCH_TUNE_CAPS = (0, 32, 48, 64, 96)   # item caps of the batched tuner
+BATCH_TUNE_CAPS = (0, 32, 64, 96, 128, 160)   # item caps of the batched tuner
 
 
 def tune_setting(k: int, caps) -> dict:

@@ -266,7 +266,7 @@ extern "C" hacc_status hacc_batch_tick(hacc_ctx *ctx, const hacc_split *split, i
 
 // Item caps the batched tuner tries (0: cell-wide items of up to kItemMax);
 // setting k = (cap index * 2 + queue order) * kForceVariants + variant.
-static const int kTuneCaps[] = {0, 32, 48, 64, 96};
+static const int kTuneCaps[] = {0, 32, 64, 96, 128, 160};
 static constexpr int kTuneSettings = (int)(sizeof(kTuneCaps) / sizeof(kTuneCaps[0])) * 2 * kForceVariants;
 static_assert(kTuneSettings == HACC_BATCH_TUNE_SETTINGS, "tuner table size");
 
