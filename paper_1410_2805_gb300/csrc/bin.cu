@@ -464,37 +464,59 @@ __device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int
     return true;
 }
 
-// Bitonic sort of N = 32 KPL keys held KPL per lane (key of slot lane + 32 q in
-// x[q]): stages that pair keys of different lanes (j < 32) exchange them with
-// shuffles, the others (j >= 32) compare two registers of the same lane.
-// Afterwards x[q] holds the key of sorted slot lane + 32 q.
+// Bitonic sort of N = 32 KPL keys held KPL per lane (key of slot e = lane +
+// 32 q in x[q]), in the form without directions: merging sorted runs of k/2
+// into runs of k first compares slot e with e ^ (k - 1) (the second run
+// reversed), then with e ^ j for j = k/4 .. 1; in every compare the lower slot
+// keeps the minimum.  Pairs across lanes (j < 32) exchange keys with shuffles,
+// the others compare two registers of the same lane.  Afterwards x[q] holds
+// the key of sorted slot lane + 32 q.
 template <int KPL>
 __device__ __forceinline__ void bitonic_lanes(uint32_t (&x)[KPL], int lane) {
     constexpr int N = 32 * KPL;
 #pragma unroll
-    for (int k = 2; k <= N; k <<= 1)
+    for (int k = 2; k <= N; k <<= 1) {
+        if (k <= 32) {
+            const bool low = (lane & (k >> 1)) == 0;
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int q = 0; q < KPL; ++q) {
+                const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], k - 1);
+                x[q] = low ? min(x[q], y) : max(x[q], y);
+            }
+        } else {
+            // slot (lane, q) meets (lane ^ 31, q ^ m): the one with the lower q is lower
+            const int m = (k >> 5) - 1;
+#pragma unroll
+            for (int q = 0; q < KPL; ++q) {
+                if (q & (k >> 6)) continue;
+                const int qq = q ^ m;
+                const uint32_t yb = __shfl_xor_sync(0xffffffffu, x[qq], 31);
+                const uint32_t ya = __shfl_xor_sync(0xffffffffu, x[q], 31);
+                x[q] = min(x[q], yb);
+                x[qq] = max(x[qq], ya);
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
             if (j >= 32) {
                 const int qj = j >> 5;
 #pragma unroll
                 for (int q = 0; q < KPL; ++q) {
-                    if (q & qj) continue;   // q is the lower slot of the pair (q, q | qj)
-                    const bool up = ((lane + 32 * q) & k) == 0;
+                    if (q & qj) continue;
                     const uint32_t a = x[q], b = x[q | qj];
-                    x[q] = up ? min(a, b) : max(a, b);
-                    x[q | qj] = up ? max(a, b) : min(a, b);
+                    x[q] = min(a, b);
+                    x[q | qj] = max(a, b);
                 }
             } else {
                 const bool low = (lane & j) == 0;
 #pragma unroll
                 for (int q = 0; q < KPL; ++q) {
                     const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], j);
-                    const bool up = ((lane + 32 * q) & k) == 0;
-                    x[q] = low == up ? min(x[q], y) : max(x[q], y);
+                    x[q] = low ? min(x[q], y) : max(x[q], y);
                 }
             }
         }
+    }
 }
 
 // The cell's cnt <= 32 KPL keys sorted by bitonic_lanes (slots past the cell
@@ -515,7 +537,7 @@ __device__ __forceinline__ void sort_cell(const Seg &seg, uint32_t cnt, int lane
 // by stretches for row-ordered cells (the input follows a previous cell
 // order).
 template <bool SUB>
-__global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint32_t *__restrict__ count,
+__global__ void __launch_bounds__(kBlock, 5) k_order_rows(int64_t ncell, const uint32_t *__restrict__ count,
                                                         const unsigned long long *__restrict__ packed,
                                                         int32_t *__restrict__ perm_tmp,
                                                         int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
@@ -525,9 +547,11 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
     __shared__ uint32_t keys[kOrdCap];
     __shared__ uint32_t heads[kBlock / 32][3][kHeads];    // a warp's stretch heads: keys, slots, ranks
     __shared__ uint32_t cstart[kOrdCells], ccount[kOrdCells];
+    __shared__ int next_cell;   // the warps take the block's cells in turn (cells differ widely in cost)
     const int64_t c0 = (int64_t)blockIdx.x * kOrdCells;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int ncb = ncell - c0 < kOrdCells ? (int)(ncell - c0) : kOrdCells;   // cells of this block (>= 1)
+    if (t == 0) next_cell = 0;
     if (t < kOrdCells) {
         uint32_t cnt = 0, st = 0;
         if (t < ncb) {
@@ -545,7 +569,11 @@ __global__ void __launch_bounds__(kBlock) k_order_rows(int64_t ncell, const uint
         __syncthreads();
     }
     const uint32_t row_mask = SUB ? (1u << 24) - 1u : 0xffffffffu;
-    for (int q = w; q < ncb; q += kBlock / 32) {
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(&next_cell, 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= ncb) break;
         const uint32_t cnt = ccount[q];
         if (cnt == 0) continue;
         const uint32_t st = cstart[q];
