@@ -1205,7 +1205,7 @@ hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm,
 // values (before the closing PM half kick, which only reads pos).
 static hacc_status step_impl(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                              int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream,
-                             cudaEvent_t vel_ready, cudaEvent_t pos_final) {
+                             const PmHostIO *open_io, const PmHostIO *close_io) {
     if (n_c < 1) return set_error(ctx, HACC_EINVAL, "n_c must be >= 1");
     HACC_TRY(check_particles(ctx, n, pos_m, vel));
     if (n > 0 && !vel) return set_error(ctx, HACC_EINVAL, "vel is NULL");
@@ -1214,11 +1214,9 @@ static hacc_status step_impl(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
     float4 *v = reinterpret_cast<float4 *>(vel);
     if (!split) return set_error(ctx, HACC_EINVAL, "split is NULL");
     // M_lr(dt/2): kick by the long-range force
-    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s, vel_ready));
-    if (vel_ready && n == 0) HACC_CUDA(cudaStreamWaitEvent(s, vel_ready, 0), "cudaStreamWaitEvent");
+    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s, nullptr, open_io));
     HACC_TRY(hacc_subcycle(ctx, box, split, n, pos_m, vel, dt, n_c, stream));
-    if (pos_final) HACC_CUDA(cudaEventRecord(pos_final, s), "cudaEventRecord");
-    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s));
+    HACC_TRY(pm_accel(ctx, box, pm, split->G, n, p, nullptr, v, (float)(0.5 * dt), s, nullptr, close_io));
     return HACC_OK;
 }
 
@@ -1272,8 +1270,10 @@ hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split 
     char *base = static_cast<char *>(ctx->io_base);
     float *dp = reinterpret_cast<float *>(base);
     float *dv = reinterpret_cast<float *>(base + ((bytes + 255) & ~size_t(255)));
-    // a second stream overlaps the velocity upload with the first PM field
-    // solve and the position download with the closing PM half kick
+    // a second stream carries the copies, overlapped with the PM stages: the
+    // positions go up chunk by chunk, each chunk deposited as it lands, then
+    // the velocities; at the end the positions come down while the closing
+    // field is solved and the velocities chunk by chunk as they are kicked
     if (!ctx->io_stream) {
         cudaStream_t a = nullptr;
         HACC_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -1287,17 +1287,20 @@ hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split 
     cudaStream_t aux = static_cast<cudaStream_t>(ctx->io_stream);
     cudaEvent_t ev_start = static_cast<cudaEvent_t>(ctx->io_ev[0]);
     cudaEvent_t ev_vel = static_cast<cudaEvent_t>(ctx->io_ev[1]);
-    cudaEvent_t ev_pos = static_cast<cudaEvent_t>(ctx->io_ev[2]);
+    PmHostIO open_io, close_io;
+    open_io.copy = close_io.copy = aux;
+    for (int c = 0; c < kPmChunks; ++c) open_io.ev[c] = close_io.ev[c] = static_cast<cudaEvent_t>(ctx->io_ev[3 + c]);
+    open_io.pos_up = reinterpret_cast<const float4 *>(pos_m);
+    open_io.vel_up = reinterpret_cast<const float4 *>(vel);
+    open_io.vel_ready = ev_vel;
+    close_io.pos_down = reinterpret_cast<float4 *>(pos_m);
+    close_io.vel_down = reinterpret_cast<float4 *>(vel);
+    // the copy stream starts after the work already queued on the stream
     HACC_CUDA(cudaEventRecord(ev_start, s), "cudaEventRecord");
     HACC_CUDA(cudaStreamWaitEvent(aux, ev_start, 0), "cudaStreamWaitEvent");
-    HACC_CUDA(cudaMemcpyAsync(dp, pos_m, bytes, cudaMemcpyHostToDevice, s), "H2D copy");
-    HACC_CUDA(cudaMemcpyAsync(dv, vel, bytes, cudaMemcpyHostToDevice, aux), "H2D copy");
-    HACC_CUDA(cudaEventRecord(ev_vel, aux), "cudaEventRecord");
-    HACC_TRY(step_impl(ctx, box, split, pm, n, dp, dv, dt, n_c, stream, ev_vel, ev_pos));
-    HACC_CUDA(cudaStreamWaitEvent(aux, ev_pos, 0), "cudaStreamWaitEvent");
-    HACC_CUDA(cudaMemcpyAsync(pos_m, dp, bytes, cudaMemcpyDeviceToHost, aux), "D2H copy");
+    HACC_TRY(step_impl(ctx, box, split, pm, n, dp, dv, dt, n_c, stream, n > 0 ? &open_io : nullptr,
+                       n > 0 ? &close_io : nullptr));
     HACC_CUDA(cudaEventRecord(ev_start, aux), "cudaEventRecord");
-    HACC_CUDA(cudaMemcpyAsync(vel, dv, bytes, cudaMemcpyDeviceToHost, s), "D2H copy");
     HACC_CUDA(cudaStreamWaitEvent(s, ev_start, 0), "cudaStreamWaitEvent");
     return hacc_ctx_sync(ctx, stream);
 }

@@ -83,7 +83,7 @@ struct hacc_ctx {
     // host-buffer full steps (api.cu): a second stream and events that let the
     // velocity upload and the position download overlap the PM stages
     void *io_stream = nullptr;
-    void *io_ev[3] = {nullptr, nullptr, nullptr};
+    void *io_ev[3 + 8] = {};   // [0..2] step events, [3..] the PM stage's chunk events (kPmChunks)
     bool ml_graph_off = false;   // set when the device refused the graph once
 };
 
@@ -406,12 +406,32 @@ cudaError_t diag_mass_moment_ci(int64_t n, const int32_t *cell, const float4 *of
                                 cudaStream_t s);
 
 // ---- PM (pm.cu) ------------------------------------------------------------
+// Host copies of a full step overlapped with its PM stages (hacc_step_host):
+// on the copy stream, positions are uploaded in kPmChunks chunks, each
+// deposited as soon as it has landed, then the velocities (vel_ready recorded
+// after them); at the closing kick the positions are downloaded while the
+// field is solved, and the kicked velocities chunk by chunk as they are
+// interpolated.  The deposit sums fixed-point integers, so the chunking
+// changes no bit.
+constexpr int kPmChunks = 8;
+struct PmHostIO {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev[kPmChunks] = {};
+    const float4 *pos_up = nullptr;     // host positions to upload into pos
+    const float4 *vel_up = nullptr;     // host velocities to upload into vel_kick, after the positions
+    cudaEvent_t vel_ready = nullptr;    // recorded on copy after the velocity upload
+    float4 *pos_down = nullptr;         // host: the positions, downloaded at the start of the stage
+    float4 *vel_down = nullptr;         // host: the kicked velocities, downloaded chunk by chunk
+};
+
 // Long-range acceleration G * a_PM at pos; stored to acc (if non-null) and/or
 // added as a kick vel += kick * a (if vel_kick is non-null).
 // before_kick (nullable): an event the stream waits for between the field
-// solve and the interpolation, which is the first use of vel_kick.
+// solve and the interpolation, which is the first use of vel_kick.  io
+// (nullable): host copies overlapped with the stage (see PmHostIO).
 hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, double G, int64_t n, const float4 *pos,
-                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s, cudaEvent_t before_kick = nullptr);
+                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s, cudaEvent_t before_kick = nullptr,
+                     const PmHostIO *io = nullptr);
 void pm_destroy(hacc_ctx *ctx);
 
 }  // namespace hacc

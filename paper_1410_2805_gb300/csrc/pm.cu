@@ -20,6 +20,7 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -249,7 +250,8 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBl
 }  // namespace
 
 hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, double G, int64_t n, const float4 *pos,
-                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s, cudaEvent_t before_kick) {
+                     float4 *acc, float4 *vel_kick, float kick, cudaStream_t s, cudaEvent_t before_kick,
+                     const PmHostIO *io) {
     if (!box || !pm) return set_error(ctx, HACC_EINVAL, "box or pm is NULL");
     const double L = box->L;
     if (!(L > 0) || !std::isfinite(L)) return set_error(ctx, HACC_EINVAL, "box side L must be finite and > 0");
@@ -265,9 +267,42 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
     const double D = L / ng;
     const float inv_d = (float)(ng / L);
     cudaError_t e;
+    // chunk c of the particles: [lo, hi)
+    const int nch = io ? kPmChunks : 1;
+    const int64_t per = (n + nch - 1) / nch;
+    auto bounds = [&](int c, int64_t *lo, int64_t *hi) {
+        *lo = std::min<int64_t>(n, c * per);
+        *hi = std::min<int64_t>(n, (c + 1) * per);
+    };
+    if (io && io->pos_down) {
+        // the positions are final: download them while the field is solved
+        if ((e = cudaEventRecord(io->ev[0], s)) != cudaSuccess) return check_cuda(ctx, e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(io->copy, io->ev[0], 0)) != cudaSuccess)
+            return check_cuda(ctx, e, "cudaStreamWaitEvent");
+        if ((e = cudaMemcpyAsync(io->pos_down, pos, (size_t)n * 16, cudaMemcpyDeviceToHost, io->copy)) != cudaSuccess)
+            return check_cuda(ctx, e, "D2H copy");
+    }
     if ((e = cudaMemsetAsync(st->mass, 0, ng3 * 8, s)) != cudaSuccess) return check_cuda(ctx, e, "PM memset");
-    k_deposit<<<blocks_for(n), kBlock, 0, s>>>(n, pos, inv_d, ng, st->mass);
-    note_launch();
+    for (int c = 0; c < nch; ++c) {
+        int64_t lo, hi;
+        bounds(c, &lo, &hi);
+        if (hi <= lo) continue;
+        if (io && io->pos_up) {
+            if ((e = cudaMemcpyAsync(const_cast<float4 *>(pos) + lo, io->pos_up + lo, (size_t)(hi - lo) * 16,
+                                     cudaMemcpyHostToDevice, io->copy)) != cudaSuccess)
+                return check_cuda(ctx, e, "H2D copy");
+            if ((e = cudaEventRecord(io->ev[c], io->copy)) != cudaSuccess) return check_cuda(ctx, e, "cudaEventRecord");
+            if ((e = cudaStreamWaitEvent(s, io->ev[c], 0)) != cudaSuccess) return check_cuda(ctx, e, "cudaStreamWaitEvent");
+        }
+        k_deposit<<<blocks_for(hi - lo), kBlock, 0, s>>>(hi - lo, pos + lo, inv_d, ng, st->mass);
+        note_launch();
+    }
+    if (io && io->vel_up) {
+        if ((e = cudaMemcpyAsync(vel_kick, io->vel_up, (size_t)n * 16, cudaMemcpyHostToDevice, io->copy)) !=
+            cudaSuccess)
+            return check_cuda(ctx, e, "H2D copy");
+        if ((e = cudaEventRecord(io->vel_ready, io->copy)) != cudaSuccess) return check_cuda(ctx, e, "cudaEventRecord");
+    }
     k_fix_to_density<<<blocks_for((int64_t)ng3), kBlock, 0, s>>>((int64_t)ng3, st->mass, 1.0 / (kFix * D * D * D),
                                                                    st->rho);
     note_launch();
@@ -290,8 +325,24 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
     note_launch();
     if (before_kick && (e = cudaStreamWaitEvent(s, before_kick, 0)) != cudaSuccess)
         return check_cuda(ctx, e, "cudaStreamWaitEvent");
-    k_interp<<<blocks_for(n), kBlock, 0, s>>>(n, pos, inv_d, ng, st->field, acc, vel_kick, kick);
-    note_launch();
+    if (io && io->vel_up && (e = cudaStreamWaitEvent(s, io->vel_ready, 0)) != cudaSuccess)
+        return check_cuda(ctx, e, "cudaStreamWaitEvent");
+    for (int c = 0; c < nch; ++c) {
+        int64_t lo, hi;
+        bounds(c, &lo, &hi);
+        if (hi <= lo) continue;
+        k_interp<<<blocks_for(hi - lo), kBlock, 0, s>>>(hi - lo, pos + lo, inv_d, ng, st->field, acc ? acc + lo : nullptr,
+                                                        vel_kick ? vel_kick + lo : nullptr, kick);
+        note_launch();
+        if (io && io->vel_down) {
+            if ((e = cudaEventRecord(io->ev[c], s)) != cudaSuccess) return check_cuda(ctx, e, "cudaEventRecord");
+            if ((e = cudaStreamWaitEvent(io->copy, io->ev[c], 0)) != cudaSuccess)
+                return check_cuda(ctx, e, "cudaStreamWaitEvent");
+            if ((e = cudaMemcpyAsync(io->vel_down + lo, vel_kick + lo, (size_t)(hi - lo) * 16, cudaMemcpyDeviceToHost,
+                                     io->copy)) != cudaSuccess)
+                return check_cuda(ctx, e, "D2H copy");
+        }
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(ctx, e, "PM kernels");
     return HACC_OK;
 }
