@@ -260,6 +260,88 @@ __global__ void __launch_bounds__(kBlock) k_place(int64_t n, const int32_t *__re
 // input row by k_order_big.
 constexpr uint32_t kBigCell = 512;
 
+// Bitonic sort of N = 32 KPL keys held KPL per lane (key of slot e = lane +
+// 32 q in x[q]), in the form without directions: merging sorted runs of k/2
+// into runs of k first compares slot e with e ^ (k - 1) (the second run
+// reversed), then with e ^ j for j = k/4 .. 1; in every compare the lower slot
+// keeps the minimum.  Pairs across lanes (j < 32) exchange keys with shuffles,
+// the others compare two registers of the same lane.  Afterwards x[q] holds
+// the key of sorted slot lane + 32 q.
+template <int KPL>
+__device__ __forceinline__ void bitonic_lanes(uint32_t (&x)[KPL], int lane) {
+    constexpr int N = 32 * KPL;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+        if (k <= 32) {
+            const bool low = (lane & (k >> 1)) == 0;
+#pragma unroll
+            for (int q = 0; q < KPL; ++q) {
+                const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], k - 1);
+                x[q] = low ? min(x[q], y) : max(x[q], y);
+            }
+        } else {
+            // slot (lane, q) meets (lane ^ 31, q ^ m): the one with the lower q is lower
+            const int m = (k >> 5) - 1;
+#pragma unroll
+            for (int q = 0; q < KPL; ++q) {
+                if (q & (k >> 6)) continue;
+                const int qq = q ^ m;
+                const uint32_t yb = __shfl_xor_sync(0xffffffffu, x[qq], 31);
+                const uint32_t ya = __shfl_xor_sync(0xffffffffu, x[q], 31);
+                x[q] = min(x[q], yb);
+                x[qq] = max(x[qq], ya);
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int qj = j >> 5;
+#pragma unroll
+                for (int q = 0; q < KPL; ++q) {
+                    if (q & qj) continue;
+                    const uint32_t a = x[q], b = x[q | qj];
+                    x[q] = min(a, b);
+                    x[q | qj] = max(a, b);
+                }
+            } else {
+                const bool low = (lane & j) == 0;
+#pragma unroll
+                for (int q = 0; q < KPL; ++q) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], j);
+                    x[q] = low ? min(x[q], y) : max(x[q], y);
+                }
+            }
+        }
+    }
+}
+
+// The cell's cnt <= 32 KPL keys sorted by bitonic_lanes (slots past the cell
+// hold the largest key); out[slot] = rowf(the slot's key).
+template <int KPL, class Seg, class RowF>
+__device__ __forceinline__ void sort_cell_f(const Seg &seg, uint32_t cnt, int lane, int32_t *out, const RowF &rowf) {
+    uint32_t x[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) x[q] = (uint32_t)(lane + 32 * q) < cnt ? seg(lane + 32 * q) : 0xffffffffu;
+    bitonic_lanes<KPL>(x, lane);
+#pragma unroll
+    for (int q = 0; q < KPL; ++q)
+        if ((uint32_t)(lane + 32 * q) < cnt) out[lane + 32 * q] = rowf(x[q]);
+}
+
+template <int KPL, class Seg>
+__device__ __forceinline__ void sort_cell(const Seg &seg, uint32_t cnt, int lane, int32_t *out, uint32_t row_mask) {
+    sort_cell_f<KPL>(seg, cnt, lane, out, [row_mask](uint32_t k) { return (int32_t)(k & row_mask); });
+}
+
+// A cell of cnt <= 256 keys through the smallest network that holds it.
+template <class Seg, class RowF>
+__device__ __forceinline__ void sort_small_cell(const Seg &seg, uint32_t cnt, int lane, int32_t *out, const RowF &rowf) {
+    if (cnt <= 32) sort_cell_f<1>(seg, cnt, lane, out, rowf);
+    else if (cnt <= 64) sort_cell_f<2>(seg, cnt, lane, out, rowf);
+    else if (cnt <= 128) sort_cell_f<4>(seg, cnt, lane, out, rowf);
+    else sort_cell_f<8>(seg, cnt, lane, out, rowf);
+}
+
 struct RowOf32 {
     __device__ int32_t operator()(int32_t k) const { return k; }
 };
@@ -300,7 +382,8 @@ __global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint3
                                                        int32_t *__restrict__ perm_tmp,
                                                        int32_t *__restrict__ perm, int32_t *__restrict__ big_list,
                                                        int *__restrict__ big_count,
-                                                       const unsigned long long *__restrict__ order_tmp) {
+                                                       const unsigned long long *__restrict__ order_tmp,
+                                                       uint32_t row_below) {
     int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (c >= ncell) return;
@@ -315,6 +398,12 @@ __global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint3
     }
     int32_t *out = perm + s;
     const unsigned long long *seg = order_tmp + s;
+    if (cnt <= row_below) {
+        // a cell that becomes one work item keeps row order (cnt <= 160)
+        sort_small_cell([&](uint32_t e) { return (uint32_t)seg[e]; }, cnt, lane, out,
+                        [](uint32_t k) { return (int32_t)k; });
+        return;
+    }
     uint32_t lo = 0xffffffffu, hi = 0u;
     for (uint32_t e = lane; e < cnt; e += 32) {
         const uint32_t r = (uint32_t)seg[e];
@@ -327,10 +416,9 @@ __global__ void __launch_bounds__(kBlock) k_order_sub(int64_t ncell, const uint3
     unsigned long long *w = keys[threadIdx.x >> 5];
     if (hi - lo < (1u << 24)) {
         const RowOfPacked row{lo};
-        if (cnt <= 32) {
-            uint32_t v = 0xffffffffu;
-            if (lane < (int)cnt) v = ((uint32_t)(seg[lane] >> 32) << 24) | ((uint32_t)seg[lane] - lo);
-            rank_warp(v, (int)cnt, lane, out, row);
+        if (cnt <= 256) {
+            sort_small_cell([&](uint32_t e) { return ((uint32_t)(seg[e] >> 32) << 24) | ((uint32_t)seg[e] - lo); },
+                            cnt, lane, out, [lo](uint32_t k) { return (int32_t)((k & 0xffffffu) + lo); });
             return;
         }
         uint32_t *w32 = reinterpret_cast<uint32_t *>(w);
@@ -462,74 +550,6 @@ __device__ __forceinline__ bool rank_stretches(const Seg &seg, uint32_t cnt, int
     }
     __syncwarp();
     return true;
-}
-
-// Bitonic sort of N = 32 KPL keys held KPL per lane (key of slot e = lane +
-// 32 q in x[q]), in the form without directions: merging sorted runs of k/2
-// into runs of k first compares slot e with e ^ (k - 1) (the second run
-// reversed), then with e ^ j for j = k/4 .. 1; in every compare the lower slot
-// keeps the minimum.  Pairs across lanes (j < 32) exchange keys with shuffles,
-// the others compare two registers of the same lane.  Afterwards x[q] holds
-// the key of sorted slot lane + 32 q.
-template <int KPL>
-__device__ __forceinline__ void bitonic_lanes(uint32_t (&x)[KPL], int lane) {
-    constexpr int N = 32 * KPL;
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-        if (k <= 32) {
-            const bool low = (lane & (k >> 1)) == 0;
-#pragma unroll
-            for (int q = 0; q < KPL; ++q) {
-                const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], k - 1);
-                x[q] = low ? min(x[q], y) : max(x[q], y);
-            }
-        } else {
-            // slot (lane, q) meets (lane ^ 31, q ^ m): the one with the lower q is lower
-            const int m = (k >> 5) - 1;
-#pragma unroll
-            for (int q = 0; q < KPL; ++q) {
-                if (q & (k >> 6)) continue;
-                const int qq = q ^ m;
-                const uint32_t yb = __shfl_xor_sync(0xffffffffu, x[qq], 31);
-                const uint32_t ya = __shfl_xor_sync(0xffffffffu, x[q], 31);
-                x[q] = min(x[q], yb);
-                x[qq] = max(x[qq], ya);
-            }
-        }
-#pragma unroll
-        for (int j = k >> 2; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int qj = j >> 5;
-#pragma unroll
-                for (int q = 0; q < KPL; ++q) {
-                    if (q & qj) continue;
-                    const uint32_t a = x[q], b = x[q | qj];
-                    x[q] = min(a, b);
-                    x[q | qj] = max(a, b);
-                }
-            } else {
-                const bool low = (lane & j) == 0;
-#pragma unroll
-                for (int q = 0; q < KPL; ++q) {
-                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x[q], j);
-                    x[q] = low ? min(x[q], y) : max(x[q], y);
-                }
-            }
-        }
-    }
-}
-
-// The cell's cnt <= 32 KPL keys sorted by bitonic_lanes (slots past the cell
-// hold the largest key); out[slot] = the row of the slot's key.
-template <int KPL, class Seg>
-__device__ __forceinline__ void sort_cell(const Seg &seg, uint32_t cnt, int lane, int32_t *out, uint32_t row_mask) {
-    uint32_t x[KPL];
-#pragma unroll
-    for (int q = 0; q < KPL; ++q) x[q] = (uint32_t)(lane + 32 * q) < cnt ? seg(lane + 32 * q) : 0xffffffffu;
-    bitonic_lanes<KPL>(x, lane);
-#pragma unroll
-    for (int q = 0; q < KPL; ++q)
-        if ((uint32_t)(lane + 32 * q) < cnt) out[lane + 32 * q] = (int32_t)(x[q] & row_mask);
 }
 
 // row_below: with SUB, cells of at most row_below particles are ordered by
@@ -1261,7 +1281,7 @@ cudaError_t bin_sort(int64_t n, int64_t ncell, const BinBuffers &b, bool make_it
         if ((e = cudaMemsetAsync(b.big_count, 0, sizeof(int), s)) != cudaSuccess) return e;
         if (sub && n > kOrdSubMaxRows)
             k_order_sub<<<blocks_for(ncell * 32), kBlock, 0, s>>>(ncell, b.count, b.packed, b.perm_tmp, b.perm,
-                                                                  b.big_list, b.big_count, b.order_tmp);
+                                                                  b.big_list, b.big_count, b.order_tmp, row_below);
         else if (sub)
             k_order_rows<true><<<blocks_for(ncell, kOrdCells), kBlock, 0, s>>>(
                 ncell, b.count, b.packed, b.perm_tmp, b.perm, b.big_list, b.big_count, b.order_tmp, row_below,

@@ -218,3 +218,33 @@ def test_batch200_smallest_boxes_against_oracle(env, split_params):
         assert np.abs(V[o:o + k, :3].cpu().numpy() - vo).max() < 1e-3 * vscale
     x = P.cpu().numpy()
     assert np.isfinite(x).all()
+
+
+def test_over_2_24_particles_in_sub_cell_order(env, split_params, zel256):
+    # more than 2^24 particles with an item cap: the in-cell order takes the
+    # path for rows beyond 24 bits (cells of up to the cap by row, the others
+    # by (sub-cell, row) relative to the cell's first row); the pairs summed
+    # do not depend on the order, the forces only through rounding
+    torch, hacc, ctx = env
+    pos, _, L = zel256
+    extra = synth.uniform(4096, L, seed=224)
+    allp = np.concatenate([pos, extra])
+    assert len(allp) > 1 << 24
+    sp = _f32_split(split_params)
+    p = torch.from_numpy(allp).cuda()
+    box = hacc.Box(L=L)
+    try:
+        ctx.set_item_cap(0)
+        a0 = ctx.sr_force(box, sp, p).cpu().numpy()
+        counts0 = ctx.pair_counts(box, sp, p)
+        ctx.set_item_cap(48)
+        a48 = ctx.sr_force(box, sp, p).cpu().numpy()
+        counts48 = ctx.pair_counts(box, sp, p)
+    finally:
+        ctx.set_item_cap(-1)
+    assert counts48 == counts0
+    rms = np.sqrt((a0[:, :3].astype(np.float64) ** 2).sum(1).mean())
+    assert np.abs(a48[:, :3] - a0[:, :3]).max() / rms <= FORCE_TOL
+    sel = np.sort(np.random.default_rng(224).choice(len(allp), size=1024, replace=False))
+    ref, _ = oracle.force_mesh(allp, L, sp, sel=sel)
+    assert np.abs(a48[sel, :3] - ref).max() / np.sqrt((ref ** 2).sum(1).mean()) <= FORCE_TOL
