@@ -252,12 +252,16 @@ __global__ void __launch_bounds__(kBlock) k_place(int64_t n, const int32_t *__re
 
 // The arrival order from the atomics is arbitrary, so each element's final
 // slot is the number of smaller keys in its cell.  The key is the input row
-// (distinct), which gives ascending input row within the cell (k_order_rows),
-// or the pair (Morton sub-cell, input row), which groups the cell's particles
-// by sub-cell (k_order_sub, one warp per cell); when the cell's rows span less
-// than 2^24 the pair is ranked as one 32-bit key (sub-cell code << 24 | row -
-// smallest row; codes are below 2^8).  Cells of more than kBigCell particles go to a list sorted by
-// input row by k_order_big.
+// (distinct), which gives ascending input row within the cell, or the pair
+// (Morton sub-cell, input row), which groups the cell's particles by sub-cell.
+// k_order_rows serves calls of up to 2^24 rows (the pair as one 32-bit key,
+// code << 24 | row); k_order_sub, one warp per cell, larger ones: a cell that
+// becomes one work item by row, the others by the pair with the row taken
+// relative to the cell's smallest row (one 32-bit key when the cell's rows
+// span less than 2^24, else 64-bit keys; codes are below 2^8), cells of up to
+// 256 keys through the register networks above, larger ones by counting.
+// Cells of more than kBigCell particles go to a list sorted by input row by
+// k_order_big.
 constexpr uint32_t kBigCell = 512;
 
 // Bitonic sort of N = 32 KPL keys held KPL per lane (key of slot e = lane +
@@ -342,9 +346,6 @@ __device__ __forceinline__ void sort_small_cell(const Seg &seg, uint32_t cnt, in
     else sort_cell_f<8>(seg, cnt, lane, out, rowf);
 }
 
-struct RowOf32 {
-    __device__ int32_t operator()(int32_t k) const { return k; }
-};
 struct RowOf64 {
     __device__ int32_t operator()(unsigned long long k) const { return (int32_t)(uint32_t)k; }
 };
