@@ -215,7 +215,12 @@ hacc_status hacc_diagnostics(hacc_ctx *ctx, const hacc_box *box, const hacc_spli
 /* Host-buffer variants: pos_m, vel (and acc) are HOST pointers (page-locked
  * memory gives the fastest copies).  Each call copies the inputs to scratch
  * on the device, runs the device entry point of the same name, copies the
- * results back and waits for the stream. */
+ * results back and waits for the stream.  hacc_step_host runs its copies on a
+ * second stream of the context, overlapped with the PM stages: the positions
+ * go up in chunks that are deposited as they land, then the velocities; at
+ * the end the positions come down while the closing field is solved and the
+ * velocities chunk by chunk as they are kicked.  The results are the bits of
+ * hacc_step's.  The host arrays must not be touched until the call returns. */
 hacc_status hacc_sr_force_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
                                const float *pos_m, float *acc, hacc_stream_t stream);
 hacc_status hacc_subcycle_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, int64_t n,
