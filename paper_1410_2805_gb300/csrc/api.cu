@@ -1200,9 +1200,8 @@ hacc_status hacc_pm_force(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm,
                     nullptr, 0.0f, s);
 }
 
-// The full step (Eq. tstep); vel_ready (nullable) is waited for before the
-// first use of vel, pos_final (nullable) is recorded once pos holds its final
-// values (before the closing PM half kick, which only reads pos).
+// The full step (Eq. tstep); open_io / close_io (nullable): host copies
+// overlapped with the opening and the closing PM half kick (PmHostIO).
 static hacc_status step_impl(hacc_ctx *ctx, const hacc_box *box, const hacc_split *split, const hacc_pm *pm,
                              int64_t n, float *pos_m, float *vel, double dt, int32_t n_c, hacc_stream_t stream,
                              const PmHostIO *open_io, const PmHostIO *close_io) {
@@ -1286,13 +1285,11 @@ hacc_status hacc_step_host(hacc_ctx *ctx, const hacc_box *box, const hacc_split 
     }
     cudaStream_t aux = static_cast<cudaStream_t>(ctx->io_stream);
     cudaEvent_t ev_start = static_cast<cudaEvent_t>(ctx->io_ev[0]);
-    cudaEvent_t ev_vel = static_cast<cudaEvent_t>(ctx->io_ev[1]);
     PmHostIO open_io, close_io;
     open_io.copy = close_io.copy = aux;
     for (int c = 0; c < kPmChunks; ++c) open_io.ev[c] = close_io.ev[c] = static_cast<cudaEvent_t>(ctx->io_ev[3 + c]);
     open_io.pos_up = reinterpret_cast<const float4 *>(pos_m);
     open_io.vel_up = reinterpret_cast<const float4 *>(vel);
-    open_io.vel_ready = ev_vel;
     close_io.pos_down = reinterpret_cast<float4 *>(pos_m);
     close_io.vel_down = reinterpret_cast<float4 *>(vel);
     // the copy stream starts after the work already queued on the stream

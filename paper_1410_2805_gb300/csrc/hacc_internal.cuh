@@ -408,18 +408,17 @@ cudaError_t diag_mass_moment_ci(int64_t n, const int32_t *cell, const float4 *of
 // ---- PM (pm.cu) ------------------------------------------------------------
 // Host copies of a full step overlapped with its PM stages (hacc_step_host):
 // on the copy stream, positions are uploaded in kPmChunks chunks, each
-// deposited as soon as it has landed, then the velocities (vel_ready recorded
-// after them); at the closing kick the positions are downloaded while the
-// field is solved, and the kicked velocities chunk by chunk as they are
-// interpolated.  The deposit sums fixed-point integers, so the chunking
-// changes no bit.
+// deposited as soon as it has landed, then the velocities in the same chunks,
+// each kicked as soon as it has landed and the field is solved; at the
+// closing kick the positions are downloaded while the field is solved, and
+// the kicked velocities chunk by chunk as they are interpolated.  The deposit
+// sums fixed-point integers, so the chunking changes no bit.
 constexpr int kPmChunks = 8;
 struct PmHostIO {
     cudaStream_t copy = nullptr;
     cudaEvent_t ev[kPmChunks] = {};
     const float4 *pos_up = nullptr;     // host positions to upload into pos
     const float4 *vel_up = nullptr;     // host velocities to upload into vel_kick, after the positions
-    cudaEvent_t vel_ready = nullptr;    // recorded on copy after the velocity upload
     float4 *pos_down = nullptr;         // host: the positions, downloaded at the start of the stage
     float4 *vel_down = nullptr;         // host: the kicked velocities, downloaded chunk by chunk
 };

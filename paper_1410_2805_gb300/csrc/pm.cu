@@ -298,10 +298,18 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
         note_launch();
     }
     if (io && io->vel_up) {
-        if ((e = cudaMemcpyAsync(vel_kick, io->vel_up, (size_t)n * 16, cudaMemcpyHostToDevice, io->copy)) !=
-            cudaSuccess)
-            return check_cuda(ctx, e, "H2D copy");
-        if ((e = cudaEventRecord(io->vel_ready, io->copy)) != cudaSuccess) return check_cuda(ctx, e, "cudaEventRecord");
+        // the velocities follow in the same chunks; each chunk's kick waits for
+        // its own (the events are reused: the deposits' waits were enqueued
+        // against the position records already)
+        for (int c = 0; c < nch; ++c) {
+            int64_t lo, hi;
+            bounds(c, &lo, &hi);
+            if (hi <= lo) continue;
+            if ((e = cudaMemcpyAsync(vel_kick + lo, io->vel_up + lo, (size_t)(hi - lo) * 16, cudaMemcpyHostToDevice,
+                                     io->copy)) != cudaSuccess)
+                return check_cuda(ctx, e, "H2D copy");
+            if ((e = cudaEventRecord(io->ev[c], io->copy)) != cudaSuccess) return check_cuda(ctx, e, "cudaEventRecord");
+        }
     }
     k_fix_to_density<<<blocks_for((int64_t)ng3), kBlock, 0, s>>>((int64_t)ng3, st->mass, 1.0 / (kFix * D * D * D),
                                                                    st->rho);
@@ -325,12 +333,12 @@ hacc_status pm_accel(hacc_ctx *ctx, const hacc_box *box, const hacc_pm *pm, doub
     note_launch();
     if (before_kick && (e = cudaStreamWaitEvent(s, before_kick, 0)) != cudaSuccess)
         return check_cuda(ctx, e, "cudaStreamWaitEvent");
-    if (io && io->vel_up && (e = cudaStreamWaitEvent(s, io->vel_ready, 0)) != cudaSuccess)
-        return check_cuda(ctx, e, "cudaStreamWaitEvent");
     for (int c = 0; c < nch; ++c) {
         int64_t lo, hi;
         bounds(c, &lo, &hi);
         if (hi <= lo) continue;
+        if (io && io->vel_up && (e = cudaStreamWaitEvent(s, io->ev[c], 0)) != cudaSuccess)
+            return check_cuda(ctx, e, "cudaStreamWaitEvent");
         k_interp<<<blocks_for(hi - lo), kBlock, 0, s>>>(hi - lo, pos + lo, inv_d, ng, st->field, acc ? acc + lo : nullptr,
                                                         vel_kick ? vel_kick + lo : nullptr, kick);
         note_launch();
