@@ -113,6 +113,7 @@ const int kTuneCaps[] = {0, 16, 24, 32, 48};
 constexpr int kTuneCapCount = 5;
 constexpr int kTuneSettings = kTuneCapCount * 2 * kForceVariants;   // cap x queue order x variant
 static_assert(kTuneSettings == HACC_TUNE_SETTINGS, "tuner table size");
+static_assert(sizeof(hacc_ctx::io_ev) / sizeof(void *) >= 3 + kPmChunks, "one event per PM chunk");
 
 static double binom(int n, int k) {
     double r = 1.0;

@@ -83,7 +83,7 @@ struct hacc_ctx {
     // host-buffer full steps (api.cu): a second stream and events that let the
     // velocity upload and the position download overlap the PM stages
     void *io_stream = nullptr;
-    void *io_ev[3 + 8] = {};   // [0..2] step events, [3..] the PM stage's chunk events (kPmChunks)
+    void *io_ev[3 + 16] = {};   // [0..2] step events, [3..] the PM stage's chunk events (kPmChunks)
     bool ml_graph_off = false;   // set when the device refused the graph once
 };
 
@@ -413,7 +413,7 @@ cudaError_t diag_mass_moment_ci(int64_t n, const int32_t *cell, const float4 *of
 // closing kick the positions are downloaded while the field is solved, and
 // the kicked velocities chunk by chunk as they are interpolated.  The deposit
 // sums fixed-point integers, so the chunking changes no bit.
-constexpr int kPmChunks = 8;
+constexpr int kPmChunks = 16;
 struct PmHostIO {
     cudaStream_t copy = nullptr;
     cudaEvent_t ev[kPmChunks] = {};
