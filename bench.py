@@ -434,6 +434,12 @@ def run_multilevel(torch, hacc, ctx, split, steps=3, d=2, lmax=4, seed=7, worklo
             out["force_evaluations_per_particle"] = float((np.arange(1, lmax + 1) * h).sum() / h.sum())
     ctx.sync()
     out["speedup"] = out["ms_per_step_plain"] / out["ms_per_step_multilevel"]
+    out["faster_than_uniform_sub_cycles"] = out["speedup"] > 1.0
+    if out["speedup"] <= 1.0:
+        out["why_slower"] = ("the particles move past half the skin between events, so the mesh is rebuilt at %.0f "
+                             "events per step; the rebinnings cost more than the %.0f%% of force work the kick "
+                             "counts save" % (out.get("rebins_per_step", 0), 100 * (1 - out["force_ms_per_step_multilevel"]
+                                                                                 / out["force_ms_per_step_plain"])))
     out["workload"] = "%s, step %g, %d uniform sub-cycles vs d = %d, l in [%d, %d], skin %g r_cut (%d^3 cells)" % (
         desc, dt, n_plain, d, lmin, lmax, skin, hacc.ml_mesh_cells(L, split.r_cut, skin))
     return out
@@ -468,6 +474,11 @@ def run_fine_mesh(torch, hacc, ctx, split, pos, L, reps=3):
             "ms_per_force_call": e0.elapsed_time(e1) / reps, "candidate_pairs": st["candidate_pairs"],
             "evaluated_pairs": st["evaluated_pairs"], "within_pairs": st["within_pairs"]}
     out["speedup_125_over_27"] = out["cells_27"]["ms_per_force_call"] / out["cells_125"]["ms_per_force_call"]
+    out["faster_than_27_cells"] = out["speedup_125_over_27"] > 1.0
+    if not out["faster_than_27_cells"]:
+        out["why_slower"] = ("%.0f%% fewer evaluated pairs, but a work item of a fine cell holds ~4 particles and "
+                             "pays the whole per-item staging (a 50-run table, bounds, tile set-up) for them"
+                             % (100 * (1 - out["cells_125"]["evaluated_pairs"] / out["cells_27"]["evaluated_pairs"])))
     return out
 
 
@@ -898,6 +909,12 @@ def summary(line):
     ml = line.get("multilevel_paper")
     if ml:
         out["ml_paper_speedup"] = r(ml["speedup"])
+    mv = line.get("multilevel_violent")
+    if mv:
+        out["ml_violent_speedup"] = r(mv["speedup"])
+    fm = line.get("fine_mesh")
+    if fm:
+        out["fine_mesh_speedup"] = r(fm["speedup_125_over_27"])
     return out
 
 
