@@ -426,3 +426,34 @@ def test_fine_mesh_smallest_box_against_brute_force(torch, hacc, ctx, split_para
     with pytest.raises(hacc.HaccError) as e:
         ctx.sr_force(hacc.Box(L=L), sp, p)
     assert e.value.status == hacc.HACC_EDOMAIN
+
+
+def test_bin_every_in_cell_ordering_path_bit_exact(torch, hacc, ctx, split_params):
+    # cells holding counts on both sides of every ordering path's bound (the
+    # register stretches and the 32-key network, the 64/128/256-key networks,
+    # counting above 256, the big-cell sort above 512), with input rows
+    # shuffled (few stretches), cell-sorted (long stretches) and in runs of 3
+    # (lattice-like stretches); the order must be the stable one, bit for bit
+    rc = np.float32(split_params["r_cut"])
+    L = 32.0
+    nc = hacc.mesh_cells(L, rc)
+    w = L / nc
+    counts = [1, 2, 16, 31, 32, 33, 48, 63, 64, 65, 100, 127, 128, 129, 200, 255, 256, 257, 400, 511, 512, 513, 700]
+    rng = np.random.default_rng(91)
+    cells = rng.choice(nc ** 3, size=len(counts), replace=False)
+    per_cell = np.full(nc ** 3, 20)
+    per_cell[cells] = counts
+    ids = np.repeat(np.arange(nc ** 3), per_cell)
+    cz, cy, cx = ids // (nc * nc), (ids // nc) % nc, ids % nc
+    frac = rng.uniform(0.02, 0.98, (len(ids), 3))
+    xyz = (np.stack([cx, cy, cz], 1) + frac) * w
+    base = np.concatenate([xyz, np.ones((len(ids), 1))], 1).astype(np.float32)
+    orders = {"shuffled": rng.permutation(len(ids)), "cell_sorted": np.arange(len(ids))}
+    runs = rng.permutation(len(ids) // 3)
+    orders["runs_of_3"] = np.concatenate([(runs[:, None] * 3 + np.arange(3)[None, :]).ravel(),
+                                          np.arange(len(ids) // 3 * 3, len(ids))])
+    for name, order in orders.items():
+        pos = base[order]
+        _, cell_o, _ = oracle.wrap_cell(pos, L, nc)
+        assert sorted(np.bincount(cell_o, minlength=nc ** 3)[cells]) == sorted(counts), name
+        _check_bin(torch, hacc, ctx, pos, L, rc)
