@@ -56,11 +56,12 @@ def test_full_step_parity(env, split_params):
     assert np.abs(vv[:, :3] - vo).max() < 1e-3 * vscale
 
 
-def test_step_host_equals_device(env, split_params):
+@pytest.mark.parametrize("n", [4000, 5])   # 5: fewer particles than the copy chunks
+def test_step_host_equals_device(env, split_params, n):
     torch, hacc, ctx = env
     L = 16.0
-    pos = synth.blob_mixture(4000, L, seed=52)
-    vel = synth.gaussian_velocities(4000, seed=52)
+    pos = synth.blob_mixture(n, L, seed=52)
+    vel = synth.gaussian_velocities(n, seed=52)
     p, v = torch.from_numpy(pos.copy()).cuda(), torch.from_numpy(vel.copy()).cuda()
     ctx.step(hacc.Box(L=L), split_params, hacc.PM(), p, v, 0.1, 2)
     ctx.sync()
